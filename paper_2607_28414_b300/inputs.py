@@ -1,0 +1,242 @@
+"""Seeded synthetic inputs for the reduced Kelvin-Voigt shear-wave solver.
+
+This module builds the *inputs* of the method only: material maps (G, rho, eta),
+body-force patterns b0(x), the temporal envelope table g(t_n), sensor lists and
+initial velocity fields. It holds none of the method's arithmetic (no stencil,
+no projection, no stability bound), so it can feed both the CUDA library and
+the CPU oracle without sharing any computation between them.
+
+Conventions
+-----------
+* Arrays are float32, C-contiguous, shape (nz, ny, nx): x is the fastest axis.
+* Node (i, j, k) sits at x = i*dx, y = j*dx, z = k*dx. The outer node layer is
+  the Dirichlet layer of the solver.
+* Gaussians use the 1/e-width convention exp(-(r/sigma)^2), as in the QIBA
+  force model of Sec. 4.4 (Eq. gaussexc).
+* Workload recipes name the shapes of the paper's experiments: the Gaussian
+  push (Sec. 4.4), soft-tissue moduli, densities and viscosities (Sec. 2.1,
+  Sec. 5), a 200 us step push (Sec. 3.3: g(t)=1 during the push).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MM = 1e-3
+
+
+def _axes(nx: int, ny: int, nz: int, dx: float, centre_ijk):
+    ci, cj, ck = centre_ijk
+    x = (np.arange(nx, dtype=np.float64) - ci) * dx
+    y = (np.arange(ny, dtype=np.float64) - cj) * dx
+    z = (np.arange(nz, dtype=np.float64) - ck) * dx
+    return x[None, None, :], y[None, :, None], z[:, None, None]
+
+
+def centre_node(nx: int, ny: int, nz: int):
+    """Integer centre node (nx//2, ny//2, nz//2) so that sensors sit on nodes."""
+    return (nx // 2, ny // 2, nz // 2)
+
+
+def gaussian_push(nx, ny, nz, dx, amplitude=1e3, sigma_lat=1 * MM, sigma_ax=2 * MM,
+                  centre_ijk=None, axis=2):
+    """Separable Gaussian push b0 along one axis (default z).
+
+    b_axis = A exp(-(lateral/sigma_lat)^2 - (axial/sigma_ax)^2), the other two
+    components zero. Returns (fx, fy, fz) float32 arrays.
+    """
+    if centre_ijk is None:
+        centre_ijk = centre_node(nx, ny, nz)
+    x, y, z = _axes(nx, ny, nz, dx, centre_ijk)
+    coords = [x, y, z]
+    ax = coords[axis]
+    lat = [c for a, c in enumerate(coords) if a != axis]
+    val = amplitude * np.exp(-(lat[0] / sigma_lat) ** 2 - (lat[1] / sigma_lat) ** 2
+                             - (ax / sigma_ax) ** 2)
+    val = np.ascontiguousarray(np.broadcast_to(val, (nz, ny, nx)), dtype=np.float32)
+    out = [np.zeros((nz, ny, nx), np.float32) for _ in range(3)]
+    out[axis] = val
+    return tuple(out)
+
+
+def lognormal_speckle(rng, shape, sigma=0.3):
+    """I.i.d. unit-mean lognormal speckle exp(sigma*xi - sigma^2/2), xi ~ N(0,1)."""
+    xi = rng.standard_normal(shape)
+    return np.exp(sigma * xi - 0.5 * sigma * sigma)
+
+
+def beam_push(nx, ny, nz, dx, rng, amplitude=1e3, core=1 * MM, focal_depth=10 * MM,
+              focal_len=4 * MM, speckle_sigma=0.3, axis_ij=None, z0=0.0):
+    """Non-separable axial beam force f_z: Gaussian core around the beam axis,
+    Gaussian focal zone along z, times lognormal speckle.
+
+    f_z = A exp(-(r_perp/core)^2) exp(-((z - z0 - focal_depth)/focal_len)^2) * S(x)
+    The beam enters from the z = z0 face; its axis passes through node columns
+    axis_ij = (i, j) (default: the x-y centre).
+    """
+    if axis_ij is None:
+        axis_ij = (nx // 2, ny // 2)
+    x, y, _ = _axes(nx, ny, nz, dx, (axis_ij[0], axis_ij[1], 0))
+    z = (np.arange(nz, dtype=np.float64) * dx)[:, None, None]
+    core_prof = np.exp(-(x * x + y * y) / core ** 2)
+    ax_prof = np.exp(-((z - z0 - focal_depth) / focal_len) ** 2)
+    fz = amplitude * core_prof * ax_prof
+    fz = fz * lognormal_speckle(rng, (nz, ny, nx), speckle_sigma)
+    fz = np.ascontiguousarray(fz, dtype=np.float32)
+    z0s = np.zeros((nz, ny, nx), np.float32)
+    return z0s, z0s.copy(), fz
+
+
+@dataclass
+class Inclusion:
+    centre: tuple  # metres (x, y, z)
+    radius: float
+    G: float
+    rho: float
+    eta: float
+
+
+def spherical_inclusions(nx, ny, nz, dx, rng, n=8, G_bg=3e3, rho_bg=1000.0, eta_bg=0.5,
+                         r_range=(2 * MM, 6 * MM), G_range=(1e3, 10e3),
+                         rho_range=(1000.0, 1100.0), eta_range=(0.0, 1.5), margin=1 * MM):
+    """Heterogeneous medium: background plus n seeded spheres.
+
+    Each sphere draws r ~ U(r_range), a centre uniform inside the box with a wall
+    margin of r + margin, and G, rho, eta uniform in their ranges. A later sphere
+    overwrites an earlier one where they overlap. Returns (G, rho, eta, list).
+    """
+    L = np.array([(nx - 1) * dx, (ny - 1) * dx, (nz - 1) * dx])
+    G = np.full((nz, ny, nx), G_bg, np.float64)
+    rho = np.full((nz, ny, nx), rho_bg, np.float64)
+    eta = np.full((nz, ny, nx), eta_bg, np.float64)
+    x = (np.arange(nx) * dx)[None, None, :]
+    y = (np.arange(ny) * dx)[None, :, None]
+    z = (np.arange(nz) * dx)[:, None, None]
+    incl = []
+    for _ in range(n):
+        r = rng.uniform(*r_range)
+        c = [rng.uniform(r + margin, L[a] - r - margin) for a in range(3)]
+        g = rng.uniform(*G_range)
+        rh = rng.uniform(*rho_range)
+        et = rng.uniform(*eta_range)
+        inside = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= r * r
+        G[inside] = g
+        rho[inside] = rh
+        eta[inside] = et
+        incl.append(Inclusion(tuple(c), r, g, rh, et))
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return f32(G), f32(rho), f32(eta), incl
+
+
+def push_envelope(n_steps, dt, t_push):
+    """Step envelope of a push: g_n = 1 while t_n = n*dt < t_push, else 0."""
+    n = np.arange(n_steps, dtype=np.float64)
+    return (n * dt < t_push).astype(np.float32)
+
+
+def pulsed_envelope(n_steps, dt, t_on, t_off, n_pulses):
+    """Pulsed push train: n_pulses repetitions of t_on on, t_off off."""
+    t = np.arange(n_steps, dtype=np.float64) * dt
+    period = t_on + t_off
+    idx = np.floor(t / period)
+    on = (t - idx * period) < t_on
+    return (on & (idx < n_pulses)).astype(np.float32)
+
+
+def line_sensors(start_ijk, axis, stop, stride=1):
+    """Sensors along one axis from start_ijk (inclusive) to stop (exclusive)."""
+    pts = []
+    for s in range(start_ijk[axis], stop, stride):
+        p = list(start_ijk)
+        p[axis] = s
+        pts.append(p)
+    return np.asarray(pts, dtype=np.int32).reshape(-1, 3)
+
+
+def curl_gaussian_velocity(nx, ny, nz, dx, sigma=3 * MM, peak=1e-3, centre_ijk=None,
+                           envelope="xy"):
+    """Divergence-free initial velocity v0 = curl(psi * e_y).
+
+    envelope="xy": psi = exp(-(x^2 + y^2)/sigma^2), a Gaussian envelope in the
+    x-y plane (Sec. 4.1), so v0 = (0, 0, d(psi)/dx): z motion, odd in x.
+    envelope="xyz": psi = exp(-r^2/sigma^2), v0 = (-d(psi)/dz, 0, d(psi)/dx).
+    Analytic derivatives at nodes, scaled to a peak speed `peak`.
+    """
+    if centre_ijk is None:
+        centre_ijk = centre_node(nx, ny, nz)
+    x, y, z = _axes(nx, ny, nz, dx, centre_ijk)
+    if envelope == "xy":
+        psi = np.exp(-(x * x + y * y) / sigma ** 2) + 0.0 * z
+        vx = np.zeros((nz, ny, nx))
+    elif envelope == "xyz":
+        psi = np.exp(-(x * x + y * y + z * z) / sigma ** 2)
+        vx = np.broadcast_to((2.0 * z / sigma ** 2) * psi, (nz, ny, nx))
+    else:
+        raise ValueError(envelope)
+    vz = np.broadcast_to(-(2.0 * x / sigma ** 2) * psi, (nz, ny, nx))
+    s = peak / float(np.sqrt(vx * vx + vz * vz).max())
+    f32 = lambda a: np.ascontiguousarray(a * s, dtype=np.float32)
+    return f32(vx), np.zeros((nz, ny, nx), np.float32), f32(vz)
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    """One synthetic problem: grid, medium, force pattern, envelope, sensors.
+
+    dt is not part of a workload: the caller takes `cfl_fraction` of the
+    stability limit computed by the solver (or by the oracle in tests).
+    """
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    G: object  # float (homogeneous) or float32 array (nz, ny, nx)
+    rho: object
+    eta: object
+    force: tuple  # (fx, fy, fz) float32 arrays
+    t_push: float
+    n_steps: int
+    sensors: np.ndarray
+    tol: float
+    cfl_fraction: float = 0.5
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self):
+        return self.nx * self.ny * self.nz
+
+
+def homogeneous_push(n=64, dx=0.2 * MM, G=4e3, rho=1000.0, eta=0.0, n_steps=400,
+                     t_push=200e-6, tol=1e-10, name=None, ny=None, nz=None):
+    """Plain method on a homogeneous grid with the separable Gaussian push along z
+    (sigma 1 mm lateral, 2 mm axial, centred, 1e3 N/m^3), sensors on the x line
+    through the centre from the centre to the last interior node."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    nx = n
+    c = centre_node(nx, ny, nz)
+    force = gaussian_push(nx, ny, nz, dx, 1e3, 1 * MM, 2 * MM, c, axis=2)
+    sensors = line_sensors(c, 0, nx - 1, 1)
+    return Workload(name or f"homogeneous_{nx}x{ny}x{nz}", nx, ny, nz, dx, float(G), float(rho),
+                    float(eta), force, t_push, n_steps, sensors, tol)
+
+
+def heterogeneous_inclusions(n=256, dx=0.2 * MM, seed=102, n_steps=2000, t_push=200e-6,
+                             tol=1e-8, n_incl=8, name=None):
+    """Heterogeneous medium with 8 seeded spherical inclusions and a speckled
+    axial beam focused 10 mm below the z = 0 face; sensors every second node
+    on the x line at the focal depth."""
+    rng = np.random.default_rng(seed)
+    G, rho, eta, incl = spherical_inclusions(n, n, n, dx, rng, n=n_incl)
+    force = beam_push(n, n, n, dx, rng)
+    kf = int(round(10 * MM / dx))
+    sensors = line_sensors((1, n // 2, kf), 0, n - 1, 2)
+    return Workload(name or f"heterogeneous_inclusions_{n}^3", n, n, n, dx, G, rho, eta, force,
+                    t_push, n_steps, sensors, tol, extra={"inclusions": incl, "seed": seed})

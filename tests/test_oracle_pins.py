@@ -1,0 +1,448 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+eigenvalues, exactness on quadratics, dense Kronecker solves, a sine-transform
+direct solve, manufactured solutions, conserved energies, scalar recurrences of
+single modes and the paper's stability bound.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+
+DX = 2e-4
+
+
+def grid_coords(nx, ny, nz, dx=DX):
+    x = (np.arange(nx) * dx)[None, None, :]
+    y = (np.arange(ny) * dx)[None, :, None]
+    z = (np.arange(nz) * dx)[:, None, None]
+    return x, y, z
+
+
+def interior_mask(nx, ny, nz):
+    m = np.zeros((nz, ny, nx), bool)
+    m[1:-1, 1:-1, 1:-1] = True
+    return m
+
+
+def sine_mode(nx, ny, nz, kx, ky, kz):
+    """Discrete Dirichlet eigenvector prod sin(pi k_a i_a / (n_a - 1))."""
+    i = np.arange(nx)
+    j = np.arange(ny)
+    k = np.arange(nz)
+    sx = np.sin(np.pi * kx * i / (nx - 1))
+    sy = np.sin(np.pi * ky * j / (ny - 1))
+    sz = np.sin(np.pi * kz * k / (nz - 1))
+    return sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+
+
+def sine_eigenvalue(n_axes, k_axes, dx=DX):
+    """-L s = lam s with lam = sum_a (4/dx^2) sin^2(pi k_a / (2 (n_a - 1)))."""
+    return sum(4.0 / dx ** 2 * np.sin(np.pi * k / (2.0 * (n - 1))) ** 2
+               for n, k in zip(n_axes, k_axes))
+
+
+def dense_negative_laplacian(nx, ny, nz, dx=DX):
+    """Textbook matrix of -L on interior unknowns: Kronecker sum of 1D second
+    differences tridiag(1, -2, 1)/dx^2 (x fastest)."""
+    def T(n):
+        m = n - 2
+        return (np.diag(-2.0 * np.ones(m)) + np.diag(np.ones(m - 1), 1)
+                + np.diag(np.ones(m - 1), -1)) / dx ** 2
+    Ix, Iy, Iz = (np.eye(n - 2) for n in (nx, ny, nz))
+    L = (np.kron(Iz, np.kron(Iy, T(nx))) + np.kron(Iz, np.kron(T(ny), Ix))
+         + np.kron(T(nz), np.kron(Iy, Ix)))
+    return -L
+
+
+def bump(nx, ny, nz, lo, hi, seed=0):
+    """Smooth compactly supported bump: prod sin^4 over the node box [lo, hi],
+    exactly zero outside it, times a fixed random polynomial-free scale."""
+    out = np.zeros((nz, ny, nx))
+    rng = np.random.default_rng(seed)
+    def w(n, a, b):
+        t = np.zeros(n)
+        idx = np.arange(a, b + 1)
+        t[idx] = np.sin(np.pi * (idx - a) / (b - a)) ** 4
+        return t
+    out[:] = (w(nz, lo[2], hi[2])[:, None, None] * w(ny, lo[1], hi[1])[None, :, None]
+              * w(nx, lo[0], hi[0])[None, None, :])
+    return out * (1.0 + rng.uniform())
+
+
+# ---------------------------------------------------------------------------
+# 7-point Laplacian (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def test_laplacian_exact_on_quadratics():
+    nx, ny, nz = 9, 7, 8
+    x, y, z = grid_coords(nx, ny, nz)
+    q = 3.0 * x ** 2 - 1.5 * y ** 2 + 0.25 * z ** 2 + 2.0 * x * y - 0.7 * y * z + 5 * x - 2 * z + 1
+    q = np.broadcast_to(q, (nz, ny, nx))
+    L = orc.laplacian(q, DX)
+    m = interior_mask(nx, ny, nz)
+    expect = 2 * (3.0 - 1.5 + 0.25)
+    assert np.allclose(L[m], expect, rtol=1e-8, atol=1e-8 * abs(expect))
+    assert np.all(L[~m] == 0.0)
+
+
+@pytest.mark.parametrize("modes", [(1, 1, 1), (2, 3, 1), (5, 1, 4)])
+def test_laplacian_sine_eigenvalues(modes):
+    n = (12, 10, 11)
+    s = sine_mode(*n, *modes)
+    L = orc.laplacian(s, DX)
+    lam = sine_eigenvalue(n, modes)
+    m = interior_mask(*n)
+    np.testing.assert_allclose(L[m], -lam * s[m], rtol=0, atol=1e-9 * lam)
+
+
+def test_div_and_grad_on_linear_fields():
+    nx, ny, nz = 8, 9, 7
+    x, y, z = grid_coords(nx, ny, nz)
+    sh = (nz, ny, nx)
+    fx, fy, fz = (np.broadcast_to(v, sh) for v in (2.0 * x + y, -3.0 * y + z, 0.5 * z + x))
+    d = orc.div_minus(fx, fy, fz, DX)
+    m = interior_mask(nx, ny, nz)
+    np.testing.assert_allclose(d[m], 2.0 - 3.0 + 0.5, rtol=1e-9)
+    assert np.all(d[~m] == 0)
+    phi = np.broadcast_to(4.0 * x - 2.0 * y + 7.0 * z, sh)
+    gx, gy, gz = orc.grad_plus(phi, DX)
+    np.testing.assert_allclose(gx[:, :, :-1], 4.0, rtol=1e-9)
+    np.testing.assert_allclose(gy[:, :-1, :], -2.0, rtol=1e-9)
+    np.testing.assert_allclose(gz[:-1, :, :], 7.0, rtol=1e-9)
+    # phi = 0 beyond the last node
+    np.testing.assert_allclose(gx[:, :, -1], -phi[:, :, -1] / DX, rtol=1e-12)
+
+
+def test_div_of_grad_is_laplacian():
+    """Mimetic pair: D-(D+ phi) = L phi on the interior when phi vanishes on the
+    outer layer (brute-force check on a random field)."""
+    n = (9, 8, 10)
+    rng = np.random.default_rng(3)
+    phi = rng.standard_normal(n[::-1])
+    phi[~interior_mask(*n)] = 0
+    g = orc.grad_plus(phi, DX)
+    d = orc.div_minus(*g, DX)
+    L = orc.laplacian(phi, DX)
+    np.testing.assert_allclose(d, L, rtol=0, atol=1e-9 * np.abs(L).max())
+
+
+# ---------------------------------------------------------------------------
+# Masked CG (Sec. 3.2.3)
+# ---------------------------------------------------------------------------
+
+def test_cg_matches_dense_solve():
+    nx, ny, nz = 8, 7, 9
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal((nz, ny, nx))
+    m = interior_mask(nx, ny, nz)
+    b[~m] = 0
+    A = dense_negative_laplacian(nx, ny, nz)
+    x_dense = np.linalg.solve(A, b[1:-1, 1:-1, 1:-1].ravel())
+    phi, status, st = orc.cg(b, DX, 1e-14, 1000)
+    assert status == "converged"
+    np.testing.assert_allclose(phi[1:-1, 1:-1, 1:-1].ravel(), x_dense, rtol=0,
+                               atol=1e-12 * np.abs(x_dense).max())
+    assert np.all(phi[~m] == 0)
+    assert st["true_rel_res"] < 1e-12
+
+
+def dst_solve(b, dx=DX):
+    """Direct solve of -L phi = b by discrete sine transforms written from the
+    eigen-decomposition: S_{pq} = sin(pi p q / (n - 1)), S^{-1} = 2/(n-1) S."""
+    nz, ny, nx = b.shape
+    def S(n):
+        p = np.arange(1, n - 1)
+        return np.sin(np.pi * np.outer(p, p) / (n - 1))
+    Sx, Sy, Sz = S(nx), S(ny), S(nz)
+    bi = b[1:-1, 1:-1, 1:-1]
+    bh = np.einsum("ai,bj,ck,kji->cba", Sx, Sy, Sz, bi, optimize=True)
+    lam = (4 / dx ** 2 * np.sin(np.pi * np.arange(1, nz - 1) / (2 * (nz - 1))) ** 2)[:, None, None] \
+        + (4 / dx ** 2 * np.sin(np.pi * np.arange(1, ny - 1) / (2 * (ny - 1))) ** 2)[None, :, None] \
+        + (4 / dx ** 2 * np.sin(np.pi * np.arange(1, nx - 1) / (2 * (nx - 1))) ** 2)[None, None, :]
+    ph = bh / lam
+    scale = (2.0 / (nx - 1)) * (2.0 / (ny - 1)) * (2.0 / (nz - 1))
+    phi_i = scale * np.einsum("ai,bj,ck,kji->cba", Sx, Sy, Sz, ph, optimize=True)
+    out = np.zeros_like(b)
+    out[1:-1, 1:-1, 1:-1] = phi_i
+    return out
+
+
+def test_cg_matches_sine_transform_solve():
+    nx, ny, nz = 26, 22, 30
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((nz, ny, nx))
+    b[~interior_mask(nx, ny, nz)] = 0
+    ref = dst_solve(b)
+    phi, status, st = orc.cg(b, DX, 1e-13, 5000)
+    assert status == "converged"
+    np.testing.assert_allclose(phi, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_cg_stopping_rule_and_guards():
+    nx = ny = nz = 12
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal((nz, ny, nx))
+    b[~interior_mask(nx, ny, nz)] = 0
+    phi, status, st = orc.cg(b, DX, 1e-6, 1000)
+    assert status == "converged" and st["rel_res"] < 1e-6
+    # one iteration fewer must not have met the tolerance
+    _, status2, st2 = orc.cg(b, DX, 1e-6, st["iters"] - 1)
+    assert status2 == "maxiter" and st2["rel_res"] >= 1e-6
+    # zero right-hand side: phi = 0, no iterations
+    phi0, s0, st0 = orc.cg(np.zeros_like(b), DX, 1e-8, 100)
+    assert s0 == "zero_rhs" and st0["iters"] == 0 and not phi0.any()
+    # non-finite right-hand side
+    bn = b.copy()
+    bn[5, 5, 5] = np.nan
+    _, sn, _ = orc.cg(bn, DX, 1e-8, 100)
+    assert sn == "nonfinite"
+
+
+def test_cg_eigenvector_rhs_converges_in_one_iteration():
+    n = (10, 9, 11)
+    s = sine_mode(*n, 2, 1, 3)
+    lam = sine_eigenvalue(n, (2, 1, 3))
+    phi, status, st = orc.cg(s, DX, 1e-12, 50)
+    assert st["iters"] == 1 and status == "converged"
+    np.testing.assert_allclose(phi, s / lam, atol=1e-12 * np.abs(s / lam).max())
+
+
+# ---------------------------------------------------------------------------
+# Solenoidal projection (Sec. 3.2.1, 3.3)
+# ---------------------------------------------------------------------------
+
+def backward_diff(q, axis, dx=DX):
+    """D- along an axis (array axis order z, y, x), zero in the first slice."""
+    out = np.zeros_like(q)
+    sl_hi = [slice(None)] * 3
+    sl_lo = [slice(None)] * 3
+    sl_hi[axis] = slice(1, None)
+    sl_lo[axis] = slice(0, -1)
+    out[tuple(sl_hi)] = (q[tuple(sl_hi)] - q[tuple(sl_lo)]) / dx
+    return out
+
+
+def forward_diff(q, axis, dx=DX):
+    out = np.zeros_like(q)
+    sl_hi = [slice(None)] * 3
+    sl_lo = [slice(None)] * 3
+    sl_hi[axis] = slice(1, None)
+    sl_lo[axis] = slice(0, -1)
+    out[tuple(sl_lo)] = (q[tuple(sl_hi)] - q[tuple(sl_lo)]) / dx
+    return out
+
+
+def curl_minus(px, py, pz):
+    """Curl built from backward differences; its backward divergence is zero."""
+    X, Y, Z = 2, 1, 0
+    cx = backward_diff(pz, Y) - backward_diff(py, Z)
+    cy = backward_diff(px, Z) - backward_diff(pz, X)
+    cz = backward_diff(py, X) - backward_diff(px, Y)
+    return cx, cy, cz
+
+
+def manufactured(n=(20, 18, 22)):
+    nx, ny, nz = n
+    phi_star = bump(nx, ny, nz, (3, 3, 4), (nx - 5, ny - 4, nz - 4), seed=1)
+    psi = [bump(nx, ny, nz, (4 + a, 3, 3 + a), (nx - 6, ny - 5 + a, nz - 4), seed=2 + a)
+           for a in range(3)]
+    gx, gy, gz = (forward_diff(phi_star, ax) for ax in (2, 1, 0))
+    cx, cy, cz = curl_minus(*psi)
+    return phi_star, (gx, gy, gz), (cx, cy, cz)
+
+
+def test_projection_recovers_manufactured_parts():
+    phi_star, grad, curl = manufactured()
+    f = [g + c for g, c in zip(grad, curl)]
+    phi, fs, status, st = orc.project(*f, DX, tol=1e-13)
+    assert status == "converged"
+    np.testing.assert_allclose(phi, phi_star, atol=1e-9 * np.abs(phi_star).max())
+    for a in range(3):
+        np.testing.assert_allclose(fs[a], curl[a], atol=1e-9 * np.abs(curl[a]).max())
+
+
+def test_projection_invariants():
+    rng = np.random.default_rng(7)
+    n = (18, 16, 20)
+    nx, ny, nz = n
+    f = [rng.standard_normal((nz, ny, nx)) for _ in range(3)]
+    m = interior_mask(nx, ny, nz)
+    phi, fs, status, st = orc.project(*f, DX, tol=1e-12)
+    assert status == "converged"
+    div_f = orc.div_minus(*f, DX)
+    div_fs = orc.div_minus(*fs, DX)
+    # ||D-.f_S|| / ||D-.f|| equals the true relative residual of the solve
+    ratio = np.linalg.norm(div_fs) / np.linalg.norm(div_f)
+    assert ratio < 1e-11
+    assert ratio == pytest.approx(st["true_rel_res"], rel=1e-2, abs=1e-14)
+    # idempotence: P(P f) = P f
+    _, fs2, _, _ = orc.project(*fs, DX, tol=1e-12)
+    for a in range(3):
+        np.testing.assert_allclose(fs2[a], fs[a], atol=1e-9 * np.abs(fs[a]).max())
+    # linearity
+    g = [rng.standard_normal((nz, ny, nx)) for _ in range(3)]
+    _, fsg, _, _ = orc.project(*g, DX, tol=1e-13)
+    _, fsc, _, _ = orc.project(*[2.0 * a - 0.5 * b for a, b in zip(f, g)], DX, tol=1e-13)
+    for a in range(3):
+        np.testing.assert_allclose(fsc[a], 2.0 * fs[a] - 0.5 * fsg[a],
+                                   atol=1e-9 * np.abs(fsc[a]).max())
+
+
+def test_projection_removes_gradients():
+    phi_star, grad, _ = manufactured()
+    _, fs, status, _ = orc.project(*grad, DX, tol=1e-13)
+    for a in range(3):
+        assert np.abs(fs[a]).max() < 1e-9 * np.abs(grad[a]).max()
+
+
+# ---------------------------------------------------------------------------
+# Time stepping (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def mode_coefficients(a_lam, b_lam, n_steps, c0=1.0, cm1=1.0):
+    """Closed form of one Laplacian eigenmode under the recurrence:
+    c_{n+1} = (2 - (a+b) lam) c_n - (1 - b lam) c_{n-1}, solved through the
+    roots of z^2 - (2 - (a+b) lam) z + (1 - b lam) = 0."""
+    p = 2.0 - a_lam - b_lam
+    q = 1.0 - b_lam
+    disc = np.sqrt(complex(p * p - 4 * q))
+    z1, z2 = (p + disc) / 2, (p - disc) / 2
+    # c_n = P z1^n + Q z2^n with c_0 = c0, c_{-1} = cm1
+    M = np.array([[1, 1], [1 / z1, 1 / z2]])
+    P, Q = np.linalg.solve(M, np.array([c0, cm1], complex))
+    n = np.arange(1, n_steps + 1)
+    return (P * z1 ** n + Q * z2 ** n).real
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.8])
+def test_step_sine_mode_closed_form(eta):
+    n = (12, 11, 13)
+    nx, ny, nz = n
+    G, rho = 4e3, 1000.0
+    dt = 0.5 * orc.stable_dt(G, rho, eta, DX)
+    modes = [(1, 2, 1), (3, 1, 2), (2, 2, 3)]
+    u0 = [sine_mode(*n, *mk) for mk in modes]
+    um = [0.9 * s for s in u0]  # c_{-1} = 0.9: the mode starts moving
+    n_steps = 60
+    sensors = np.array([[3, 4, 5], [7, 2, 9]], np.int32)
+    tr, u_end, _ = orc.run(nx, ny, nz, DX, dt, G, rho, eta, n_steps, sensors,
+                           u_in=u0, uprev_in=um, want_state=True)
+    for c, mk in enumerate(modes):
+        lam = sine_eigenvalue(n, mk)
+        coef = mode_coefficients(dt * dt * G / rho * lam, dt * eta / rho * lam, n_steps,
+                                 1.0, 0.9)
+        for s, (i, j, k) in enumerate(sensors):
+            np.testing.assert_allclose(tr[:, s, c], coef * u0[c][k, j, i], rtol=0,
+                                       atol=1e-10 * abs(u0[c][k, j, i]) + 1e-14)
+        np.testing.assert_allclose(u_end[c], coef[-1] * u0[c], atol=1e-10)
+
+
+def energy(u_next, u_cur, A, dx=DX):
+    """E^{n+1/2} = sum (u^{n+1}-u^n)^2 / A - <u^{n+1}, L u^n>, A = dt^2 mu/rho,
+    with L written here with numpy slicing (interior, Dirichlet layer = 0)."""
+    def lap(q):
+        out = np.zeros_like(q)
+        c = q[1:-1, 1:-1, 1:-1]
+        out[1:-1, 1:-1, 1:-1] = (q[2:, 1:-1, 1:-1] + q[:-2, 1:-1, 1:-1] + q[1:-1, 2:, 1:-1]
+                                 + q[1:-1, :-2, 1:-1] + q[1:-1, 1:-1, 2:] + q[1:-1, 1:-1, :-2]
+                                 - 6 * c) / dx ** 2
+        return out
+    m = interior_mask(*u_cur.shape[1:][::-1])
+    e = 0.0
+    for c in range(3):
+        v = (u_next[c] - u_cur[c])[m]
+        e += np.sum(v * v / A[m]) - np.sum(u_next[c] * lap(u_cur[c]))
+    return e
+
+
+def test_step_conserves_weighted_energy_heterogeneous():
+    """eta = 0, no force, pointwise mu(x)/rho(x): the leapfrog conserves
+    E^{n+1/2} exactly (to rounding); any index or coefficient slip breaks it."""
+    nx, ny, nz = 14, 12, 13
+    rng = np.random.default_rng(21)
+    mu = rng.uniform(1e3, 10e3, (nz, ny, nx))
+    rho = rng.uniform(1000, 1100, (nz, ny, nx))
+    dt = 0.5 * orc.stable_dt(mu, rho, 0.0, DX)
+    u0 = [rng.standard_normal((nz, ny, nx)) * 1e-6 for _ in range(3)]
+    um = [q * 0.97 for q in u0]
+    A = dt * dt * mu / rho
+    _, ua, uam = orc.run(nx, ny, nz, DX, dt, mu, rho, 0.0, 5, np.zeros((1, 3), np.int32),
+                         u_in=u0, uprev_in=um, want_state=True)
+    _, ub, ubm = orc.run(nx, ny, nz, DX, dt, mu, rho, 0.0, 137, np.zeros((1, 3), np.int32),
+                         u_in=u0, uprev_in=um, want_state=True)
+    ea = energy(ua, uam, A)
+    eb = energy(ub, ubm, A)
+    assert ea > 0
+    assert abs(eb - ea) < 1e-10 * abs(ea)
+    # with viscosity the same energy decays
+    _, uc, ucm = orc.run(nx, ny, nz, DX, 0.5 * orc.stable_dt(mu, rho, 0.5, DX), mu, rho, 0.5, 137,
+                         np.zeros((1, 3), np.int32), u_in=u0, uprev_in=um, want_state=True)
+    dtv = 0.5 * orc.stable_dt(mu, rho, 0.5, DX)
+    _, ud, udm = orc.run(nx, ny, nz, DX, dtv, mu, rho, 0.5, 5, np.zeros((1, 3), np.int32),
+                         u_in=u0, uprev_in=um, want_state=True)
+    Av = dtv * dtv * mu / rho
+    assert energy(uc, ucm, Av) < energy(ud, udm, Av)
+
+
+def test_stable_dt_reduces_to_paper_bound():
+    """Sec. 3.1: at eta = 0, dt_max = (1/c_s) (3/dx^2)^(-1/2)."""
+    for G in (1e3, 4e3, 50e3):
+        c = np.sqrt(G / 1000.0)
+        assert orc.stable_dt(G, 1000.0, 0.0, DX) == pytest.approx(DX / (c * np.sqrt(3)), rel=1e-14)
+    # config 1 of the plain method: dt = 0.5 dx / (c sqrt 3) = 28.868 us
+    assert 0.5 * orc.stable_dt(4e3, 1000.0, 0.0, DX) == pytest.approx(28.8675e-6, rel=1e-5)
+
+
+def _grows(dt, eta, n_steps=400):
+    nx = ny = nz = 16
+    rng = np.random.default_rng(2)
+    u0 = [rng.standard_normal((nz, ny, nx)) * 1e-6 for _ in range(3)]
+    _, u, _ = orc.run(nx, ny, nz, DX, dt, 4e3, 1000.0, eta, n_steps, np.zeros((1, 3), np.int32),
+                      u_in=u0, uprev_in=u0, want_state=True)
+    return np.abs(u).max() > 1e-3
+
+
+def test_stability_bound_separates_growth():
+    bound0 = orc.stable_dt(4e3, 1000.0, 0.0, DX)
+    assert not _grows(0.95 * bound0, 0.0)
+    assert _grows(1.05 * bound0, 0.0)
+    # with viscosity the eta = 0 bound is unstable; the viscous bound is not
+    boundv = orc.stable_dt(4e3, 1000.0, 1.5, DX)
+    assert boundv < 0.2 * bound0
+    assert _grows(0.9 * bound0, 1.5, 200)
+    assert not _grows(0.95 * boundv, 1.5, 2000)
+    assert _grows(1.1 * boundv, 1.5, 2000)
+
+
+def test_curl_source_symmetry():
+    """Sec. 4.1: the curl source drives motion in x-z with u_z odd in x."""
+    from paper_2607_28414_b300 import inputs
+    n = 25
+    v0 = inputs.curl_gaussian_velocity(n, n, n, DX, sigma=1e-3)
+    c = n // 2
+    sensors = np.array([[c + 4, c, c], [c - 4, c, c]], np.int32)
+    dt = 0.5 * orc.stable_dt(4e3, 1000.0, 0.0, DX)
+    tr = orc.run(n, n, n, DX, dt, 4e3, 1000.0, 0.0, 40, sensors, v0=v0)
+    assert np.abs(tr[:, 0, 2]).max() > 0
+    np.testing.assert_allclose(tr[:, 0, 2], -tr[:, 1, 2], atol=1e-12 * np.abs(tr).max())
+    np.testing.assert_allclose(tr[:, 0, 1], 0.0, atol=1e-20)
+
+
+def test_force_linearity_and_separable_envelope():
+    """Sec. 3.3: with f = b0 g(t), doubling b0 doubles the response, and the
+    envelope enters only through g(t_n)."""
+    from paper_2607_28414_b300 import inputs
+    n = 20
+    f = inputs.gaussian_push(n, n, n, DX, 1e3, 1e-3, 2e-3)
+    _, fs, _, _ = orc.project(*f, DX, tol=1e-12)
+    dt = 0.5 * orc.stable_dt(4e3, 1000.0, 0.3, DX)
+    g = inputs.push_envelope(30, dt, 5 * dt)
+    sensors = np.array([[n // 2 + 3, n // 2, n // 2]], np.int32)
+    t1 = orc.run(n, n, n, DX, dt, 4e3, 1000.0, 0.3, 30, sensors, fs=fs, g=g)
+    t2 = orc.run(n, n, n, DX, dt, 4e3, 1000.0, 0.3, 30, sensors, fs=[2 * a for a in fs], g=g)
+    t3 = orc.run(n, n, n, DX, dt, 4e3, 1000.0, 0.3, 30, sensors, fs=fs, g=2 * g)
+    np.testing.assert_allclose(t2, 2 * t1, rtol=1e-12, atol=1e-30)
+    np.testing.assert_allclose(t3, 2 * t1, rtol=1e-12, atol=1e-30)
+    assert g.sum() == 5  # t_n < 5 dt for n = 0..4
