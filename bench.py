@@ -1,0 +1,337 @@
+"""Benchmark of the reduced Kelvin-Voigt hot path on one B300 per rank.
+
+One bench step is one whole pass of the pre-computed-projection pipeline over
+the 256^3 heterogeneous workload (8 seeded spherical inclusions, speckled axial
+beam, dx = 0.2 mm, dt = 0.5 x the stability limit): fold the medium into the
+step coefficients, zero the state, project the force (CG to a true relative
+residual of 1e-8), run 2000 fused time steps with sensor recording and read
+the traces.
+
+value  = cell-updates of the pass (nx*ny*nz*2000) / pass time, in Gcell/s,
+         inputs resident on the device.
+e2e    = the same metric through the C ABI with host inputs (pinned host
+         medium and force, copied every pass) and the traces read back to the
+         host every pass.
+Also reported: step-only Gcell/s, projection ms and CG iterations, the roofline
+of the step kernel (the dominant kernel) against the measured HBM copy peak,
+the clocks seen during the timed region and the FP64 CPU oracle timed on a
+bounded sample (cpu_baseline).
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+Multi-GPU (torchrun): every rank runs its own replica (the path has no
+exchange step); value is the sum over ranks divided by the slowest rank's
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_TIME_STEPS = 2000
+GRID = 256
+STEP_BYTES_PER_CELL = 56  # (u, d) read + write 48 B, coefficients A', B' 8 B
+FORCE_BYTES_PER_CELL = 12  # projected force on force steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
+    ap.add_argument("--cg-tol", type=float, default=1e-8,
+                    help="projection tolerance (1e-8 is the workload's; larger values only for "
+                         "short profiling runs)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def workload(grid, n_steps):
+    from paper_2607_28414_b300 import inputs
+    return inputs.heterogeneous_inclusions(n=grid, n_steps=n_steps)
+
+
+def cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=6, n_sample_iters=6):
+    """Time the FP64 oracle on a bounded sample of the pass: n_sample_iters CG
+    iterations and n_sample_steps time steps of the same workload; the whole
+    pass is extrapolated with the GPU's CG iteration count."""
+    import oracle as orc
+    t0 = time.perf_counter()
+    phi, fs, status, st = orc.project(*w.force, w.dx, tol=1e-30, max_iter=n_sample_iters)
+    t_cg = (time.perf_counter() - t0) / max(1, st["iters"])
+    t0 = time.perf_counter()
+    orc.run(w.nx, w.ny, w.nz, w.dx, dt, w.G, w.rho, w.eta, n_sample_steps, w.sensors, fs=fs,
+            g=np.ones(n_sample_steps, np.float32))
+    t_step = (time.perf_counter() - t0) / n_sample_steps
+    total = cg_iters * t_cg + w.n_steps * t_step
+    value = w.n_cells * w.n_steps / total / 1e9
+    return value, {"cores": orc.get_threads(), "t_cg_iter_s": t_cg, "t_step_s": t_step,
+                   "sample": (f"{n_sample_iters} CG iterations + {n_sample_steps} time steps of the "
+                              f"{w.nx}^3 workload, extrapolated to {cg_iters} CG iterations + "
+                              f"{w.n_steps} steps")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2607_28414_b300 import inputs
+    import oracle as orc
+    w = workload(args.grid, args.time_steps)
+    dt = 0.5 * orc.stable_dt(w.G, w.rho, w.eta, w.dx)
+    cg_iters = 400
+    vals = []
+    for it in range(args.warmup + args.steps):
+        v, info = cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=2, n_sample_iters=2)
+        if it >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    ms = w.n_cells * w.n_steps / (value * 1e9) * 1e3
+    line = {"metric": "KV-FDTD Gcell-updates/s (projection + 2000 steps)", "value": value,
+            "unit": "Gcell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "time_steps": w.n_steps,
+                       "cg_tol": w.tol},
+            "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": info["cores"],
+                             "kind": "oracle", "sample": info["sample"] + " (CG iteration count "
+                             "fixed at 400 for the extrapolation)"},
+            "e2e": {"value": value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2607_28414_b300 import inputs, kv
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload(args.grid, args.time_steps)
+    w.tol = args.cg_tol
+    N = w.n_cells
+    stream = torch.cuda.Stream(device)  # a non-default stream shared by torch events and libkv
+    torch.cuda.set_stream(stream)
+    medium_d = [torch.from_numpy(a).to(device) for a in (w.G, w.rho, w.eta)]
+    force_d = [torch.from_numpy(a).to(device) for a in w.force]
+    dt = 0.5 * kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *medium_d)
+    h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, *medium_d, stream=stream.cuda_stream)
+    g = inputs.push_envelope(w.n_steps, dt, w.t_push)
+    n_force_steps = int(g.sum())
+    kv.kv_set_envelope(h, g)
+    kv.kv_set_sensors(h, w.sensors, w.n_steps)
+    traces_d = torch.zeros((w.n_steps, len(w.sensors), 3), dtype=torch.float32, device=device)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stats_last = {}
+
+    def one_pass(step_events=None, medium=medium_d, force=force_d, traces=traces_d):
+        kv.kv_set_medium(h, *medium)
+        kv.kv_reset(h)
+        st = kv.kv_project_force(h, *force, w.tol)
+        stats_last.update(st)
+        if step_events is not None:
+            step_events[0].record(stream)
+        kv.kv_step(h, w.n_steps)
+        if step_events is not None:
+            step_events[1].record(stream)
+        kv.kv_read_traces(h, traces)
+
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize(device)
+
+    # ---- timed region: inputs resident on the device ----
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(device)
+    clocks.start()
+    launches0 = kv.kv_launch_count(h)
+    e0, e1 = ev(), ev()
+    step_evs = [(ev(), ev()) for _ in range(args.steps)]
+    cg_iters, cg_ms = [], []
+    e0.record(stream)
+    for k in range(args.steps):
+        one_pass(step_evs[k])
+        cg_iters.append(stats_last["iters"])
+        cg_ms.append(stats_last["ms"])
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier()
+    clk = clocks.stop()
+    launches = kv.kv_launch_count(h) - launches0
+    t_total = e0.elapsed_time(e1) / 1e3
+    t_steps = sum(a.elapsed_time(b) for a, b in step_evs) / 1e3
+    t_max = t_total
+    if world > 1:
+        t = torch.tensor([t_total], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * N * w.n_steps * args.steps / t_max / 1e9
+    step_gcells = N * w.n_steps * args.steps / t_steps / 1e9
+    launch_s = t_steps / (w.n_steps * args.steps)
+    alg_bytes = (N * STEP_BYTES_PER_CELL * w.n_steps + N * FORCE_BYTES_PER_CELL * n_force_steps) \
+        / w.n_steps
+    achieved = alg_bytes / launch_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "kv_step_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            if tj.get("grid") == [w.nx, w.ny, w.nz]:
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        medium_h = [torch.from_numpy(a).pin_memory() for a in (w.G, w.rho, w.eta)]
+        force_h = [torch.from_numpy(a).pin_memory() for a in w.force]
+        traces_h = torch.zeros((w.n_steps, len(w.sensors), 3), dtype=torch.float32).pin_memory()
+        one_pass(None, medium_h, force_h, traces_h)
+        torch.cuda.synchronize(device)
+        barrier()
+        t0 = time.perf_counter()
+        f0, f1 = ev(), ev()
+        f0.record(stream)
+        for _ in range(args.steps):
+            one_pass(None, medium_h, force_h, traces_h)
+            _ = float(traces_h[-1, 0, 2])  # host reads the result
+        f1.record(stream)
+        torch.cuda.synchronize(device)
+        barrier()
+        t_e2e = max(f0.elapsed_time(f1) / 1e3, 1e-12)
+        if world > 1:
+            t = torch.tensor([t_e2e], device=device, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * N * w.n_steps * args.steps / t_e2e / 1e9,
+               "unit": "Gcell-updates/s", "h2d_bytes_per_step": 6 * N * 4,
+               "d2h_bytes_per_step": int(traces_h.numel() * 4),
+               "wall_s": time.perf_counter() - t0}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = cpu_oracle_sample(w, dt, int(np.median(cg_iters)))
+        cpu = {"value": v, "unit": "Gcell-updates/s", "cores": info["cores"], "kind": "oracle",
+               "sample": info["sample"]}
+
+    kv.kv_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": "KV-FDTD Gcell-updates/s (projection + 2000 steps)",
+            "value": value, "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "dx_m": w.dx,
+                       "time_steps": w.n_steps, "force_steps": n_force_steps, "cg_tol": w.tol,
+                       "medium": "8 seeded spherical inclusions (seed 102), speckled beam",
+                       "reductions": "f64", "parallelism": f"replicas{world}",
+                       "l2": "state 0.8 GB > 126 MB L2 (inputs larger than L2)"},
+            "kv_step_gcells": step_gcells,
+            "projection_ms": float(np.mean(cg_ms)), "cg_iters": int(np.median(cg_iters)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_step_tma", "peak_kind": peak_kind,
+                         "bytes_model": f"{STEP_BYTES_PER_CELL} B/cell + {FORCE_BYTES_PER_CELL} "
+                                        "B/cell on force steps"},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * kv.h -- C ABI of libkv: the B300 (sm_103a) hot path of the reduced
+ * Kelvin-Voigt shear-wave method (explicit FDTD time stepping of
+ * rho u_tt = mu lap(u) + eta lap(u_t) + f_S, with the body force projected
+ * onto its solenoidal part by a matrix-free conjugate-gradient Poisson solve).
+ *
+ * Paper: "A reduced viscoelastic FDTD formulation for ultrasound-driven shear
+ * wave propagation in soft tissue". Sections cited below:
+ *   Sec. 2.3 reduced shear equation (Eq. shear_reduced_kv)
+ *   Sec. 3.1 explicit leapfrog update, 7-point Laplacian, eta = 0 CFL bound
+ *   Sec. 3.2 solenoidal projection, masked CG (recurrences, stop rule, guards)
+ *   Sec. 3.3 pre-computed projection for separable forces f = b0(x) g(t)
+ *   Sec. 3.5 Dirichlet outer layer, curl-based initial velocity
+ *   Sec. 4   sensor traces (displacement at fixed nodes every step)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid      nx*ny*nz nodes at spacing dx on every axis, x fastest. A dense
+ *           field is nx*ny*nz contiguous values at index (k*ny + j)*nx + i.
+ *           The outer node layer is the Dirichlet layer (u = 0 there).
+ * Precision KV_FP32: state, coefficients and force in float; every inner
+ *           product and residual norm of the CG, and the potential phi, in
+ *           double. KV_FP64: everything in double (a check mode).
+ * Pointers  Inputs are described by kv_field: a scalar, a host pointer or a
+ *           device pointer (the current CUDA device). The caller owns every
+ *           pointer it passes; libkv copies what it needs into its own device
+ *           memory (allocated in kv_create, freed in kv_destroy) and never
+ *           keeps a caller pointer after a call returns.
+ * Streams   Every call is asynchronous on the handle's stream except those
+ *           documented as synchronising (kv_create, kv_set_medium,
+ *           kv_project_force, kv_read_*, kv_sync). Host inputs are copied
+ *           before the call returns, so the caller may reuse them.
+ * Errors    Every call returns a kv_status and never aborts. A CUDA error, a
+ *           device-side timeout or a non-finite CG puts the handle in an
+ *           error state; kv_last_error() gives a one-line description.
+ *           Asynchronous CUDA errors surface on the next synchronising call.
+ */
+#ifndef KV_H_
+#define KV_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KV_OK = 0,
+    KV_ERR_ARG = 1,          /* invalid argument (size, pointer, enum) */
+    KV_ERR_CUDA = 2,         /* a CUDA runtime or driver call failed */
+    KV_ERR_OOM = 3,          /* device allocation failed */
+    KV_ERR_UNSTABLE_DT = 4,  /* dt above the stability limit (kv_stable_dt) */
+    KV_ERR_NONFINITE = 5,    /* NaN/Inf in an input or in a CG residual */
+    KV_CG_BREAKDOWN = 6,     /* p.Ap non-finite or <= 0 (Sec. 3.2.3 guard) */
+    KV_CG_MAXITER = 7,       /* tolerance not met within max_iter iterations */
+    KV_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+    KV_ERR_STATE = 9,        /* call out of order or handle in an error state */
+    KV_ERR_UNSUPPORTED = 10  /* option not available in this build */
+} kv_status;
+
+typedef enum { KV_FP32 = 0, KV_FP64 = 1 } kv_precision;
+
+typedef enum { KV_SCALAR = 0, KV_HOST = 1, KV_DEVICE = 2 } kv_where;
+
+/* A scalar or a dense nx*ny*nz float field on the host or the device. */
+typedef struct {
+    const float *data; /* dense field (KV_HOST / KV_DEVICE), else ignored */
+    double value;      /* the value when where == KV_SCALAR */
+    int where;         /* kv_where */
+} kv_field;
+
+/* Statistics of one projection solve (Sec. 3.2.3). */
+typedef struct {
+    int iters;                /* CG iterations (all refinement cycles) */
+    int refinements;          /* true-residual evaluations after the first */
+    int status;               /* kv_status of the solve */
+    double rel_res_true;      /* ||b - A phi||_2 / ||b||_2, evaluated in FP64 */
+    double rel_res_recursive; /* last recursive ||r|| / ||b|| */
+    double ms;                /* wall time of the call */
+} kv_cg_stats;
+
+typedef struct kv_handle kv_handle;
+
+/*
+ * Stability limit of the explicit update (Sec. 3.1; extended to eta > 0).
+ * For frozen coefficients a Laplacian mode follows
+ *   c_{n+1} = (2 - (a+b) lam) c_n - (1 - b lam) c_{n-1},
+ * a = dt^2 G/rho, b = dt eta/rho, lam <= 12/dx^2, which is stable iff
+ * dt^2 c^2 + 2 dt nu <= dx^2/3 with c^2 = G/rho, nu = eta/rho. *dt_max gets the
+ * positive root minimised over nodes; at eta = 0 it is the paper's bound
+ * dt <= (1/c)(3/dx^2)^(-1/2). Synchronising. Fields as in kv_create.
+ */
+kv_status kv_stable_dt(int nx, int ny, int nz, double dx, kv_field G, kv_field rho,
+                       kv_field eta, double *dt_max);
+
+/*
+ * Create a solver for one grid (Sec. 3.1, 3.5). G (shear modulus mu, Pa),
+ * rho (kg/m^3), eta (Pa s) are scalars or dense fields; all three scalar gives
+ * the homogeneous kernels. dt must not exceed kv_stable_dt (else
+ * KV_ERR_UNSTABLE_DT). stream: a cudaStream_t, or NULL for a stream the
+ * handle creates and owns. Allocates all device memory the handle needs
+ * (state, coefficients, force, CG vectors). Synchronising.
+ */
+kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double dt, kv_field G,
+                    kv_field rho, kv_field eta, int precision, void *stream);
+
+/* Re-fold a new medium into an existing handle (Sec. 3.1 coefficients
+ * A = dt^2 G/rho, B = dt eta/rho, S = dt^2/rho). The homogeneous/heterogeneous
+ * choice must match kv_create's. Synchronising (it checks dt). */
+kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta);
+
+/* Temporal envelope g(t_n), n = 0..n-1 (Sec. 3.3, Eq. separable_force); g = 0
+ * beyond the table. g: float table on the host or device (where). */
+kv_status kv_set_envelope(kv_handle *h, const float *g, int n, int where);
+
+/* Sensors (Sec. 4): host array of n (i, j, k) node triples, every node inside
+ * the grid. capacity: steps of trace storage ([capacity][n][3] values).
+ * Resets the trace record. */
+kv_status kv_set_sensors(kv_handle *h, const int *ijk, int n, int capacity);
+
+/* Zero the displacement state, the step counter and the trace record. */
+kv_status kv_reset(kv_handle *h);
+
+/* Initial velocity v0 (Sec. 3.5 curl-based start): u^0 = 0, u^{-1} = -dt v0,
+ * applied on interior nodes. Resets the step counter and traces. */
+kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_field vz);
+
+/*
+ * Pre-computed solenoidal projection of a force pattern b0 (Sec. 3.2, 3.3):
+ *   b   = -(D- . b0) on interior nodes (backward differences),
+ *   A phi = b with A = -L (7-point), phi = 0 on the outer layer, by masked CG
+ *         from phi = 0, stopped when ||b - A phi|| / ||b|| < tol (true residual,
+ *         evaluated in FP64),
+ *   f_S0 = b0 - D+ phi (forward differences) on every node,
+ * and stores F = (dt^2/rho) f_S0 for the time step. fx, fy, fz: dense fields.
+ * max_iter <= 0 selects 20 * max(nx, ny, nz). mode: 0 = zero initial guess
+ * (other values are reserved, KV_ERR_UNSUPPORTED). fs_out: NULL, or a device
+ * pointer to 3*nx*ny*nz floats (component-major) that receives f_S0.
+ * stats: NULL or filled. Returns KV_OK, KV_CG_MAXITER, KV_CG_BREAKDOWN or
+ * KV_ERR_NONFINITE (the stats say which). A zero right-hand side gives
+ * phi = 0, f_S0 = b0 and 0 iterations. Synchronising.
+ */
+kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol,
+                           int max_iter, int mode, float *fs_out, kv_cg_stats *stats);
+
+/* Drop the projected force (the step then runs unforced). */
+kv_status kv_clear_force(kv_handle *h);
+
+/*
+ * Advance n time steps (Sec. 3.1 with Sec. 3.3's f_S^n = g(t_n) f_S0):
+ *   u^{n+1} = 2u^n - u^{n-1} + dt^2 [ (G/rho) L u^n + (eta/rho) L (u^n-u^{n-1})/dt
+ *                                     + g(t_n) f_S0 / rho ]
+ * on interior nodes, computed in the equivalent increment form
+ *   d^{n+1} = d^n + A' L^ u^n + B' L^ d^n + g_n F,  u^{n+1} = u^n + d^{n+1},
+ * d = u^n - u^{n-1}, L^ the unscaled 7-point stencil, A' = A/dx^2, B' = B/dx^2.
+ * After each step the sensors record u^{n+1}. Asynchronous.
+ */
+kv_status kv_step(kv_handle *h, int n);
+
+/* Steps taken since the last reset (host-side count). */
+long long kv_steps_taken(kv_handle *h);
+
+/* Copy the trace record [n_written][n_sensors][3] (float for KV_FP32, double
+ * for KV_FP64) to out (host or device per where). *n_written = steps recorded
+ * (at most the capacity). Synchronising. */
+kv_status kv_read_traces(kv_handle *h, void *out, int where, int *n_written);
+
+/*
+ * Copy one dense field out (element type as for traces; phi always double):
+ *   which 0: u^n component comp     which 1: d^n = u^n - u^{n-1}, component comp
+ *   which 2: phi (comp ignored)     which 3: F = dt^2 f_S0 / rho, component comp
+ * out: nx*ny*nz elements on the host or device (where). Synchronising.
+ */
+kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where);
+
+/* Wait for all work on the handle's stream; report device-side errors. */
+kv_status kv_sync(kv_handle *h);
+
+/* Kernel selection and tile shape of the FP32 step (autotuning and tests).
+ * variant 0: TMA-staged z-march kernel (default); 1: plain per-node kernel.
+ * tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in [64, 512],
+ * zc >= 1 planes per block. Values <= 0 keep the current choice. */
+kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc);
+
+/* Number of kernel launches libkv has issued on this handle. */
+long long kv_launch_count(kv_handle *h);
+
+kv_status kv_destroy(kv_handle *h);
+
+/* One-line description of the last error on h (or of the last failed
+ * kv_create when h is NULL). Never NULL. */
+const char *kv_last_error(kv_handle *h);
+
+/* Name of a status code. */
+const char *kv_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KV_H_ */

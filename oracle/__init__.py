@@ -55,7 +55,7 @@ def lib():
         L.or_project.restype = i
         L.or_run.argtypes = [i, i, i, d, d, dp, dp, dp, dp, dp, i, dp, dp, dp, i, ip, i, dp, dp, dp]
         L.or_run.restype = i
-        L.or_kv1d_run.argtypes = [i, d, d, d, d, d, d, d, i, ip, i, dp]
+        L.or_kv1d_run.argtypes = [i, d, d, d, d, d, d, d, d, i, ip, i, dp]
         L.or_kv1d_run.restype = i
         _LIB = L
         set_threads(int(os.environ.get("KV_ORACLE_THREADS", os.cpu_count() or 1)))
@@ -217,12 +217,13 @@ def run(nx, ny, nz, dx, dt, G, rho, eta, n_steps, sensors, fs=None, g=None, v0=N
     return traces
 
 
-def kv1d_run(n, dx, dt, mu, rho, eta, omega, amp, n_steps, sensors):
+def kv1d_run(n, dx, dt, mu, rho, eta, omega, amp, n_steps, sensors, t_ramp=0.0):
     """Sec. 4.3: 1D harmonic Kelvin-Voigt chain (same recurrence, 1D Laplacian),
-    driven by u_0 = amp sin(omega t). Returns rec[n_steps, ns] (entry s = u^{s+1})."""
+    driven by u_0 = amp r(t) sin(omega t), r a raised-cosine ramp over t_ramp.
+    Returns rec[n_steps, ns] (entry s = u^{s+1})."""
     sensors = np.ascontiguousarray(np.asarray(sensors, np.int32))
     rec, rp = _d(np.zeros((n_steps, len(sensors))))
-    lib().or_kv1d_run(int(n), dx, dt, mu, rho, eta, omega, amp, int(n_steps),
+    lib().or_kv1d_run(int(n), dx, dt, mu, rho, eta, omega, amp, float(t_ramp), int(n_steps),
                       sensors.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(sensors), rp)
     return rec
 

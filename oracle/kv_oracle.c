@@ -351,13 +351,14 @@ int or_run(int nx, int ny, int nz, double dx, double dt, const double *mu, const
 
 /*
  * 1D restriction of the same recurrence (Sec. 4.3 harmonic benchmark): a chain
- * of n nodes, u_0^n = amp sin(omega t_n) driven (Dirichlet), u_{n-1} = 0,
+ * of n nodes, u_0^n = amp r(t_n) sin(omega t_n) driven (Dirichlet), u_{n-1} = 0,
+ * r(t) = (1 - cos(pi t / t_ramp)) / 2 for t < t_ramp, else 1 (t_ramp <= 0: r = 1),
  *   u_i^{n+1} = 2u_i^n - u_i^{n-1}
  *             + dt^2 [ (mu/rho) D2 u^n + (eta/rho) D2 (u^n - u^{n-1})/dt ]_i.
  * Records u at the sensor nodes for every step: rec[step][s] holds u^{step+1}.
  */
 int or_kv1d_run(int n, double dx, double dt, double mu, double rho, double eta, double omega,
-                double amp, int n_steps, const int *sensors, int ns, double *rec)
+                double amp, double t_ramp, int n_steps, const int *sensors, int ns, double *rec)
 {
     double *um = (double *)calloc(n, sizeof(double));
     double *u0 = (double *)calloc(n, sizeof(double));
@@ -377,7 +378,9 @@ int or_kv1d_run(int n, double dx, double dt, double mu, double rho, double eta, 
             double a = (mu / rho) * lu + (eta / rho) * lw;
             up[i] = 2.0 * u0[i] - um[i] + dt * dt * a;
         }
-        up[0] = amp * sin(omega * (double)(s + 1) * dt);
+        const double tn = (double)(s + 1) * dt;
+        const double ramp = (t_ramp > 0.0 && tn < t_ramp) ? 0.5 * (1.0 - cos(M_PI * tn / t_ramp)) : 1.0;
+        up[0] = amp * ramp * sin(omega * tn);
         up[n - 1] = 0.0;
         for (int q = 0; q < ns; ++q) rec[(size_t)s * ns + q] = up[sensors[q]];
         double *t = um;

@@ -1,0 +1,528 @@
+// kv_api.cu -- the extern "C" boundary of libkv (declared in include/kv.h).
+// Argument checking, device memory ownership, staging of caller fields into
+// the pitched device layout, the step loop (CUDA graph for blocks of steps)
+// and the synchronising reads.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kv_internal.cuh"
+
+static thread_local char g_create_err[512] = "";
+
+namespace kv {
+
+kv_status set_error(kv_handle *h, kv_status st, const char *fmt, ...) {
+    char *buf = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+kv_status cuda_check(kv_handle *h, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return KV_OK;
+    if (h) h->sticky = 1;
+    return set_error(h, e == cudaErrorMemoryAllocation ? KV_ERR_OOM : KV_ERR_CUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+kv_status launch_fold(kv_handle *h, const float *G, double Gs, const float *rho, double rhos,
+                      const float *eta, double etas);
+kv_status launch_init_velocity(kv_handle *h, const float *v_pitched);
+
+}  // namespace kv
+
+using namespace kv;
+
+namespace {
+
+bool field_ok(const kv_field &f) {
+    if (f.where == KV_SCALAR) return isfinite(f.value);
+    if (f.where == KV_HOST || f.where == KV_DEVICE) return f.data != nullptr;
+    return false;
+}
+
+// Copy a dense caller field into a pitched float plane of the handle.
+kv_status stage(kv_handle *h, const kv_field &f, float *dst) {
+    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)h->px * 4, f.data, (size_t)h->nx * 4,
+                                      (size_t)h->nx * 4, (size_t)h->ny * h->nz, cudaMemcpyDefault,
+                                      h->stream);
+    return cuda_check(h, e, "copy of an input field");
+}
+
+// Host-side stability limit over host arrays or scalars (same formula as the
+// device reduction: dt <= h^2 / (nu + sqrt(nu^2 + c^2 h^2)), h^2 = dx^2 / 3).
+double dt_limit_node(double g, double r, double e, double dx) {
+    const double h2 = dx * dx / 3.0;
+    if (!(r > 0.0) || g < 0.0 || e < 0.0 || !isfinite(g) || !isfinite(r) || !isfinite(e))
+        return -1.0;
+    const double c2 = g / r, nu = e / r;
+    const double den = nu + sqrt(nu * nu + c2 * h2);
+    return den > 0.0 ? h2 / den : INFINITY;
+}
+
+kv_status stable_dt_impl(kv_handle *h, int nx, int ny, int nz, double dx, const kv_field &G,
+                         const kv_field &rho, const kv_field &eta, double *out) {
+    const kv_field *fs[3] = {&G, &rho, &eta};
+    int n_host = 0, n_dev = 0;
+    for (auto *f : fs) {
+        if (!field_ok(*f)) return set_error(h, KV_ERR_ARG, "invalid medium field");
+        n_host += f->where == KV_HOST;
+        n_dev += f->where == KV_DEVICE;
+    }
+    if (n_host && n_dev)
+        return set_error(h, KV_ERR_ARG, "medium arrays must all be on the host or all on the device");
+    const long long n = (long long)nx * ny * nz;
+    double m;
+    if (n_dev) {
+        kv_status st = stable_dt_device(h ? h->stream : 0, h ? h->dtmin : nullptr, (int)n, dx,
+                                        G.where == KV_DEVICE ? G.data : nullptr, G.value,
+                                        rho.where == KV_DEVICE ? rho.data : nullptr, rho.value,
+                                        eta.where == KV_DEVICE ? eta.data : nullptr, eta.value, &m);
+        if (st != KV_OK) return set_error(h, st, "device stability reduction failed");
+    } else if (n_host) {
+        m = INFINITY;
+        for (long long c = 0; c < n; ++c) {
+            const double g = G.where == KV_HOST ? G.data[c] : G.value;
+            const double r = rho.where == KV_HOST ? rho.data[c] : rho.value;
+            const double e = eta.where == KV_HOST ? eta.data[c] : eta.value;
+            m = fmin(m, dt_limit_node(g, r, e, dx));
+        }
+    } else {
+        m = dt_limit_node(G.value, rho.value, eta.value, dx);
+    }
+    if (m < 0.0) return set_error(h, KV_ERR_ARG, "medium has rho <= 0, G < 0, eta < 0 or non-finite values");
+    *out = m;
+    return KV_OK;
+}
+
+void free_graphs(kv_handle *h) {
+    for (int b = 0; b < 2; ++b)
+        if (h->graph[b]) {
+            cudaGraphExecDestroy(h->graph[b]);
+            h->graph[b] = nullptr;
+        }
+}
+
+kv_status poll_flags(kv_handle *h) {
+    long long flags = 0;
+    cudaError_t e = cudaMemcpyAsync(&flags, h->ctrl + kErrFlags, sizeof(flags),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_check(h, e, "synchronise");
+    if (flags & 1) {
+        h->sticky = 1;
+        return set_error(h, KV_ERR_TIMEOUT, "a bounded device wait timed out in the step kernel");
+    }
+    return KV_OK;
+}
+
+kv_status fold(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_field &eta) {
+    if (!h->het) {
+        h->A_s = h->dt * h->dt * G.value / rho.value / (h->dx * h->dx);
+        h->B_s = h->dt * eta.value / rho.value / (h->dx * h->dx);
+        h->S_s = h->dt * h->dt / rho.value;
+        return KV_OK;
+    }
+    const kv_field *fs[3] = {&G, &rho, &eta};
+    const float *ptr[3];
+    for (int q = 0; q < 3; ++q) {
+        ptr[q] = nullptr;
+        if (fs[q]->where != KV_SCALAR) {
+            kv_status st = stage(h, *fs[q], h->fstage + q * h->Np);
+            if (st != KV_OK) return st;
+            ptr[q] = h->fstage + q * h->Np;
+        }
+    }
+    kv_status st = launch_fold(h, ptr[0], G.value, ptr[1], rho.value, ptr[2], eta.value);
+    if (st != KV_OK) return st;
+    return cuda_check(h, cudaStreamSynchronize(h->stream), "medium fold");
+}
+
+template <typename P>
+kv_status dalloc(kv_handle *h, P **p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_check(h, e, "cudaMalloc");
+    }
+    return KV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kv_status_string(int s) {
+    switch (s) {
+        case KV_OK: return "KV_OK";
+        case KV_ERR_ARG: return "KV_ERR_ARG";
+        case KV_ERR_CUDA: return "KV_ERR_CUDA";
+        case KV_ERR_OOM: return "KV_ERR_OOM";
+        case KV_ERR_UNSTABLE_DT: return "KV_ERR_UNSTABLE_DT";
+        case KV_ERR_NONFINITE: return "KV_ERR_NONFINITE";
+        case KV_CG_BREAKDOWN: return "KV_CG_BREAKDOWN";
+        case KV_CG_MAXITER: return "KV_CG_MAXITER";
+        case KV_ERR_TIMEOUT: return "KV_ERR_TIMEOUT";
+        case KV_ERR_STATE: return "KV_ERR_STATE";
+        case KV_ERR_UNSUPPORTED: return "KV_ERR_UNSUPPORTED";
+        default: return "KV_UNKNOWN";
+    }
+}
+
+const char *kv_last_error(kv_handle *h) { return h ? h->err : g_create_err; }
+
+kv_status kv_stable_dt(int nx, int ny, int nz, double dx, kv_field G, kv_field rho, kv_field eta,
+                       double *dt_max) {
+    if (nx < 3 || ny < 3 || nz < 3 || !(dx > 0.0) || !dt_max)
+        return set_error(nullptr, KV_ERR_ARG, "kv_stable_dt: invalid grid, dx or output pointer");
+    return stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, dt_max);
+}
+
+kv_status kv_destroy(kv_handle *h) {
+    if (!h) return KV_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_graphs(h);
+    void *dev[] = {h->state[0], h->state[1], h->F, h->coef, h->S, h->g_dev, h->sens_dev,
+                   h->traces, h->ctrl, h->r, h->p[0], h->p[1], h->e, h->phi, h->b, h->scal,
+                   h->partials, h->fstage, h->dtmin};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
+    if (h->scal_host) cudaFreeHost(h->scal_host);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    free(h);
+    return KV_OK;
+}
+
+kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double dt, kv_field G,
+                    kv_field rho, kv_field eta, int precision, void *stream) {
+    if (!out) return set_error(nullptr, KV_ERR_ARG, "kv_create: out is NULL");
+    *out = nullptr;
+    if (nx < 3 || ny < 3 || nz < 3 || !(dx > 0.0) || !(dt > 0.0) ||
+        (precision != KV_FP32 && precision != KV_FP64))
+        return set_error(nullptr, KV_ERR_ARG, "kv_create: invalid grid %dx%dx%d, dx, dt or precision",
+                         nx, ny, nz);
+    const long long px = round_up(nx, kPitchAlign);
+    if (px * ny * (long long)nz > (1ll << 31) - 1)
+        return set_error(nullptr, KV_ERR_ARG, "kv_create: grid too large (more than 2^31 padded nodes)");
+    double dt_max;
+    kv_status st = stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, &dt_max);
+    if (st != KV_OK) return st;
+    if (dt > dt_max * (1.0 + 1e-12))
+        return set_error(nullptr, KV_ERR_UNSTABLE_DT,
+                         "dt = %.6e s exceeds the stability limit %.6e s", dt, dt_max);
+
+    kv_handle *h = (kv_handle *)calloc(1, sizeof(kv_handle));
+    if (!h) return set_error(nullptr, KV_ERR_OOM, "kv_create: host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->px = (int)px;
+    h->Np = px * ny * nz;
+    h->dx = dx;
+    h->dt = dt;
+    h->dt_max = dt_max;
+    h->precision = precision;
+    h->esize = precision == KV_FP64 ? 8 : 4;
+    h->het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
+    h->variant = 0;
+    h->tx = 64;
+    h->ty = 8;
+    h->zc = 32;
+    h->graph_steps = 32;
+    cudaGetDevice(&h->device);
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        if ((st = cuda_check(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking),
+                             "cudaStreamCreate")) != KV_OK)
+            goto fail;
+        h->own_stream = 1;
+    }
+    {
+        const size_t Np = (size_t)h->Np, es = h->esize;
+        const dim3 g((nx + 31) / 32, (ny + 7) / 8, (nz + 7) / 8);
+        h->partials_len = 2 * g.x * g.y * g.z;
+        if ((st = dalloc(h, &h->state[0], 6 * Np * es)) || (st = dalloc(h, &h->state[1], 6 * Np * es)) ||
+            (st = dalloc(h, &h->F, 3 * Np * es)) || (st = dalloc(h, &h->fstage, 3 * Np * 4)) ||
+            (st = dalloc(h, &h->r, Np * es)) || (st = dalloc(h, &h->p[0], Np * es)) ||
+            (st = dalloc(h, &h->p[1], Np * es)) || (st = dalloc(h, &h->e, Np * es)) || (st = dalloc(h, &h->phi, Np * 8)) ||
+            (st = dalloc(h, &h->b, Np * 8)) || (st = dalloc(h, &h->ctrl, kCtrlWords * 8)) ||
+            (st = dalloc(h, &h->scal, kCgScalars * 8)) ||
+            (st = dalloc(h, &h->partials, (size_t)h->partials_len * 8)) ||
+            (st = dalloc(h, &h->dtmin, kDtBlocks * 8)))
+            goto fail;
+        if (h->het && ((st = dalloc(h, &h->coef, 2 * Np * es)) || (st = dalloc(h, &h->S, Np * es))))
+            goto fail;
+        if ((st = cuda_check(h, cudaMallocHost((void **)&h->ctrl_host, kCtrlWords * 8), "cudaMallocHost")) ||
+            (st = cuda_check(h, cudaMallocHost((void **)&h->scal_host, kCgScalars * 8), "cudaMallocHost")))
+            goto fail;
+        cudaError_t e = cudaSuccess;
+        void *zero[] = {h->state[0], h->state[1], h->F, h->fstage, h->r, h->p[0], h->p[1], h->e,
+                        h->phi, h->b};
+        size_t zbytes[] = {6 * Np * es, 6 * Np * es, 3 * Np * es, 3 * Np * 4, Np * es, Np * es, Np * es,
+                           Np * es, Np * 8, Np * 8};
+        for (int q = 0; q < 10 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zero[q], 0, zbytes[q], h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, kCtrlWords * 8, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, kCgScalars * 8, h->stream);
+        if (e == cudaSuccess && h->het) e = cudaMemsetAsync(h->coef, 0, 2 * Np * es, h->stream);
+        if (e == cudaSuccess && h->het) e = cudaMemsetAsync(h->S, 0, Np * es, h->stream);
+        if ((st = cuda_check(h, e, "initial memset")) != KV_OK) goto fail;
+    }
+    if ((st = fold(h, G, rho, eta)) != KV_OK) goto fail;
+    if ((st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_create")) != KV_OK) goto fail;
+    *out = h;
+    return KV_OK;
+fail:
+    snprintf(g_create_err, sizeof(g_create_err), "%s", h->err);
+    kv_destroy(h);
+    return st;
+}
+
+kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    const int het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
+    if (het != h->het)
+        return set_error(h, KV_ERR_ARG, "kv_set_medium: homogeneous/heterogeneous kind differs from kv_create");
+    double dt_max;
+    kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_medium");
+    if (st != KV_OK) return st;
+    if ((st = stable_dt_impl(h, h->nx, h->ny, h->nz, h->dx, G, rho, eta, &dt_max)) != KV_OK) return st;
+    if (h->dt > dt_max * (1.0 + 1e-12))
+        return set_error(h, KV_ERR_UNSTABLE_DT, "dt = %.6e s exceeds the stability limit %.6e s", h->dt,
+                         dt_max);
+    h->dt_max = dt_max;
+    free_graphs(h);
+    return fold(h, G, rho, eta);
+}
+
+kv_status kv_set_envelope(kv_handle *h, const float *g, int n, int where) {
+    if (!h || n < 0 || (n > 0 && !g) || (where != KV_HOST && where != KV_DEVICE))
+        return set_error(h, KV_ERR_ARG, "kv_set_envelope: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    if (n > h->n_g || !h->g_dev) {
+        if (h->g_dev) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->g_dev);
+            h->g_dev = nullptr;
+        }
+        kv_status st = dalloc(h, &h->g_dev, (size_t)std::max(n, 1) * 4);
+        if (st != KV_OK) return st;
+    }
+    h->n_g = n;
+    free_graphs(h);
+    if (n == 0) return KV_OK;
+    kv_status st = cuda_check(
+        h, cudaMemcpyAsync(h->g_dev, g, (size_t)n * 4, cudaMemcpyDefault, h->stream), "envelope copy");
+    if (st == KV_OK && where == KV_HOST)
+        st = cuda_check(h, cudaStreamSynchronize(h->stream), "envelope copy");
+    return st;
+}
+
+kv_status kv_set_sensors(kv_handle *h, const int *ijk, int n, int capacity) {
+    if (!h || n < 0 || capacity < 0 || (n > 0 && !ijk))
+        return set_error(h, KV_ERR_ARG, "kv_set_sensors: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    for (int s = 0; s < n; ++s) {
+        const int i = ijk[3 * s], j = ijk[3 * s + 1], k = ijk[3 * s + 2];
+        if (i < 0 || i >= h->nx || j < 0 || j >= h->ny || k < 0 || k >= h->nz)
+            return set_error(h, KV_ERR_ARG, "sensor %d at (%d,%d,%d) is outside the grid", s, i, j, k);
+    }
+    cudaStreamSynchronize(h->stream);
+    if (h->sens_dev) cudaFree(h->sens_dev);
+    if (h->traces) cudaFree(h->traces);
+    h->sens_dev = nullptr;
+    h->traces = nullptr;
+    h->ns = 0;
+    h->cap = 0;
+    free_graphs(h);
+    if (n == 0 || capacity == 0) return KV_OK;
+    kv_status st;
+    if ((st = dalloc(h, &h->sens_dev, (size_t)n * 3 * 4)) != KV_OK) return st;
+    if ((st = dalloc(h, &h->traces, (size_t)capacity * n * 3 * h->esize)) != KV_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h->sens_dev, ijk, (size_t)n * 3 * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->traces, 0, (size_t)capacity * n * 3 * h->esize, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if ((st = cuda_check(h, e, "kv_set_sensors")) != KV_OK) return st;
+    h->ns = n;
+    h->cap = capacity;
+    return KV_OK;
+}
+
+kv_status kv_reset(kv_handle *h) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    const size_t bytes = 6 * (size_t)h->Np * h->esize;
+    cudaError_t e = cudaMemsetAsync(h->state[0], 0, bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->state[1], 0, bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, 3 * sizeof(long long), h->stream);
+    if (e == cudaSuccess && h->traces)
+        e = cudaMemsetAsync(h->traces, 0, (size_t)h->cap * h->ns * 3 * h->esize, h->stream);
+    h->cur = 0;
+    h->steps_host = 0;
+    return cuda_check(h, e, "kv_reset");
+}
+
+kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_field vz) {
+    if (!h) return KV_ERR_ARG;
+    const kv_field *v[3] = {&vx, &vy, &vz};
+    for (auto *f : v)
+        if (!field_ok(*f) || (f->where == KV_SCALAR && f->value != 0.0))
+            return set_error(h, KV_ERR_ARG, "initial velocity components must be arrays or 0");
+    kv_status st = kv_reset(h);
+    if (st != KV_OK) return st;
+    cudaError_t e = cudaMemsetAsync(h->fstage, 0, 3 * (size_t)h->Np * 4, h->stream);
+    if ((st = cuda_check(h, e, "kv_set_initial_velocity")) != KV_OK) return st;
+    for (int q = 0; q < 3; ++q)
+        if (v[q]->where != KV_SCALAR && (st = stage(h, *v[q], h->fstage + q * h->Np)) != KV_OK) return st;
+    if ((st = launch_init_velocity(h, h->fstage)) != KV_OK) return st;
+    return cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_initial_velocity");
+}
+
+kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol,
+                           int max_iter, int mode, float *fs_out, kv_cg_stats *stats) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    if (mode != 0) return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
+    if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");
+    const kv_field *f[3] = {&fx, &fy, &fz};
+    for (auto *q : f)
+        if (!field_ok(*q) || (q->where == KV_SCALAR && q->value != 0.0))
+            return set_error(h, KV_ERR_ARG, "force components must be arrays or 0");
+    if (max_iter <= 0) max_iter = 20 * std::max(h->nx, std::max(h->ny, h->nz));
+    kv_status st = cuda_check(h, cudaMemsetAsync(h->fstage, 0, 3 * (size_t)h->Np * 4, h->stream),
+                              "kv_project_force");
+    if (st != KV_OK) return st;
+    for (int q = 0; q < 3; ++q)
+        if (f[q]->where != KV_SCALAR && (st = stage(h, *f[q], h->fstage + q * h->Np)) != KV_OK) return st;
+    free_graphs(h);
+    h->have_force = 0;
+    return project(h, tol, max_iter, fs_out, stats);
+}
+
+kv_status kv_clear_force(kv_handle *h) {
+    if (!h) return KV_ERR_ARG;
+    h->have_force = 0;
+    free_graphs(h);
+    return KV_OK;
+}
+
+kv_status kv_step(kv_handle *h, int n) {
+    if (!h || n < 0) return set_error(h, KV_ERR_ARG, "kv_step: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    kv_status st;
+    const int G = h->graph_steps;
+    if (n >= G && G > 0 && (G % 2) == 0) {
+        if (!h->graph[h->cur]) {
+            if (h->precision == KV_FP32 && h->variant == 0 && !h->tma_ready &&
+                (st = step_prepare(h)) != KV_OK)
+                return st;
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+            if ((st = cuda_check(h, e, "graph capture")) != KV_OK) return st;
+            const long long before = h->launches;
+            for (int i = 0; i < G; ++i) {
+                st = step_launch(h, (h->cur + i) & 1);
+                if (st != KV_OK) break;
+            }
+            h->launches = before;
+            e = cudaStreamEndCapture(h->stream, &graph);
+            if (st != KV_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if ((st = cuda_check(h, e, "graph capture")) != KV_OK) return st;
+            e = cudaGraphInstantiate(&h->graph[h->cur], graph, 0);
+            cudaGraphDestroy(graph);
+            if ((st = cuda_check(h, e, "graph instantiate")) != KV_OK) return st;
+        }
+        while (n >= G) {
+            if ((st = cuda_check(h, cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch")) != KV_OK)
+                return st;
+            h->launches += G;
+            h->steps_host += G;
+            n -= G;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        if ((st = step_launch(h, h->cur)) != KV_OK) return st;
+        h->cur = 1 - h->cur;
+        h->steps_host++;
+    }
+    return KV_OK;
+}
+
+long long kv_steps_taken(kv_handle *h) { return h ? h->steps_host : 0; }
+
+long long kv_launch_count(kv_handle *h) { return h ? h->launches : 0; }
+
+kv_status kv_sync(kv_handle *h) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    return poll_flags(h);
+}
+
+kv_status kv_read_traces(kv_handle *h, void *out, int where, int *n_written) {
+    if (!h || (where != KV_HOST && where != KV_DEVICE))
+        return set_error(h, KV_ERR_ARG, "kv_read_traces: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    kv_status st = poll_flags(h);
+    if (st != KV_OK) return st;
+    const long long n = std::min<long long>(h->steps_host, h->cap);
+    if (n_written) *n_written = (int)n;
+    if (n == 0 || h->ns == 0) return KV_OK;
+    if (!out) return set_error(h, KV_ERR_ARG, "kv_read_traces: out is NULL");
+    cudaError_t e = cudaMemcpyAsync(out, h->traces, (size_t)n * h->ns * 3 * h->esize, cudaMemcpyDefault,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_check(h, e, "kv_read_traces");
+}
+
+kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where) {
+    if (!h || !out || which < 0 || which > 3 || (which != 2 && (comp < 0 || comp > 2)) ||
+        (where != KV_HOST && where != KV_DEVICE))
+        return set_error(h, KV_ERR_ARG, "kv_read_field: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    kv_status st = poll_flags(h);
+    if (st != KV_OK) return st;
+    const char *src;
+    size_t es = h->esize;
+    if (which == 0) src = (const char *)h->state[h->cur] + (size_t)comp * h->Np * es;
+    else if (which == 1) src = (const char *)h->state[h->cur] + (size_t)(3 + comp) * h->Np * es;
+    else if (which == 2) { src = (const char *)h->phi; es = 8; }
+    else src = (const char *)h->F + (size_t)comp * h->Np * es;
+    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)h->nx * es, src, (size_t)h->px * es, (size_t)h->nx * es,
+                                      (size_t)h->ny * h->nz, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_check(h, e, "kv_read_field");
+}
+
+kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc) {
+    if (!h) return KV_ERR_ARG;
+    if (variant > 1 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
+        (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 16))
+        return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant or tile");
+    const int ntx = tx > 0 ? tx : h->tx, nty = ty > 0 ? ty : h->ty;
+    if (ntx * nty / 4 < 64 || ntx * nty / 4 > 512)
+        return set_error(h, KV_ERR_ARG, "kv_set_step_config: tile %dx%d out of range", ntx, nty);
+    cudaStreamSynchronize(h->stream);
+    if (variant >= 0) h->variant = variant;
+    h->tx = ntx;
+    h->ty = nty;
+    if (zc > 0) h->zc = zc;
+    h->tma_ready = 0;
+    free_graphs(h);
+    if (h->precision == KV_FP32 && h->variant == 0) return step_prepare(h);
+    return KV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,512 @@
+// kv_cg.cu -- pre-computed solenoidal projection (Sec. 3.2, 3.3).
+//
+//   b    = -(D- . f) on interior nodes (backward differences), ||b||^2 in FP64
+//   A phi = b, A = -L (7-point, phi = 0 on the outer layer), masked CG
+//   f_S0 = f - D+ phi on every node;  F = (dt^2/rho) f_S0 for the time step
+//
+// Precision (KV_FP32). The CG vectors r, p and the running correction e are
+// float; the potential phi and the right-hand side b are double. Every inner
+// product and residual norm is accumulated with FP64-class precision: per
+// thread in float-float (error-free products and sums on the FP32 pipes, whose
+// rate on B300 is many times the FP64 rate), then in double across threads
+// and blocks. The solution is updated in groups and the residual is replaced
+// by the true one ("reliable updates"): the FP32 iterations accumulate
+// e += alpha p; whenever the recursive ||r|| has dropped by kReplace since the
+// last replacement (or below tol/2 relative to ||b||, or at max_iter), a
+// replacement folds phi += e in double, recomputes r = b - A phi in double and
+// tests the true relative residual against tol. The search direction p is
+// kept across replacements, so CG does not restart. KV_FP64 runs the same
+// kernels with double vectors and plain double accumulation (no intermediate
+// replacements).
+//
+// One CG iteration is two fused stencil passes:
+//   pass 1: p' = r + beta p at each node and its six neighbours, Ap' on the
+//           fly, p'.Ap' reduced; p' stored (ping-pong buffer). -> alpha
+//   pass 2: Ap' recomputed from p', e += alpha p', r -= alpha Ap', r.r
+//           reduced. -> beta, replacement and stop tests
+// Both passes march z per thread column with the z neighbours in registers.
+// Each reduction ends in the last block to finish (ticket), which sums the
+// per-block partials in a fixed order and updates the device scalars, so the
+// host only polls the control word every few iterations.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "kv_internal.cuh"
+
+namespace kv {
+
+constexpr int kCgBX = 32, kCgBY = 8;  // block of one CG pass: 32 x 8 columns, zc planes
+constexpr double kReplace = 1e-2;     // residual replacement after each 100x drop of ||r||
+
+__device__ __forceinline__ bool is_interior(int i, int j, int k, int nx, int ny, int nz) {
+    return i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+}
+
+// ---------------------------------------------------------------------------
+// Accumulators: float-float for float vectors, double for double vectors.
+// ---------------------------------------------------------------------------
+struct AccFF {
+    float hi = 0.f, lo = 0.f;
+    // acc += x * y with the product and the sum formed exactly (TwoProd by FMA,
+    // TwoSum), then renormalised.
+    __device__ __forceinline__ void add_prod(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        const float pe = __fmaf_rn(x, y, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        const float t = __fadd_rn(__fadd_rn(e, pe), lo);
+        hi = __fadd_rn(s, t);
+        lo = __fsub_rn(t, __fsub_rn(hi, s));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+struct AccD {
+    double v = 0.0;
+    __device__ __forceinline__ void add_prod(double x, double y) { v = __fma_rn(x, y, v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = AccFF; };
+template <> struct AccOf<double> { using type = AccD; };
+
+// Last-block finisher: returns true in the block that finished last; sums[q]
+// then holds the deterministic grand total of partial slot q.
+template <int NQ>
+__device__ __forceinline__ bool last_block_sums(const CgParams &p, const double (&v)[NQ],
+                                                double (&sums)[NQ]) {
+    __shared__ double sh[33];
+    __shared__ int s_last;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int tid = threadIdx.x;
+    for (int q = 0; q < NQ; ++q) {
+        double t = block_sum_d(v[q], sh);
+        if (tid == 0) p.partials[(size_t)q * p.nblocks + bid] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long t =
+            atomicAdd(reinterpret_cast<unsigned long long *>(&p.ctrl[kCgTicket]), 1ull);
+        s_last = (t == (unsigned long long)(p.nblocks - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int q = 0; q < NQ; ++q) {
+        double acc = 0.0;
+        for (int b = tid; b < p.nblocks; b += blockDim.x)
+            acc += __ldcg(&p.partials[(size_t)q * p.nblocks + b]);
+        sums[q] = block_sum_d(acc, sh);
+    }
+    if (tid == 0) p.ctrl[kCgTicket] = 0;
+    return true;
+}
+
+// The CG kernels use 1D blocks of kCgBX*kCgBY threads mapped to (x, y) columns.
+__device__ __forceinline__ void node_of(int &i, int &j) {
+    i = blockIdx.x * kCgBX + (threadIdx.x % kCgBX);
+    j = blockIdx.y * kCgBY + (threadIdx.x / kCgBX);
+}
+
+// b = -(D- . f) on interior nodes, ||b||^2.
+__global__ void __launch_bounds__(kCgBX *kCgBY)
+k_rhs(const float *__restrict__ f, double *__restrict__ b, CgParams p) {
+    int i, j;
+    node_of(i, j);
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz);
+    double acc = 0.0;
+    if (i < p.nx && j < p.ny) {
+        for (int k = k0; k < k1; ++k) {
+            const long long c = k * sz + j * sy + i;
+            double v = 0.0;
+            if (is_interior(i, j, k, p.nx, p.ny, p.nz)) {
+                const float *fx = f, *fy = f + p.Np, *fz = f + 2 * p.Np;
+                const double d = ((double)fx[c] - (double)fx[c - 1]) +
+                                 ((double)fy[c] - (double)fy[c - sy]) +
+                                 ((double)fz[c] - (double)fz[c - sz]);
+                v = -(d * p.inv_dx);
+            }
+            b[c] = v;
+            acc += v * v;
+        }
+    }
+    double v1[1] = {acc}, s[1];
+    if (last_block_sums<1>(p, v1, s) && threadIdx.x == 0) p.scal[kBB] = s[0];
+}
+
+// Group update of the solution: phi += e (double), e = 0. Elementwise.
+template <typename T>
+__global__ void k_fold_e(double *__restrict__ phi, T *__restrict__ e, long long Np, CgParams p) {
+    if (__ldcg(&p.ctrl[kCgStatus]) != kCgNeedTrue) return;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < Np;
+         c += (long long)gridDim.x * blockDim.x) {
+        const T ev = e[c];
+        if (ev != T(0)) {
+            phi[c] += (double)ev;
+            e[c] = T(0);
+        }
+    }
+}
+
+// Residual replacement: r = b - A phi (FP64), stored as T; tests the true
+// residual; on continuation keeps p and sets beta from the replaced residual.
+template <typename T>
+__global__ void __launch_bounds__(kCgBX *kCgBY)
+k_true_res(const double *__restrict__ b, const double *__restrict__ phi, T *__restrict__ r,
+           CgParams p) {
+    if (__ldcg(&p.ctrl[kCgStatus]) != kCgNeedTrue) return;
+    int i, j;
+    node_of(i, j);
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz);
+    double acc_t = 0.0, acc_r = 0.0;
+    if (i < p.nx && j < p.ny) {
+        for (int k = k0; k < k1; ++k) {
+            if (!is_interior(i, j, k, p.nx, p.ny, p.nz)) continue;
+            const long long c = k * sz + j * sy + i;
+            const double s = ((phi[c - 1] + phi[c + 1]) + (phi[c - sy] + phi[c + sy])) +
+                             (phi[c - sz] + phi[c + sz]);
+            const double lap = (s - 6.0 * phi[c]) * p.inv_dx2;
+            const double rt = b[c] + lap;  // b - A phi, A = -L
+            const T rs = T(rt);
+            r[c] = rs;
+            acc_t += rt * rt;
+            acc_r += (double)rs * (double)rs;
+        }
+    }
+    double v[2] = {acc_t, acc_r}, s[2];
+    if (last_block_sums<2>(p, v, s) && threadIdx.x == 0) {
+        const double bb = p.scal[kBB];
+        p.scal[kTrue2] = s[0];
+        p.ctrl[kCgRefine] += 1;
+        if (!isfinite(s[0]) || !isfinite(s[1])) {
+            p.ctrl[kCgStatus] = kCgNonfinite;
+        } else if (sqrt(s[0] / bb) < p.scal[kTol]) {
+            p.ctrl[kCgStatus] = kCgConverged;
+        } else if (p.ctrl[kCgIters] >= p.ctrl[kCgMaxIter]) {
+            p.ctrl[kCgStatus] = kCgMaxIterHit;
+        } else {
+            const double rr_prev = p.scal[kRR];
+            p.scal[kBeta] = (p.ctrl[kCgIters] == 0 || rr_prev <= 0.0) ? 0.0 : s[1] / rr_prev;
+            p.scal[kRR] = s[1];
+            p.scal[kRR0] = s[1];
+            p.scal[kRRLast] = s[1];
+            p.ctrl[kCgStatus] = kCgRunning;
+        }
+    }
+}
+
+// Pass 1: p' = r + beta p (centre and neighbours), Ap' on the fly, p'.Ap'.
+template <typename T>
+__global__ void __launch_bounds__(kCgBX *kCgBY)
+k_cg_dir(const T *__restrict__ r, T *__restrict__ p0, T *__restrict__ p1, CgParams p) {
+    if (__ldcg(&p.ctrl[kCgStatus]) != kCgRunning) return;
+    // iteration k reads p[k & 1] and writes p[(k + 1) & 1] (device counter, so
+    // iterations skipped after a status change never flip the parity)
+    const long long it0 = __ldcg(&p.ctrl[kCgIters]);
+    const T *__restrict__ pold = (it0 & 1) ? p1 : p0;
+    T *__restrict__ pnew = (it0 & 1) ? p0 : p1;
+    const T beta = T(__ldcg(&p.scal[kBeta]));
+    int i, j;
+    node_of(i, j);
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz - 1);
+    const T inv = T(p.inv_dx2);
+    typename AccOf<T>::type acc;
+    if (i >= 1 && i <= p.nx - 2 && j >= 1 && j <= p.ny - 2) {
+        auto pn = [&](long long q) { return kv_fma(beta, pold[q], r[q]); };
+        const int ks = max(k0, 1);
+        long long c = ks * sz + j * sy + i;
+        T zm = pn(c - sz), zc = pn(c);
+        for (int k = ks; k < k1; ++k, c += sz) {
+            const T zp = pn(c + sz);
+            const T s = kv_add(kv_add(kv_add(pn(c - 1), pn(c + 1)), kv_add(pn(c - sy), pn(c + sy))),
+                               kv_add(zm, zp));
+            const T Ap = kv_fma(T(6), zc, -s) * inv;
+            pnew[c] = zc;
+            acc.add_prod(zc, Ap);
+            zm = zc;
+            zc = zp;
+        }
+    }
+    double v[1] = {acc.value()}, sm[1];
+    if (last_block_sums<1>(p, v, sm) && threadIdx.x == 0) {
+        const double pAp = sm[0];
+        p.scal[kPAP] = pAp;
+        if (!isfinite(pAp) || pAp <= 0.0)
+            p.ctrl[kCgStatus] = kCgBreakdown;
+        else
+            p.scal[kAlpha] = p.scal[kRR] / pAp;
+    }
+}
+
+// Pass 2: Ap' from p', e += alpha p', r -= alpha Ap', r.r; beta, replacement
+// and stop tests.
+template <typename T>
+__global__ void __launch_bounds__(kCgBX *kCgBY)
+k_cg_upd(const T *__restrict__ p0, const T *__restrict__ p1, T *__restrict__ r, T *__restrict__ e,
+         CgParams p) {
+    if (__ldcg(&p.ctrl[kCgStatus]) != kCgRunning) return;
+    const T *__restrict__ pc_ = (__ldcg(&p.ctrl[kCgIters]) & 1) ? p0 : p1;  // written by k_cg_dir
+    const T alpha = T(__ldcg(&p.scal[kAlpha]));
+    int i, j;
+    node_of(i, j);
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz - 1);
+    const T inv = T(p.inv_dx2);
+    typename AccOf<T>::type acc;
+    if (i >= 1 && i <= p.nx - 2 && j >= 1 && j <= p.ny - 2) {
+        const int ks = max(k0, 1);
+        long long c = ks * sz + j * sy + i;
+        T zm = pc_[c - sz], zc = pc_[c];
+        for (int k = ks; k < k1; ++k, c += sz) {
+            const T zp = pc_[c + sz];
+            const T s = kv_add(kv_add(kv_add(pc_[c - 1], pc_[c + 1]), kv_add(pc_[c - sy], pc_[c + sy])),
+                               kv_add(zm, zp));
+            const T Ap = kv_fma(T(6), zc, -s) * inv;
+            e[c] = kv_fma(alpha, zc, e[c]);
+            const T rn = kv_fma(-alpha, Ap, r[c]);
+            r[c] = rn;
+            acc.add_prod(rn, rn);
+            zm = zc;
+            zc = zp;
+        }
+    }
+    double v[1] = {acc.value()}, sm[1];
+    if (last_block_sums<1>(p, v, sm) && threadIdx.x == 0) {
+        const double rr = sm[0];
+        const long long it = p.ctrl[kCgIters] + 1;
+        p.ctrl[kCgIters] = it;
+        p.scal[kRRLast] = rr;
+        const double bb = p.scal[kBB];
+        const double tol = p.scal[kTol], repl = p.scal[kInner];
+        if (!isfinite(rr)) {
+            p.ctrl[kCgStatus] = kCgNonfinite;
+        } else if (rr <= 0.25 * tol * tol * bb || rr <= repl * repl * p.scal[kRR0] ||
+                   it >= p.ctrl[kCgMaxIter]) {
+            // k_true_res computes beta from the replaced residual and scal[kRR]
+            p.ctrl[kCgStatus] = kCgNeedTrue;
+        } else {
+            p.scal[kBeta] = rr / p.scal[kRR];
+            p.scal[kRR] = rr;
+        }
+    }
+}
+
+// f_S0 = f - D+ phi on every node (phi = 0 beyond the grid); F = S f_S0.
+template <typename T>
+__global__ void __launch_bounds__(kCgBX *kCgBY)
+k_grad(const float *__restrict__ f, const double *__restrict__ phi, const T *__restrict__ S,
+       double S_s, T *__restrict__ F, float *__restrict__ fs_out, CgParams p) {
+    int i, j;
+    node_of(i, j);
+    if (i >= p.nx || j >= p.ny) return;
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz);
+    const long long Nd = (long long)p.nx * p.ny * p.nz;
+    for (int k = k0; k < k1; ++k) {
+        const long long c = k * sz + j * sy + i;
+        const double ph = phi[c];
+        const double px_ = (i + 1 < p.nx) ? phi[c + 1] : 0.0;
+        const double py_ = (j + 1 < p.ny) ? phi[c + sy] : 0.0;
+        const double pz_ = (k + 1 < p.nz) ? phi[c + sz] : 0.0;
+        const double g[3] = {(px_ - ph) * p.inv_dx, (py_ - ph) * p.inv_dx, (pz_ - ph) * p.inv_dx};
+        const double s = S ? (double)S[c] : S_s;
+        const long long cd = ((long long)k * p.ny + j) * p.nx + i;
+        for (int comp = 0; comp < 3; ++comp) {
+            const double fsv = (double)f[comp * p.Np + c] - g[comp];
+            F[comp * p.Np + c] = T(s * fsv);
+            if (fs_out) fs_out[comp * Nd + cd] = (float)fsv;
+        }
+    }
+}
+
+// Per-node stability limit dt <= h^2 / (nu + sqrt(nu^2 + c^2 h^2)), h^2 = dx^2/3
+// (the positive root of dt^2 c^2 + 2 dt nu = h^2), block minima.
+__global__ void k_dtmin(int n, double dx, const float *G, double Gs, const float *rho, double rhos,
+                        const float *eta, double etas, double *out) {
+    __shared__ double sh[256];
+    double m = INFINITY;
+    const double h2 = dx * dx / 3.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const double g = G ? (double)G[c] : Gs;
+        const double r = rho ? (double)rho[c] : rhos;
+        const double e = eta ? (double)eta[c] : etas;
+        const double c2 = g / r, nu = e / r;
+        const double den = nu + sqrt(nu * nu + c2 * h2);
+        double v = den > 0.0 ? h2 / den : INFINITY;
+        if (!(r > 0.0) || g < 0.0 || e < 0.0 || !isfinite(g) || !isfinite(r) || !isfinite(e))
+            v = -1.0;  // invalid medium
+        m = fmin(m, v);
+    }
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+kv_status stable_dt_device(cudaStream_t stream, double *scratch, int n, double dx, const float *G,
+                           double Gs, const float *rho, double rhos, const float *eta, double etas,
+                           double *out) {
+    double *d = scratch;
+    if (!d && cudaMalloc(&d, kDtBlocks * sizeof(double)) != cudaSuccess) return KV_ERR_OOM;
+    k_dtmin<<<kDtBlocks, 256, 0, stream>>>(n, dx, G, Gs, rho, rhos, eta, etas, d);
+    double hbuf[kDtBlocks];
+    cudaError_t e = cudaMemcpyAsync(hbuf, d, sizeof(hbuf), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (!scratch) cudaFree(d);
+    if (e != cudaSuccess) return KV_ERR_CUDA;
+    double m = INFINITY;
+    for (int i = 0; i < kDtBlocks; ++i) m = fmin(m, hbuf[i]);
+    *out = m;
+    return KV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+static CgParams cg_params(kv_handle *h, dim3 grid, int zc) {
+    CgParams p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.nz = h->nz;
+    p.px = h->px;
+    p.Np = h->Np;
+    p.inv_dx2 = 1.0 / (h->dx * h->dx);
+    p.inv_dx = 1.0 / h->dx;
+    p.ctrl = h->ctrl;
+    p.scal = h->scal;
+    p.partials = h->partials;
+    p.zc = zc;
+    p.nblocks = grid.x * grid.y * grid.z;
+    return p;
+}
+
+int cg_zc(const kv_handle *h) { return kCgZc; }
+
+dim3 cg_grid(const kv_handle *h) {
+    const int zc = cg_zc(h);
+    return dim3((h->nx + kCgBX - 1) / kCgBX, (h->ny + kCgBY - 1) / kCgBY, (h->nz + zc - 1) / zc);
+}
+
+static kv_status sync_read(kv_handle *h) {
+    cudaError_t e = cudaMemcpyAsync(h->ctrl_host, h->ctrl, kCtrlWords * sizeof(long long),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->scal_host, h->scal, kCgScalars * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return cuda_check(h, e, "projection poll");
+}
+
+template <typename T>
+static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out,
+                           kv_cg_stats *st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const dim3 grid = cg_grid(h);
+    const int zc = cg_zc(h);
+    const int nt = kCgBX * kCgBY;
+    CgParams p = cg_params(h, grid, zc);
+    cudaStream_t s = h->stream;
+    cudaError_t e;
+    // reset the CG vectors and control words
+    e = cudaMemsetAsync(h->r, 0, h->Np * sizeof(T), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->p[0], 0, h->Np * sizeof(T), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->p[1], 0, h->Np * sizeof(T), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->e, 0, h->Np * sizeof(T), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_check(h, e, "projection memset");
+    long long *ci = h->ctrl_host;
+    double *si = h->scal_host;
+    e = cudaMemcpyAsync(ci, h->ctrl, kCtrlWords * sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(h, e, "projection init");
+    ci[kCgStatus] = kCgNeedTrue;
+    ci[kCgIters] = 0;
+    ci[kCgTicket] = 0;
+    ci[kCgRefine] = 0;
+    ci[kCgMaxIter] = max_iter;
+    for (int q = 0; q < kCgScalars; ++q) si[q] = 0.0;
+    si[kTol] = tol;
+    si[kInner] = (h->precision == KV_FP64) ? 0.0 : kReplace;
+    e = cudaMemcpyAsync(h->ctrl, ci, kCtrlWords * sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->scal, si, kCgScalars * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_check(h, e, "projection init");
+
+    k_rhs<<<grid, nt, 0, s>>>(h->fstage, h->b, p);
+    h->launches++;
+    kv_status ks = sync_read(h);
+    if (ks != KV_OK) return ks;
+    const double bb = h->scal_host[kBB];
+    int status = KV_OK;
+    const int fold_blocks = 148 * 8;
+    if (!isfinite(bb)) {
+        status = KV_ERR_NONFINITE;
+    } else if (bb > 0.0) {
+        const int chunk = 32;
+        while (true) {
+            const long long c = h->ctrl_host[kCgStatus];
+            if (c == kCgNeedTrue) {
+                k_fold_e<T><<<fold_blocks, 256, 0, s>>>(h->phi, (T *)h->e, h->Np, p);
+                k_true_res<T><<<grid, nt, 0, s>>>(h->b, h->phi, (T *)h->r, p);
+                h->launches += 2;
+            } else if (c == kCgRunning) {
+                T *p0 = (T *)h->p[0], *p1 = (T *)h->p[1];
+                for (int it = 0; it < chunk; ++it) {
+                    k_cg_dir<T><<<grid, nt, 0, s>>>((const T *)h->r, p0, p1, p);
+                    k_cg_upd<T><<<grid, nt, 0, s>>>(p0, p1, (T *)h->r, (T *)h->e, p);
+                    h->launches += 2;
+                }
+            } else {
+                break;
+            }
+            if ((ks = sync_read(h)) != KV_OK) return ks;
+        }
+        const long long c = h->ctrl_host[kCgStatus];
+        if (c == kCgBreakdown)
+            status = KV_CG_BREAKDOWN;
+        else if (c == kCgNonfinite)
+            status = KV_ERR_NONFINITE;
+        else if (c == kCgMaxIterHit)
+            status = KV_CG_MAXITER;
+    }
+    k_grad<T><<<grid, nt, 0, s>>>(h->fstage, h->phi, h->het ? (const T *)h->S : nullptr, h->S_s,
+                                  (T *)h->F, fs_out, p);
+    h->launches++;
+    if ((ks = sync_read(h)) != KV_OK) return ks;
+    h->have_force = 1;
+    if (st) {
+        st->iters = (int)h->ctrl_host[kCgIters];
+        st->refinements = (int)std::max(0ll, h->ctrl_host[kCgRefine] - 1);
+        st->status = status;
+        st->rel_res_true = bb > 0.0 ? sqrt(h->scal_host[kTrue2] / bb) : 0.0;
+        st->rel_res_recursive = bb > 0.0 ? sqrt(h->scal_host[kRRLast] / bb) : 0.0;
+        st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                     .count();
+    }
+    if (status == KV_ERR_NONFINITE) return set_error(h, KV_ERR_NONFINITE, "non-finite projection");
+    if (status == KV_CG_BREAKDOWN) return set_error(h, KV_CG_BREAKDOWN, "CG breakdown (p.Ap <= 0)");
+    if (status == KV_CG_MAXITER) {
+        snprintf(h->err, sizeof(h->err), "CG reached max_iter=%d, true rel. residual %.3e", max_iter,
+                 bb > 0.0 ? sqrt(h->scal_host[kTrue2] / bb) : 0.0);
+        return KV_CG_MAXITER;
+    }
+    return KV_OK;
+}
+
+kv_status project(kv_handle *h, double tol, int max_iter, float *fs_out, kv_cg_stats *st) {
+    if (h->precision == KV_FP64) return project_t<double>(h, tol, max_iter, fs_out, st);
+    return project_t<float>(h, tol, max_iter, fs_out, st);
+}
+
+}  // namespace kv

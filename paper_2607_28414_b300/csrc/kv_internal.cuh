@@ -1,0 +1,231 @@
+// kv_internal.cuh -- handle layout, launch parameters and device helpers shared
+// by the libkv translation units (step kernels, projection kernels, C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kv.h"
+
+namespace kv {
+
+// Rows are padded to a multiple of this many elements so that every row
+// starts on a 128-byte boundary (float) and float4/TMA accesses stay aligned.
+constexpr int kPitchAlign = 32;
+
+// Planes per thread column in the CG passes.
+constexpr int kCgZc = 16;
+
+// Device control block of a handle (one allocation, int64 words).
+enum CtrlWord {
+    kStep = 0,       // steps taken since reset (read by every step kernel)
+    kStepTicket = 1, // last-block ticket of the step kernels
+    kErrFlags = 2,   // bit 0: mbarrier timeout, bit 1: trace overflow
+    kCgStatus = 3,   // CG control word (CgCtl)
+    kCgIters = 4,    // CG iterations so far
+    kCgTicket = 5,   // last-block ticket of the CG kernels
+    kCgRefine = 6,   // true-residual evaluations
+    kCgMaxIter = 7,  // iteration cap
+    kCtrlWords = 16
+};
+
+enum CgCtl : long long {
+    kCgRunning = 0,
+    kCgConverged = 1,
+    kCgBreakdown = 2,
+    kCgNonfinite = 3,
+    kCgNeedTrue = 4,  // inner cycle finished: evaluate the true residual
+    kCgMaxIterHit = 5
+};
+
+// Device scalars of the CG (doubles).
+enum CgScalar {
+    kRR = 0,      // r.r of the current recursive residual
+    kPAP = 1,     // p.Ap
+    kAlpha = 2,
+    kBeta = 3,
+    kBB = 4,      // ||b||^2
+    kRR0 = 5,     // r.r at the start of the current inner cycle
+    kTrue2 = 6,   // ||b - A phi||^2 of the last true-residual pass
+    kTol = 7,     // tolerance on sqrt(true2 / bb)
+    kInner = 8,   // inner-cycle reduction factor on ||r||
+    kRRLast = 9,  // last recursive r.r (statistics)
+    kCgScalars = 16
+};
+
+struct StepParams {
+    int nx, ny, nz, px;
+    long long Np;        // px * ny * nz (elements per component)
+    double A, B;         // homogeneous coefficients (dt^2 G/(rho dx^2), dt eta/(rho dx^2))
+    const float *g;      // envelope table on the device
+    int n_g;
+    long long *ctrl;     // control block
+    const int *sensors;  // 3 * ns node indices
+    int ns;
+    void *traces;        // [cap][ns][3]
+    int cap;
+    int zc;              // planes per block (z chunk)
+    int nblocks;         // blocks in the launch
+};
+
+struct CgParams {
+    int nx, ny, nz, px;
+    long long Np;
+    double inv_dx2;      // 1/dx^2
+    double inv_dx;       // 1/dx
+    long long *ctrl;
+    double *scal;
+    double *partials;    // one double per block (or two)
+    int zc;
+    int nblocks;
+};
+
+}  // namespace kv
+
+struct kv_handle {
+    int nx, ny, nz, px;
+    long long Np;
+    double dx, dt;
+    int precision;        // KV_FP32 / KV_FP64
+    size_t esize;         // bytes per state element
+    cudaStream_t stream;
+    int own_stream;
+    int device;
+
+    // medium
+    int het;
+    double A_s, B_s, S_s;  // homogeneous scalars (A, B already divided by dx^2)
+    void *coef;            // [2][Np] (A', B') when het
+    void *S;               // [Np] dt^2/rho when het
+    double dt_max;
+
+    // state: two buffers of [6][Np] (u_x, u_y, u_z, d_x, d_y, d_z)
+    void *state[2];
+    int cur;
+    void *F;               // [3][Np] dt^2 f_S0 / rho
+    int have_force;
+
+    // envelope, sensors, traces
+    float *g_dev;
+    int n_g;
+    int *sens_dev;
+    int ns;
+    int cap;
+    void *traces;
+    long long *ctrl;       // kv::kCtrlWords
+    long long steps_host;
+
+    // projection
+    void *r;               // [Np] residual (float or double)
+    void *p[2];            // [Np] search direction, ping-pong by iteration parity
+    void *e;               // [Np] correction accumulated since the last replacement
+    double *phi;           // [Np]
+    double *b;             // [Np] right-hand side
+    double *scal;          // kv::kCgScalars
+    double *partials;      // reduction partials
+    double *dtmin;         // kDtBlocks block minima of the stability reduction
+    int partials_len;
+    float *fstage;         // [3][Np] pitched copy of the force input
+    long long *ctrl_host;  // pinned mirror of the control block
+    double *scal_host;     // pinned mirror of the scalars
+
+    // FP32 step kernel configuration and TMA descriptors
+    int variant, tx, ty, zc;
+    CUtensorMap tm_state[2], tm_coef, tm_F;
+    int tma_ready;
+
+    // CUDA graph of a block of steps (one per starting buffer)
+    cudaGraphExec_t graph[2];
+    int graph_steps;
+
+    long long launches;
+    int sticky;
+    char err[512];
+};
+
+namespace kv {
+
+kv_status set_error(kv_handle *h, kv_status st, const char *fmt, ...);
+kv_status cuda_check(kv_handle *h, cudaError_t e, const char *what);
+
+// Step kernels (kv_step.cu)
+kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attributes
+kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
+
+// Projection kernels (kv_cg.cu)
+kv_status project(kv_handle *h, double tol, int max_iter, float *fs_out, kv_cg_stats *st);
+
+// Device stability limit over dense fields: kDtBlocks block minima in
+// `scratch` (kDtBlocks doubles; NULL = a temporary allocation), synchronising.
+constexpr int kDtBlocks = 592;
+kv_status stable_dt_device(cudaStream_t stream, double *scratch, int n, double dx, const float *G,
+                           double Gs, const float *rho, double rhos, const float *eta, double etas,
+                           double *out);
+
+inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+}  // namespace kv
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T kv_fma(T a, T b, T c);
+template <>
+__device__ __forceinline__ float kv_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double kv_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T>
+__device__ __forceinline__ T kv_add(T a, T b);
+template <>
+__device__ __forceinline__ float kv_add<float>(float a, float b) { return __fadd_rn(a, b); }
+template <>
+__device__ __forceinline__ double kv_add<double>(double a, double b) { return __dadd_rn(a, b); }
+
+// One node of the increment-form update. su / sd are the sums of the six
+// neighbours of u / d, formed by the caller as ((xm + xp) + (ym + yp)) + (zm + zp).
+//   L^u = su - 6u,  L^d = sd - 6d
+//   d'  = d + A L^u + B L^d + gF,  u' = u + d'
+// Every operation is an explicit rounding step so that all step kernels give
+// bit-identical results.
+template <typename T>
+__device__ __forceinline__ void kv_update(T u, T su, T d, T sd, T A, T B, T g, T F, T &u_out,
+                                          T &d_out) {
+    T lu = kv_fma(T(-6), u, su);
+    T ld = kv_fma(T(-6), d, sd);
+    T dn = kv_fma(g, F, d);
+    dn = kv_fma(B, ld, dn);
+    dn = kv_fma(A, lu, dn);
+    d_out = dn;
+    u_out = kv_add(u, dn);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum of a double (fixed reduction tree for a given
+// blockDim). Every thread of the block must call it; the result is returned
+// to all threads.
+__device__ __forceinline__ double block_sum_d(double v, double *sh /* >= 33 doubles */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (warp == 0) t = warp_sum_d(t);
+    if (threadIdx.x == 0) sh[32] = t;
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}

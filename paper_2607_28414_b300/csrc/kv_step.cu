@@ -1,0 +1,534 @@
+// kv_step.cu -- the fused Kelvin-Voigt time step (Sec. 3.1 explicit update with
+// the pre-computed projected force of Sec. 3.3) and its helpers.
+//
+// State layout: two buffers of [6][nz][ny][px] (u_x, u_y, u_z, d_x, d_y, d_z),
+// d = u^n - u^{n-1}; px = nx rounded up to 32 elements. One step reads buffer
+// `cur` and writes the other (ping-pong), so no stencil read ever races a write.
+// The Dirichlet layer and the row padding hold zeros and are never written.
+//
+// Per interior node, component c (L^ = unscaled 7-point stencil):
+//   d' = d + A' L^u + B' L^d + g_n F,   u' = u + d'
+// with A' = dt^2 G/(rho dx^2), B' = dt eta/(rho dx^2), F = dt^2 f_S0/rho. This is
+// u^{n+1} = 2u^n - u^{n-1} + dt^2 a^n of Sec. 3.1 with udot = (u^n - u^{n-1})/dt,
+// rewritten so that the FP32 increment d keeps its own relative precision.
+//
+// The last block of every step records the sensors (u^{n+1}) and advances the
+// device step counter, so a block of steps can be replayed from a CUDA graph.
+#include <cudaTypedefs.h>
+#include <stdio.h>
+
+#include "kv_internal.cuh"
+
+namespace kv {
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier and TMA (sm_90+ forms, valid on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 SM clocks (about a second at 2 GHz).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue shared by the step kernels: the last block to finish records
+// u^{n+1} at the sensors and advances the step counter.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void step_epilogue(const T *out, const StepParams &p, long long step) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t =
+            atomicAdd(reinterpret_cast<unsigned long long *>(&p.ctrl[kStepTicket]), 1ull);
+        s_last = (t == (unsigned long long)(p.nblocks - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (step < p.cap) {
+        T *tr = reinterpret_cast<T *>(p.traces) + (size_t)step * p.ns * 3;
+        for (int s = threadIdx.x; s < p.ns; s += blockDim.x) {
+            const int i = p.sensors[3 * s], j = p.sensors[3 * s + 1], k = p.sensors[3 * s + 2];
+            const size_t c = ((size_t)k * p.ny + j) * p.px + i;
+            for (int comp = 0; comp < 3; ++comp) tr[3 * s + comp] = __ldcg(out + comp * p.Np + c);
+        }
+    } else if (threadIdx.x == 0 && p.ns > 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 2ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p.ctrl[kStepTicket] = 0;
+        p.ctrl[kStep] = step + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain per-node kernel (FP64 check mode; FP32 reference variant).
+// Grid: (ceil(nx/128), ny-2, nz-2), block 128; node (i, 1+blockIdx.y, 1+blockIdx.z).
+// ---------------------------------------------------------------------------
+template <typename T, bool HET>
+__global__ void __launch_bounds__(128)
+k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ coef,
+             const T *__restrict__ F, StepParams p) {
+    const long long step = __ldcg(&p.ctrl[kStep]);
+    const T g = (step < p.n_g) ? T(p.g[step]) : T(0);
+    const bool force = (g != T(0));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 1 + blockIdx.y;
+    const int k = 1 + blockIdx.z;
+    if (i >= 1 && i <= p.nx - 2) {
+        const long long sy = p.px, sz = (long long)p.px * p.ny;
+        const long long c = k * sz + j * sy + i;
+        const T A = HET ? coef[c] : T(p.A);
+        const T B = HET ? coef[p.Np + c] : T(p.B);
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+            const T *u = in + comp * p.Np;
+            const T *d = in + (3 + comp) * p.Np;
+            const T su = kv_add(kv_add(kv_add(u[c - 1], u[c + 1]), kv_add(u[c - sy], u[c + sy])),
+                                kv_add(u[c - sz], u[c + sz]));
+            const T sd = kv_add(kv_add(kv_add(d[c - 1], d[c + 1]), kv_add(d[c - sy], d[c + sy])),
+                                kv_add(d[c - sz], d[c + sz]));
+            const T Fv = force ? F[comp * p.Np + c] : T(0);
+            T uo, dn;
+            kv_update(u[c], su, d[c], sd, A, B, g, Fv, uo, dn);
+            out[comp * p.Np + c] = uo;
+            out[(3 + comp) * p.Np + c] = dn;
+        }
+    }
+    step_epilogue<T>(out, p, step);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged z-march kernel (FP32).
+//
+// A block owns a TX x TY column of nodes and marches planes k0..k1-1. Each
+// plane of all six state fields, with a 4-node x halo (keeps the TMA x start
+// 16-byte aligned) and a 1-node y halo, arrives in one 4D TMA box
+// (TX+8, TY+2, 1, 6) into a ring of NS shared-memory stages; the coefficient
+// (A', B') and projected-force (3 components) tiles of the centre plane ride in
+// the same stage. Planes k-1, k, k+1 are resident while plane k is computed and
+// up to NS-3 further planes are in flight. Each thread computes four
+// consecutive x nodes (one float4) of one row; its x neighbours come from warp
+// shuffles (row edges from shared memory). Outputs go straight to global
+// memory as float4 stores.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, bool HET>
+struct TmaTile {
+    static constexpr int NT = TX * TY / 4;
+    static constexpr int GX = TX / 4;
+    static constexpr int BX = TX + 8;
+    static constexpr int BY = TY + 2;
+    static constexpr int FIELD = BX * BY;
+    static constexpr int STATE = 6 * FIELD;
+    static constexpr int COEF = HET ? 2 * TX * TY : 0;
+    static constexpr int FRC = 3 * TX * TY;
+    static constexpr int STAGE = (STATE + COEF + FRC + 31) / 32 * 32;  // floats, 128 B multiple
+};
+
+constexpr int kStages = 4;
+
+template <int TX, int TY, bool HET>
+__global__ void __launch_bounds__(TX *TY / 4)
+k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
+           const __grid_constant__ CUtensorMap tm_F, float *__restrict__ out, StepParams p) {
+    using TT = TmaTile<TX, TY, HET>;
+    constexpr int NS = kStages;
+    extern __shared__ __align__(128) float smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * TT::STAGE);
+
+    const int tid = threadIdx.x;
+    const int gx = tid % TT::GX, gy = tid / TT::GX;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = 1 + blockIdx.y * TY;
+    const int k0 = 1 + blockIdx.z * p.zc;
+    const int k1 = min(k0 + p.zc, p.nz - 1);  // planes k0..k1-1 are computed
+    const int kb = k0 - 1;                     // first staged plane
+    const long long step = __ldcg(&p.ctrl[kStep]);
+    const float g = (step < p.n_g) ? p.g[step] : 0.f;
+    const bool force = (g != 0.f);
+    const uint32_t bar0 = smem_u32(bars);
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    auto issue = [&](int q) {  // thread 0: stage plane q (kb <= q <= k1)
+        const int s = (q - kb) % NS;
+        float *st = smem + s * TT::STAGE;
+        const uint32_t bar = bar0 + 8 * s;
+        const bool centre = (q >= k0 && q < k1);
+        const bool wc = centre && HET;
+        const bool wf = centre && force;
+        const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0) + (wf ? TT::FRC * 4 : 0);
+        mbar_expect_tx(bar, bytes);
+        tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 1, q, 0, bar);
+        if (wc) tma_load_4d(smem_u32(st + TT::STATE), &tm_coef, x0, y0, q, 0, bar);
+        if (wf) tma_load_4d(smem_u32(st + TT::STATE + TT::COEF), &tm_F, x0, y0, q, 0, bar);
+    };
+
+    if (tid == 0) {
+        const int last = min(k1, kb + NS - 1);
+        for (int q = kb; q <= last; ++q) issue(q);
+    }
+
+    bool ok = true;
+    const int y = y0 + gy;
+    const int x = x0 + 4 * gx;
+    const bool row_ok = (y <= p.ny - 2) && (x < p.px);
+    const int o = (gy + 1) * TT::BX + 4 + 4 * gx;  // this thread's first node in a field tile
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const unsigned FULL = 0xffffffffu;
+
+    for (int k = k0; k < k1; ++k) {
+        if (k == k0) {
+            ok &= mbar_wait_bounded(bar0 + 8 * ((kb - kb) % NS), ((kb - kb) / NS) & 1);
+            ok &= mbar_wait_bounded(bar0 + 8 * ((k0 - kb) % NS), ((k0 - kb) / NS) & 1);
+        }
+        ok &= mbar_wait_bounded(bar0 + 8 * ((k + 1 - kb) % NS), ((k + 1 - kb) / NS) & 1);
+
+        const float *sc = smem + ((k - kb) % NS) * TT::STAGE;
+        const float *sm = smem + ((k - 1 - kb) % NS) * TT::STAGE;
+        const float *sp = smem + ((k + 1 - kb) % NS) * TT::STAGE;
+
+        float4 ctr[6], sum[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const float *fc = sc + f * TT::FIELD + o;
+            const float4 c = *reinterpret_cast<const float4 *>(fc);
+            const float4 ym = *reinterpret_cast<const float4 *>(fc - TT::BX);
+            const float4 yp = *reinterpret_cast<const float4 *>(fc + TT::BX);
+            const float4 zm = *reinterpret_cast<const float4 *>(sm + f * TT::FIELD + o);
+            const float4 zp = *reinterpret_cast<const float4 *>(sp + f * TT::FIELD + o);
+            float left = __shfl_up_sync(FULL, c.w, 1);
+            float right = __shfl_down_sync(FULL, c.x, 1);
+            if (gx == 0) left = fc[-1];
+            if (gx == TT::GX - 1) right = fc[4];
+            float4 s;
+            s.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+            s.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+            s.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+            s.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+            ctr[f] = c;
+            sum[f] = s;
+        }
+        float4 A4, B4;
+        if (HET) {
+            A4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + gy * TX + 4 * gx);
+            B4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + TX * TY + gy * TX + 4 * gx);
+        } else {
+            A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+            B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+        }
+        if (row_ok) {
+            const long long gbase = k * sz + y * sy + x;
+            const bool m0 = (x >= 1) && (x <= p.nx - 2);
+            const bool m1 = (x + 1 >= 1) && (x + 1 <= p.nx - 2);
+            const bool m2 = (x + 2 <= p.nx - 2);
+            const bool m3 = (x + 3 <= p.nx - 2);
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (force)
+                    F4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + TT::COEF +
+                                                           comp * TX * TY + gy * TX + 4 * gx);
+                const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
+                float4 uo, dn;
+                kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g, F4.x, uo.x, dn.x);
+                kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g, F4.y, uo.y, dn.y);
+                kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g, F4.z, uo.z, dn.z);
+                kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g, F4.w, uo.w, dn.w);
+                if (!m0) uo.x = dn.x = 0.f;
+                if (!m1) uo.y = dn.y = 0.f;
+                if (!m2) uo.z = dn.z = 0.f;
+                if (!m3) uo.w = dn.w = 0.f;
+                *reinterpret_cast<float4 *>(out + comp * p.Np + gbase) = uo;
+                *reinterpret_cast<float4 *>(out + (3 + comp) * p.Np + gbase) = dn;
+            }
+        }
+        __syncthreads();  // every thread is done with plane k-1's stage
+        if (tid == 0) {
+            const int q = k - 1 + NS;
+            if (q <= k1) {
+                fence_proxy_async();
+                issue(q);
+            }
+        }
+    }
+
+    if (!ok) atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
+    // A wait that gave up may leave a copy in flight: drain every stage (bounded)
+    // before the block's shared memory is released.
+    if (__syncthreads_or(!ok) && tid == 0) {
+        const int rel_max = k1 - kb;
+        for (int s = 0; s < NS && s <= rel_max; ++s) {
+            const int rel_last = s + ((rel_max - s) / NS) * NS;
+            mbar_wait_bounded(bar0 + 8 * s, (rel_last / NS) & 1);
+        }
+    }
+    step_epilogue<float>(out, p, step);
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels: medium fold, initial velocity
+// ---------------------------------------------------------------------------
+// Grid: (ceil(px/128), ny, nz), block 128.
+template <typename T>
+__global__ void k_fold(const float *__restrict__ G, const float *__restrict__ rho,
+                       const float *__restrict__ eta, double Gs, double rhos, double etas,
+                       T *__restrict__ coef, T *__restrict__ S, long long Np, int nx, int px,
+                       int ny, double dt, double dx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= px) return;
+    const long long c = ((long long)blockIdx.z * ny + blockIdx.y) * px + i;
+    if (i >= nx) {  // row padding
+        coef[c] = T(0);
+        coef[Np + c] = T(0);
+        S[c] = T(0);
+        return;
+    }
+    const double g = G ? (double)G[c] : Gs;
+    const double r = rho ? (double)rho[c] : rhos;
+    const double e = eta ? (double)eta[c] : etas;
+    const double inv = 1.0 / (dx * dx);
+    coef[c] = T(dt * dt * g / r * inv);
+    coef[Np + c] = T(dt * e / r * inv);
+    S[c] = T(dt * dt / r);
+}
+
+template <typename T>
+__global__ void k_init_velocity(const float *__restrict__ v, T *__restrict__ st, int nx, int ny,
+                                int nz, int px, long long Np, double dt) {
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= Np) return;
+    const int i = (int)(c % px);
+    const long long r = c / px;
+    const int j = (int)(r % ny);
+    const int k = (int)(r / ny);
+    const bool in = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+    for (int comp = 0; comp < 3; ++comp) {
+        st[comp * Np + c] = T(0);
+        st[(3 + comp) * Np + c] = in ? T(dt * (double)v[comp * Np + c]) : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn(kv_handle *h) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !ptr) {
+            set_error(h, KV_ERR_CUDA, "cuTensorMapEncodeTiled not available (%s)",
+                      cudaGetErrorString(e));
+            return nullptr;
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+static kv_status encode_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn(h);
+    if (!fn) return KV_ERR_CUDA;
+    cuuint64_t dims[4] = {(cuuint64_t)h->px, (cuuint64_t)h->ny, (cuuint64_t)h->nz,
+                          (cuuint64_t)fields};
+    cuuint64_t strides[3] = {(cuuint64_t)h->px * 4, (cuuint64_t)h->px * h->ny * 4,
+                             (cuuint64_t)h->Np * 4};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)fields};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(h, KV_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) box %dx%dx1x%d", (int)r,
+                         bx, by, fields);
+    return KV_OK;
+}
+
+typedef void (*TmaKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
+                          StepParams);
+
+template <int TX, int TY>
+static bool pick(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (tx != TX || ty != TY) return false;
+    if (het) {
+        *k = k_step_tma<TX, TY, true>;
+        *smem = kStages * TmaTile<TX, TY, true>::STAGE * 4 + kStages * 8;
+    } else {
+        *k = k_step_tma<TX, TY, false>;
+        *smem = kStages * TmaTile<TX, TY, false>::STAGE * 4 + kStages * 8;
+    }
+    *nt = TX * TY / 4;
+    return true;
+}
+
+static bool tma_kernel_for(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    return pick<32, 8>(tx, ty, het, k, smem, nt) || pick<32, 16>(tx, ty, het, k, smem, nt) ||
+           pick<64, 4>(tx, ty, het, k, smem, nt) || pick<64, 8>(tx, ty, het, k, smem, nt) ||
+           pick<64, 16>(tx, ty, het, k, smem, nt) || pick<128, 2>(tx, ty, het, k, smem, nt) ||
+           pick<128, 4>(tx, ty, het, k, smem, nt) || pick<128, 8>(tx, ty, het, k, smem, nt);
+}
+
+kv_status step_prepare(kv_handle *h) {
+    h->tma_ready = 0;
+    if (h->precision != KV_FP32 || h->variant != 0) return KV_OK;
+    TmaKernel k;
+    size_t smem;
+    int nt;
+    if (!tma_kernel_for(h->tx, h->ty, h->het != 0, &k, &smem, &nt))
+        return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d", h->tx, h->ty);
+    if (smem > 227 * 1024)
+        return set_error(h, KV_ERR_ARG, "tile %dx%d needs %zu bytes of shared memory", h->tx, h->ty,
+                         smem);
+    kv_status st;
+    for (int b = 0; b < 2; ++b)
+        if ((st = encode_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 2)) != KV_OK)
+            return st;
+    if (h->het && (st = encode_4d(h, &h->tm_coef, h->coef, 2, h->tx, h->ty)) != KV_OK) return st;
+    if (!h->het) h->tm_coef = h->tm_state[0];  // unused placeholder
+    if ((st = encode_4d(h, &h->tm_F, h->F, 3, h->tx, h->ty)) != KV_OK) return st;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(step)");
+    h->tma_ready = 1;
+    return KV_OK;
+}
+
+static StepParams make_params(kv_handle *h, int nblocks) {
+    StepParams p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.nz = h->nz;
+    p.px = h->px;
+    p.Np = h->Np;
+    p.A = h->A_s;
+    p.B = h->B_s;
+    p.g = h->g_dev;
+    p.n_g = h->have_force ? h->n_g : 0;
+    p.ctrl = h->ctrl;
+    p.sensors = h->sens_dev;
+    p.ns = h->ns;
+    p.traces = h->traces;
+    p.cap = h->cap;
+    p.zc = h->zc;
+    p.nblocks = nblocks;
+    return p;
+}
+
+kv_status step_launch(kv_handle *h, int from) {
+    void *in = h->state[from];
+    void *out = h->state[1 - from];
+    if (h->precision == KV_FP32 && h->variant == 0) {
+        if (!h->tma_ready) {
+            kv_status st = step_prepare(h);
+            if (st != KV_OK) return st;
+        }
+        TmaKernel k;
+        size_t smem;
+        int nt;
+        tma_kernel_for(h->tx, h->ty, h->het != 0, &k, &smem, &nt);
+        dim3 grid((h->px + h->tx - 1) / h->tx, (h->ny - 2 + h->ty - 1) / h->ty,
+                  (h->nz - 2 + h->zc - 1) / h->zc);
+        StepParams p = make_params(h, grid.x * grid.y * grid.z);
+        k<<<grid, nt, smem, h->stream>>>(h->tm_state[from], h->tm_coef, h->tm_F, (float *)out, p);
+    } else {
+        dim3 grid((h->nx + 127) / 128, h->ny - 2, h->nz - 2);
+        StepParams p = make_params(h, grid.x * grid.y * grid.z);
+        if (h->precision == KV_FP64) {
+            if (h->het)
+                k_step_plain<double, true><<<grid, 128, 0, h->stream>>>(
+                    (const double *)in, (double *)out, (const double *)h->coef,
+                    (const double *)h->F, p);
+            else
+                k_step_plain<double, false><<<grid, 128, 0, h->stream>>>(
+                    (const double *)in, (double *)out, nullptr, (const double *)h->F, p);
+        } else {
+            if (h->het)
+                k_step_plain<float, true><<<grid, 128, 0, h->stream>>>(
+                    (const float *)in, (float *)out, (const float *)h->coef, (const float *)h->F,
+                    p);
+            else
+                k_step_plain<float, false><<<grid, 128, 0, h->stream>>>(
+                    (const float *)in, (float *)out, nullptr, (const float *)h->F, p);
+        }
+    }
+    h->launches++;
+    return cuda_check(h, cudaGetLastError(), "step launch");
+}
+
+// Launchers used by the C ABI (kv_api.cu).
+kv_status launch_fold(kv_handle *h, const float *G, double Gs, const float *rho, double rhos,
+                      const float *eta, double etas) {
+    const dim3 grid((h->px + 127) / 128, h->ny, h->nz);
+    if (h->precision == KV_FP64)
+        k_fold<double><<<grid, 128, 0, h->stream>>>(G, rho, eta, Gs, rhos, etas, (double *)h->coef,
+                                                    (double *)h->S, h->Np, h->nx, h->px, h->ny,
+                                                    h->dt, h->dx);
+    else
+        k_fold<float><<<grid, 128, 0, h->stream>>>(G, rho, eta, Gs, rhos, etas, (float *)h->coef,
+                                                   (float *)h->S, h->Np, h->nx, h->px, h->ny, h->dt,
+                                                   h->dx);
+    h->launches++;
+    return cuda_check(h, cudaGetLastError(), "fold launch");
+}
+
+kv_status launch_init_velocity(kv_handle *h, const float *v_pitched) {
+    const int nt = 256;
+    const long long nb = (h->Np + nt - 1) / nt;
+    if (h->precision == KV_FP64)
+        k_init_velocity<double><<<(unsigned)nb, nt, 0, h->stream>>>(
+            v_pitched, (double *)h->state[h->cur], h->nx, h->ny, h->nz, h->px, h->Np, h->dt);
+    else
+        k_init_velocity<float><<<(unsigned)nb, nt, 0, h->stream>>>(
+            v_pitched, (float *)h->state[h->cur], h->nx, h->ny, h->nz, h->px, h->Np, h->dt);
+    h->launches++;
+    return cuda_check(h, cudaGetLastError(), "initial velocity launch");
+}
+}  // namespace kv

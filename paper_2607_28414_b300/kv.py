@@ -1,0 +1,272 @@
+"""Python binding of libkv (include/kv.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the CUDA library; nothing here
+computes any part of the method. Arrays may be NumPy arrays or torch tensors
+(CPU tensors and NumPy arrays are host fields, CUDA tensors device fields);
+scalars become KV_SCALAR fields. A non-OK status raises KvError, which carries
+the status code and libkv's one-line message. The library must be built
+(`python -m paper_2607_28414_b300.build`); importing this module without it
+raises ImportError, and there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkv.so")
+
+KV_OK = 0
+KV_ERR_ARG = 1
+KV_ERR_CUDA = 2
+KV_ERR_OOM = 3
+KV_ERR_UNSTABLE_DT = 4
+KV_ERR_NONFINITE = 5
+KV_CG_BREAKDOWN = 6
+KV_CG_MAXITER = 7
+KV_ERR_TIMEOUT = 8
+KV_ERR_STATE = 9
+KV_ERR_UNSUPPORTED = 10
+
+KV_FP32 = 0
+KV_FP64 = 1
+KV_SCALAR = 0
+KV_HOST = 1
+KV_DEVICE = 2
+
+FIELD_U, FIELD_D, FIELD_PHI, FIELD_F = 0, 1, 2, 3
+
+
+class KvField(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("value", ctypes.c_double), ("where", ctypes.c_int)]
+
+
+class KvCgStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_res_true", ctypes.c_double), ("rel_res_recursive", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KvError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libkv is not built ({LIB_PATH} missing); run "
+                              "python -m paper_2607_28414_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        H = ctypes.c_void_p
+        i, d, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        F = KvField
+        L.kv_status_string.restype = ctypes.c_char_p
+        L.kv_status_string.argtypes = [i]
+        L.kv_last_error.restype = ctypes.c_char_p
+        L.kv_last_error.argtypes = [H]
+        L.kv_stable_dt.argtypes = [i, i, i, d, F, F, F, ctypes.POINTER(d)]
+        L.kv_create.argtypes = [ctypes.POINTER(H), i, i, i, d, d, F, F, F, i, vp]
+        L.kv_set_medium.argtypes = [H, F, F, F]
+        L.kv_set_envelope.argtypes = [H, vp, i, i]
+        L.kv_set_sensors.argtypes = [H, vp, i, i]
+        L.kv_reset.argtypes = [H]
+        L.kv_set_initial_velocity.argtypes = [H, F, F, F]
+        L.kv_project_force.argtypes = [H, F, F, F, d, i, i, vp, ctypes.POINTER(KvCgStats)]
+        L.kv_clear_force.argtypes = [H]
+        L.kv_step.argtypes = [H, i]
+        L.kv_steps_taken.argtypes = [H]
+        L.kv_steps_taken.restype = ctypes.c_longlong
+        L.kv_read_traces.argtypes = [H, vp, i, ctypes.POINTER(i)]
+        L.kv_read_field.argtypes = [H, i, i, vp, i]
+        L.kv_sync.argtypes = [H]
+        L.kv_set_step_config.argtypes = [H, i, i, i, i]
+        L.kv_launch_count.argtypes = [H]
+        L.kv_launch_count.restype = ctypes.c_longlong
+        L.kv_destroy.argtypes = [H]
+        for name in ("kv_stable_dt", "kv_create", "kv_set_medium", "kv_set_envelope",
+                     "kv_set_sensors", "kv_reset", "kv_set_initial_velocity", "kv_project_force",
+                     "kv_clear_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
+                     "kv_set_step_config", "kv_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _status_name(s):
+    try:
+        return lib().kv_status_string(int(s)).decode()
+    except Exception:
+        return str(s)
+
+
+def _check(st, h=None):
+    if st != KV_OK:
+        msg = lib().kv_last_error(h).decode(errors="replace")
+        raise KvError(st, msg)
+
+
+def field(x, keep):
+    """KvField for a scalar, NumPy array or torch tensor (float32, dense,
+    C-contiguous). `keep` collects objects that must outlive the call."""
+    if x is None:
+        return KvField(None, 0.0, KV_SCALAR)
+    if isinstance(x, (int, float, np.floating, np.integer)):
+        return KvField(None, float(x), KV_SCALAR)
+    if isinstance(x, np.ndarray):
+        a = np.ascontiguousarray(x, dtype=np.float32)
+        keep.append(a)
+        return KvField(a.ctypes.data, 0.0, KV_HOST)
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            x = x.contiguous().to(torch.float32)
+        keep.append(x)
+        return KvField(x.data_ptr(), 0.0, KV_DEVICE if x.is_cuda else KV_HOST)
+    raise TypeError(f"unsupported field type {type(x)}")
+
+
+def _ptr(x, keep):
+    """Raw pointer and kv_where of a NumPy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        keep.append(x)
+        return x.ctypes.data, KV_HOST
+    import torch
+    if isinstance(x, torch.Tensor):
+        keep.append(x)
+        return x.data_ptr(), (KV_DEVICE if x.is_cuda else KV_HOST)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def kv_stable_dt(nx, ny, nz, dx, G, rho, eta):
+    keep = []
+    out = ctypes.c_double()
+    _check(lib().kv_stable_dt(nx, ny, nz, dx, field(G, keep), field(rho, keep), field(eta, keep),
+                              ctypes.byref(out)))
+    return out.value
+
+
+def kv_create(nx, ny, nz, dx, dt, G, rho, eta, precision=KV_FP32, stream=None):
+    keep = []
+    h = ctypes.c_void_p()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(lib().kv_create(ctypes.byref(h), nx, ny, nz, dx, dt, field(G, keep), field(rho, keep),
+                           field(eta, keep), precision, s))
+    return h
+
+
+def kv_set_medium(h, G, rho, eta):
+    keep = []
+    _check(lib().kv_set_medium(h, field(G, keep), field(rho, keep), field(eta, keep)), h)
+
+
+def kv_set_envelope(h, g):
+    keep = []
+    if isinstance(g, np.ndarray):
+        g = np.ascontiguousarray(g, np.float32)
+    p, where = _ptr(g, keep)
+    _check(lib().kv_set_envelope(h, p, int(len(g)), where), h)
+
+
+def kv_set_sensors(h, ijk, capacity):
+    ijk = np.ascontiguousarray(np.asarray(ijk, np.int32).reshape(-1, 3))
+    _check(lib().kv_set_sensors(h, ijk.ctypes.data, ijk.shape[0], int(capacity)), h)
+
+
+def kv_reset(h):
+    _check(lib().kv_reset(h), h)
+
+
+def kv_set_initial_velocity(h, vx, vy, vz):
+    keep = []
+    _check(lib().kv_set_initial_velocity(h, field(vx, keep), field(vy, keep), field(vz, keep)), h)
+
+
+def kv_project_force(h, fx, fy, fz, tol, max_iter=0, mode=0, fs_out=None, check=True):
+    """Returns the stats dict. With check=False a CG status (maxiter,
+    breakdown, non-finite) is returned in stats['status'] instead of raised."""
+    keep = []
+    st = KvCgStats()
+    fs_ptr = None
+    if fs_out is not None:
+        fs_ptr, where = _ptr(fs_out, keep)
+        if where != KV_DEVICE:
+            raise ValueError("fs_out must be a CUDA tensor")
+    rc = lib().kv_project_force(h, field(fx, keep), field(fy, keep), field(fz, keep), float(tol),
+                                int(max_iter), int(mode), fs_ptr, ctypes.byref(st))
+    d = st.as_dict()
+    d["rc"] = rc
+    if check or rc not in (KV_CG_MAXITER, KV_CG_BREAKDOWN, KV_ERR_NONFINITE):
+        _check(rc, h)
+    return d
+
+
+def kv_clear_force(h):
+    _check(lib().kv_clear_force(h), h)
+
+
+def kv_step(h, n):
+    _check(lib().kv_step(h, int(n)), h)
+
+
+def kv_steps_taken(h):
+    return int(lib().kv_steps_taken(h))
+
+
+def kv_read_traces(h, out):
+    """Fill `out` (NumPy array or torch tensor, float32 for KV_FP32 / float64 for
+    KV_FP64, at least [n_steps, n_sensors, 3]); returns the steps written."""
+    keep = []
+    p, where = _ptr(out, keep)
+    n = ctypes.c_int()
+    _check(lib().kv_read_traces(h, p, where, ctypes.byref(n)), h)
+    return n.value
+
+
+def kv_read_field(h, which, comp, out):
+    keep = []
+    p, where = _ptr(out, keep)
+    _check(lib().kv_read_field(h, int(which), int(comp), p, where), h)
+    return out
+
+
+def kv_sync(h):
+    _check(lib().kv_sync(h), h)
+
+
+def kv_set_step_config(h, variant=-1, tx=0, ty=0, zc=0):
+    _check(lib().kv_set_step_config(h, int(variant), int(tx), int(ty), int(zc)), h)
+
+
+def kv_launch_count(h):
+    return int(lib().kv_launch_count(h))
+
+
+def kv_destroy(h):
+    if h:
+        lib().kv_destroy(h)
+
+
+def kv_last_error(h=None):
+    return lib().kv_last_error(h).decode(errors="replace")
+
+
+def exported_symbols():
+    """Names declared in include/kv.h (used by the load test)."""
+    import re
+    hdr = os.path.join(_HERE, "..", "include", "kv.h")
+    src = open(hdr).read()
+    return sorted(set(re.findall(r"\b(kv_[a-z_0-9]+)\s*\(", src)))
