@@ -25,14 +25,22 @@ FP32_TRACE_TOL = 1e-4
 FP64_TRACE_TOL = 1e-10
 
 
-def max_rel_l2(got, ref):
+def max_rel_l2(got, ref, floor=1e-9):
+    """Max over sensors of ||got - ref|| / ||ref|| (over steps and components).
+
+    Sensors whose reference trace is below `floor` times the largest one (a
+    node on a symmetry plane, where the exact trace is zero and both sides
+    hold rounding noise) are measured against the largest reference trace."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
     den = np.sqrt((ref ** 2).sum(axis=(0, 2)))
     num = np.sqrt(((got - ref) ** 2).sum(axis=(0, 2)))
-    zero = den == 0
-    assert np.all(num[zero] == 0), "sensor with a zero reference trace recorded motion"
-    return float((num[~zero] / den[~zero]).max()) if (~zero).any() else 0.0
+    top = den.max()
+    if top == 0:
+        assert np.all(num == 0), "motion recorded where the reference is at rest"
+        return 0.0
+    small = den < floor * top
+    return float(np.concatenate([num[~small] / den[~small], num[small] / top]).max())
 
 
 def oracle_reference(w, dt, n_steps, tol=1e-13, v0=None):
@@ -221,7 +229,8 @@ def test_curl_initial_velocity_matches_oracle(device, precision, gate):
     s.step()
     tr = s.read_traces().cpu().numpy()
     err = max_rel_l2(tr, ref)
-    print(f"curl start 41^3 x 120 steps, precision {precision}: {err:.3e}")
+    print(f"curl start 41^3 x 120 steps, precision {precision}: {err:.3e}, "
+          f"|gpu| {np.abs(tr).max():.3e} |oracle| {np.abs(ref).max():.3e}")
     assert err <= gate
     s.close()
 
@@ -249,9 +258,13 @@ def test_full_size_heterogeneous_bench_configuration(device):
         expect = w.force[a].astype(np.float64) - g[a]
         scale = np.abs(expect).max() + 1e-30
         assert np.abs(fs_np[a] - expect).max() <= 1e-6 * scale
-    # divergence of the projected force is the residual (discrete projection identity)
+    # divergence of the projected force is the residual (discrete projection
+    # identity), up to the float32 rounding of the stored f_S: each component
+    # carries |delta| <= 2^-24 |f_S| and ||D-|| <= 2/dx per component.
     div_fs = orc.div_minus(*fs_np, w.dx)
-    assert np.linalg.norm(div_fs) / np.linalg.norm(b) < 2e-8
+    fs_norm = np.sqrt(sum((fs_np[a].astype(np.float64) ** 2).sum() for a in range(3)))
+    round_bound = 2.0 ** -24 * (2.0 / w.dx) * np.sqrt(3.0) * fs_norm / np.linalg.norm(b)
+    assert np.linalg.norm(div_fs) / np.linalg.norm(b) < 1e-8 + round_bound
     s.step()
     tr = s.read_traces().cpu().numpy()
     g_env = inputs.push_envelope(n_steps, dt, w.t_push)
@@ -296,7 +309,7 @@ def test_minimal_grid_matches_oracle(device):
 
 
 def test_cg_status_paths(device):
-    w = small_heterogeneous(n=40, n_steps=5)
+    w = ragged_workload()
     s = Solver(w)
     st = kv.kv_project_force(s.h, *s.force, 1e-8, 3, 0, None, check=False)
     assert st["rc"] == kv.KV_CG_MAXITER and st["iters"] == 3
