@@ -143,6 +143,34 @@ kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_fie
 kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol,
                            int max_iter, int mode, float *fs_out, kv_cg_stats *stats);
 
+/*
+ * The projection of kv_project_force without any device allocation. The paper
+ * has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or cudaFree -- code whose device memory is owned by another
+ * allocator (a framework's caching allocator that has already reserved the
+ * pool, or a fixed memory budget) and code on a latency-critical stream that
+ * cannot afford the device-wide synchronisation cudaFree implies. No handle is
+ * needed. fx, fy, fz: device pointers to dense nx*ny*nz float fields. fs_out:
+ * device pointer to 3*nx*ny*nz floats (component-major) that receives
+ * f_S0 = b0 - D+ phi, as kv_project_force's fs_out does (FP32 vectors, FP64
+ * reductions, same stopping rule). tol, max_iter and stats as in
+ * kv_project_force. stream: a cudaStream_t or NULL (the legacy default stream).
+ *
+ * The working set lives in one static device array of about 11 MB that every
+ * GPU which loads libkv holds until the process exits. Limit: rows are padded
+ * to a multiple of 32 nodes and the padded grid ((nx rounded up to 32) * ny * nz)
+ * may have at most 262144 nodes (64^3 fits); larger grids are rejected with
+ * KV_ERR_ARG and a message in kv_last_error(NULL). The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture. Every call shares the array and it
+ * keeps the last call's contents: each call clears what must start at zero,
+ * and calls that overlap on the GPU (other streams, other host threads) race
+ * on it. Errors are reported in kv_last_error(NULL). Synchronising.
+ */
+kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx, const float *fx,
+                                   const float *fy, const float *fz, double tol, int max_iter,
+                                   float *fs_out, kv_cg_stats *stats, void *stream);
+
 /* Drop the projected force (the step then runs unforced). */
 kv_status kv_clear_force(kv_handle *h);
 

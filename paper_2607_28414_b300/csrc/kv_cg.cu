@@ -510,3 +510,195 @@ kv_status project(kv_handle *h, double tol, int max_iter, float *fs_out, kv_cg_s
 }
 
 }  // namespace kv
+
+// ---------------------------------------------------------------------------
+// Projection without device allocation (kv_project_force_noalloc).
+//
+// For callers that cannot call cudaMalloc or cudaFree: code whose device
+// memory is owned by another allocator (a framework's caching allocator that
+// has already reserved the pool, or a fixed memory budget), and code on a
+// latency-critical stream that cannot afford the device-wide synchronisation
+// cudaFree implies. The whole working set of the projection lives in one
+// file-scope device array of kNoallocBytes, which every GPU that loads libkv
+// holds until the process exits. The first call on a device looks up the
+// array's device address with cudaGetSymbolAddress (so make that first call
+// before any stream capture); later calls reuse the cached address. All calls
+// share the array and it keeps the last call's contents, so each call clears
+// what must start at zero, and calls that overlap on the GPU (other streams
+// or other host threads) race on it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace kv {
+
+constexpr long long kNoallocMaxNodes = 1ll << 18;  // padded nodes: up to 64^3
+constexpr int kNoallocMaxBlocks = 4096;            // CG blocks (partials slots)
+
+// Layout of the scratch array (each part 256-byte aligned).
+constexpr size_t kNaCtrl = 0;                                   // 16 x int64
+constexpr size_t kNaScal = 256;                                 // 16 x double
+constexpr size_t kNaPart = 512;                                 // 2 x kNoallocMaxBlocks doubles
+constexpr size_t kNaF = kNaPart + 2 * kNoallocMaxBlocks * 8;    // 3 x Np floats (input force)
+constexpr size_t kNaR = kNaF + 3 * kNoallocMaxNodes * 4;        // Np floats
+constexpr size_t kNaP = kNaR + kNoallocMaxNodes * 4;            // p0, p1, e: 3 x Np floats
+constexpr size_t kNaPhi = kNaP + 3 * kNoallocMaxNodes * 4;      // Np doubles
+constexpr size_t kNaB = kNaPhi + kNoallocMaxNodes * 8;          // Np doubles
+constexpr size_t kNoallocBytes = kNaB + kNoallocMaxNodes * 8;   // about 11 MB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_ptr[64];  // device address of the array, per device
+
+static kv_status noalloc_setup(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(nullptr, KV_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64)
+        return set_error(nullptr, KV_ERR_UNSUPPORTED,
+                         "device %d is beyond the 64 devices the set-up table holds", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return set_error(nullptr, KV_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s",
+                             cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return KV_OK;
+}
+
+}  // namespace kv
+
+extern "C" kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx, const float *fx,
+                                              const float *fy, const float *fz, double tol,
+                                              int max_iter, float *fs_out, kv_cg_stats *stats,
+                                              void *stream) {
+    using namespace kv;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (nx < 3 || ny < 3 || nz < 3 || !(dx > 0.0) || !(tol > 0.0) || !fx || !fy || !fz || !fs_out)
+        return set_error(nullptr, KV_ERR_ARG,
+                         "kv_project_force_noalloc: invalid grid, dx, tol or pointer");
+    const long long px = round_up(nx, kPitchAlign);
+    const long long Np = px * ny * nz;
+    if (Np > kNoallocMaxNodes)
+        return set_error(nullptr, KV_ERR_ARG,
+                         "kv_project_force_noalloc: grid %dx%dx%d needs %lld padded nodes (rows "
+                         "padded to %d); the static scratch holds at most %lld",
+                         nx, ny, nz, Np, kPitchAlign, kNoallocMaxNodes);
+    const dim3 grid((nx + kCgBX - 1) / kCgBX, (ny + kCgBY - 1) / kCgBY, (nz + kCgZc - 1) / kCgZc);
+    const long long nblocks = (long long)grid.x * grid.y * grid.z;
+    if (nblocks > kNoallocMaxBlocks)
+        return set_error(nullptr, KV_ERR_ARG,
+                         "kv_project_force_noalloc: grid %dx%dx%d needs %lld reduction blocks; at "
+                         "most %d",
+                         nx, ny, nz, nblocks, kNoallocMaxBlocks);
+    if (max_iter <= 0) max_iter = 20 * std::max(nx, std::max(ny, nz));
+    void *base = nullptr;
+    kv_status ks = noalloc_setup(&base);
+    if (ks != KV_OK) return ks;
+    unsigned char *sb = (unsigned char *)base;
+    long long *ctrl = (long long *)(sb + kNaCtrl);
+    double *scal = (double *)(sb + kNaScal);
+    float *fst = (float *)(sb + kNaF);
+    float *r = (float *)(sb + kNaR);
+    float *p0 = (float *)(sb + kNaP);
+    float *p1 = p0 + Np;
+    float *ev = p1 + Np;
+    double *phi = (double *)(sb + kNaPhi);
+    double *b = (double *)(sb + kNaB);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    CgParams p;
+    p.nx = nx;
+    p.ny = ny;
+    p.nz = nz;
+    p.px = (int)px;
+    p.Np = Np;
+    p.inv_dx2 = 1.0 / (dx * dx);
+    p.inv_dx = 1.0 / dx;
+    p.ctrl = ctrl;
+    p.scal = scal;
+    p.partials = (double *)(sb + kNaPart);
+    p.zc = kCgZc;
+    p.nblocks = (int)nblocks;
+
+    long long ch[kCtrlWords];
+    double sh[kCgScalars];
+    for (int q = 0; q < kCtrlWords; ++q) ch[q] = 0;
+    for (int q = 0; q < kCgScalars; ++q) sh[q] = 0.0;
+    ch[kCgStatus] = kCgNeedTrue;
+    ch[kCgMaxIter] = max_iter;
+    sh[kTol] = tol;
+    sh[kInner] = kReplace;
+    auto fail = [&](cudaError_t e, const char *what) {
+        return set_error(nullptr, KV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    // clear everything that must start at zero (the array keeps the last call's contents)
+    cudaError_t e = cudaMemsetAsync(sb + kNaF, 0, kNaPhi + Np * 8 - kNaF, s);
+    if (e != cudaSuccess) return fail(e, "scratch clear");
+    e = cudaMemcpyAsync(ctrl, ch, sizeof(ch), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(scal, sh, sizeof(sh), cudaMemcpyHostToDevice, s);
+    const float *fin[3] = {fx, fy, fz};
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = cudaMemcpy2DAsync(fst + q * Np, (size_t)px * 4, fin[q], (size_t)nx * 4, (size_t)nx * 4,
+                              (size_t)ny * nz, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(e, "scratch set-up copies");
+
+    auto poll = [&]() -> cudaError_t {
+        cudaError_t pe = cudaMemcpyAsync(ch, ctrl, sizeof(ch), cudaMemcpyDeviceToHost, s);
+        if (pe == cudaSuccess) pe = cudaMemcpyAsync(sh, scal, sizeof(sh), cudaMemcpyDeviceToHost, s);
+        if (pe == cudaSuccess) pe = cudaStreamSynchronize(s);
+        return pe;
+    };
+    const int nt = kCgBX * kCgBY;
+    k_rhs<<<grid, nt, 0, s>>>(fst, b, p);
+    if ((e = poll()) != cudaSuccess) return fail(e, "projection");
+    const double bb = sh[kBB];
+    int status = KV_OK;
+    if (!isfinite(bb)) {
+        status = KV_ERR_NONFINITE;
+    } else if (bb > 0.0) {
+        while (true) {
+            const long long c = ch[kCgStatus];
+            if (c == kCgNeedTrue) {
+                k_fold_e<float><<<148 * 8, 256, 0, s>>>(phi, ev, Np, p);
+                k_true_res<float><<<grid, nt, 0, s>>>(b, phi, r, p);
+            } else if (c == kCgRunning) {
+                for (int it = 0; it < 32; ++it) {
+                    k_cg_dir<float><<<grid, nt, 0, s>>>(r, p0, p1, p);
+                    k_cg_upd<float><<<grid, nt, 0, s>>>(p0, p1, r, ev, p);
+                }
+            } else {
+                break;
+            }
+            if ((e = poll()) != cudaSuccess) return fail(e, "projection");
+        }
+        const long long c = ch[kCgStatus];
+        if (c == kCgBreakdown) status = KV_CG_BREAKDOWN;
+        else if (c == kCgNonfinite) status = KV_ERR_NONFINITE;
+        else if (c == kCgMaxIterHit) status = KV_CG_MAXITER;
+    }
+    // f_S0 = f - D+ phi into fs_out; the unscaled copy F (S = 1) goes to the
+    // p0/p1/e region, which the solve no longer needs.
+    k_grad<float><<<grid, nt, 0, s>>>(fst, phi, nullptr, 1.0, p0, fs_out, p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "projection launch");
+    if ((e = poll()) != cudaSuccess) return fail(e, "projection");
+    if (stats) {
+        stats->iters = (int)ch[kCgIters];
+        stats->refinements = (int)std::max(0ll, ch[kCgRefine] - 1);
+        stats->status = status;
+        stats->rel_res_true = bb > 0.0 ? sqrt(sh[kTrue2] / bb) : 0.0;
+        stats->rel_res_recursive = bb > 0.0 ? sqrt(sh[kRRLast] / bb) : 0.0;
+        stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                        .count();
+    }
+    if (status == KV_ERR_NONFINITE) return set_error(nullptr, KV_ERR_NONFINITE, "non-finite projection");
+    if (status == KV_CG_BREAKDOWN) return set_error(nullptr, KV_CG_BREAKDOWN, "CG breakdown (p.Ap <= 0)");
+    if (status == KV_CG_MAXITER)
+        return set_error(nullptr, KV_CG_MAXITER, "CG reached max_iter=%d, true rel. residual %.3e",
+                         max_iter, bb > 0.0 ? sqrt(sh[kTrue2] / bb) : 0.0);
+    return KV_OK;
+}

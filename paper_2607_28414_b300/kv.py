@@ -94,10 +94,12 @@ def lib():
         L.kv_launch_count.argtypes = [H]
         L.kv_launch_count.restype = ctypes.c_longlong
         L.kv_destroy.argtypes = [H]
+        L.kv_project_force_noalloc.argtypes = [i, i, i, d, vp, vp, vp, d, i, vp,
+                                               ctypes.POINTER(KvCgStats), vp]
         for name in ("kv_stable_dt", "kv_create", "kv_set_medium", "kv_set_envelope",
                      "kv_set_sensors", "kv_reset", "kv_set_initial_velocity", "kv_project_force",
                      "kv_clear_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
-                     "kv_set_step_config", "kv_destroy"):
+                     "kv_set_step_config", "kv_destroy", "kv_project_force_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -212,6 +214,26 @@ def kv_project_force(h, fx, fy, fz, tol, max_iter=0, mode=0, fs_out=None, check=
     if check or rc not in (KV_CG_MAXITER, KV_CG_BREAKDOWN, KV_ERR_NONFINITE):
         _check(rc, h)
     return d
+
+
+def kv_project_force_noalloc(nx, ny, nz, dx, fx, fy, fz, tol, fs_out, max_iter=0, stream=None):
+    """Projection without device allocation (working set in libkv's static
+    device array; see include/kv.h). fx, fy, fz, fs_out: CUDA tensors.
+    Returns the stats dict."""
+    keep = []
+    ptrs = []
+    for t in (fx, fy, fz, fs_out):
+        ptr, where = _ptr(t, keep)
+        if where != KV_DEVICE:
+            raise ValueError("kv_project_force_noalloc takes device tensors")
+        ptrs.append(ptr)
+    st = KvCgStats()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    rc = lib().kv_project_force_noalloc(int(nx), int(ny), int(nz), float(dx), ptrs[0], ptrs[1],
+                                        ptrs[2], float(tol), int(max_iter), ptrs[3],
+                                        ctypes.byref(st), s)
+    _check(rc, None)
+    return st.as_dict()
 
 
 def kv_clear_force(h):
