@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
+    ap.add_argument("--step-config", default=None,
+                    help="tx,ty,zc,ns of the step kernel instead of autotuning (profiling runs)")
     ap.add_argument("--cg-tol", type=float, default=1e-8,
                     help="projection tolerance (1e-8 is the workload's; larger values only for "
                          "short profiling runs)")
@@ -201,6 +203,13 @@ def main():
     force_d = [torch.from_numpy(a).to(device) for a in w.force]
     dt = 0.5 * kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *medium_d)
     h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, *medium_d, stream=stream.cuda_stream)
+    if args.step_config:
+        tx, ty, zc, ns = (int(v) for v in args.step_config.split(","))
+        kv.kv_set_step_config(h, 0, tx, ty, zc, ns)
+        tune_ms = None
+    else:
+        tune_ms = kv.kv_autotune_step(h, 8)  # picks tile / stages / z chunk; resets the state
+    step_cfg = kv.kv_get_step_config(h)
     g = inputs.push_envelope(w.n_steps, dt, w.t_push)
     n_force_steps = int(g.sum())
     kv.kv_set_envelope(h, g)
@@ -318,6 +327,7 @@ def main():
                        "l2": "state 0.8 GB > 126 MB L2 (inputs larger than L2)"},
             "kv_step_gcells": step_gcells,
             "projection_ms": float(np.mean(cg_ms)), "cg_iters": int(np.median(cg_iters)),
+            "step_config": step_cfg, "autotune_ms_per_step": tune_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_step_tma", "peak_kind": peak_kind,

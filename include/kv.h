@@ -204,11 +204,23 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
 /* Wait for all work on the handle's stream; report device-side errors. */
 kv_status kv_sync(kv_handle *h);
 
-/* Kernel selection and tile shape of the FP32 step (autotuning and tests).
+/* Kernel selection and launch shape of the FP32 step (autotuning and tests).
  * variant 0: TMA-staged z-march kernel (default); 1: plain per-node kernel.
- * tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in [64, 512],
- * zc >= 1 planes per block. Values <= 0 keep the current choice. */
-kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc);
+ * tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in [64, 512];
+ * zc >= 1 planes per block; ns in {4, 6, 8} shared-memory stages (ns - 3
+ * planes in flight per block). Values <= 0 keep the current choice. A shape
+ * whose stages exceed the shared memory of a block is refused (KV_ERR_ARG)
+ * and the previous configuration is kept. */
+kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, int ns);
+
+/* Current step configuration: cfg[5] = {variant, tx, ty, zc, ns}. */
+kv_status kv_get_step_config(kv_handle *h, int *cfg);
+
+/* Autotuner of the FP32 step: times trial_steps launches of every supported
+ * (tile, stage count, z chunk) on this handle's grid with CUDA events on its
+ * stream, keeps the fastest, then resets the state (kv_reset). *best_ms: mean
+ * milliseconds per step of the choice (NULL allowed). Synchronising. */
+kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms);
 
 /* Number of kernel launches libkv has issued on this handle. */
 long long kv_launch_count(kv_handle *h);

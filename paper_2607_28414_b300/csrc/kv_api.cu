@@ -191,7 +191,7 @@ kv_status kv_destroy(kv_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_graphs(h);
     void *dev[] = {h->state[0], h->state[1], h->F, h->coef, h->S, h->g_dev, h->sens_dev,
-                   h->traces, h->ctrl, h->r, h->p[0], h->p[1], h->e, h->phi, h->b, h->scal,
+                   h->traces, h->ctrl, h->cgv, h->phi, h->b, h->scal,
                    h->partials, h->fstage, h->dtmin};
     for (void *p : dev)
         if (p) cudaFree(p);
@@ -237,6 +237,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     h->tx = 64;
     h->ty = 8;
     h->zc = 32;
+    h->ns_stages = 4;
     h->graph_steps = 32;
     cudaGetDevice(&h->device);
     if (stream) {
@@ -253,8 +254,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
         h->partials_len = 2 * g.x * g.y * g.z;
         if ((st = dalloc(h, &h->state[0], 6 * Np * es)) || (st = dalloc(h, &h->state[1], 6 * Np * es)) ||
             (st = dalloc(h, &h->F, 3 * Np * es)) || (st = dalloc(h, &h->fstage, 3 * Np * 4)) ||
-            (st = dalloc(h, &h->r, Np * es)) || (st = dalloc(h, &h->p[0], Np * es)) ||
-            (st = dalloc(h, &h->p[1], Np * es)) || (st = dalloc(h, &h->e, Np * es)) || (st = dalloc(h, &h->phi, Np * 8)) ||
+            (st = dalloc(h, &h->cgv, 4 * Np * es)) || (st = dalloc(h, &h->phi, Np * 8)) ||
             (st = dalloc(h, &h->b, Np * 8)) || (st = dalloc(h, &h->ctrl, kCtrlWords * 8)) ||
             (st = dalloc(h, &h->scal, kCgScalars * 8)) ||
             (st = dalloc(h, &h->partials, (size_t)h->partials_len * 8)) ||
@@ -262,15 +262,18 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
             goto fail;
         if (h->het && ((st = dalloc(h, &h->coef, 2 * Np * es)) || (st = dalloc(h, &h->S, Np * es))))
             goto fail;
+        h->p[0] = h->cgv;
+        h->r = (char *)h->cgv + Np * es;
+        h->p[1] = (char *)h->cgv + 2 * Np * es;
+        h->e = (char *)h->cgv + 3 * Np * es;
         if ((st = cuda_check(h, cudaMallocHost((void **)&h->ctrl_host, kCtrlWords * 8), "cudaMallocHost")) ||
             (st = cuda_check(h, cudaMallocHost((void **)&h->scal_host, kCgScalars * 8), "cudaMallocHost")))
             goto fail;
         cudaError_t e = cudaSuccess;
-        void *zero[] = {h->state[0], h->state[1], h->F, h->fstage, h->r, h->p[0], h->p[1], h->e,
-                        h->phi, h->b};
-        size_t zbytes[] = {6 * Np * es, 6 * Np * es, 3 * Np * es, 3 * Np * 4, Np * es, Np * es, Np * es,
-                           Np * es, Np * 8, Np * 8};
-        for (int q = 0; q < 10 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zero[q], 0, zbytes[q], h->stream);
+        void *zero[] = {h->state[0], h->state[1], h->F, h->fstage, h->cgv, h->phi, h->b};
+        size_t zbytes[] = {6 * Np * es, 6 * Np * es, 3 * Np * es, 3 * Np * 4, 4 * Np * es, Np * 8,
+                           Np * 8};
+        for (int q = 0; q < 7 && e == cudaSuccess; ++q) e = cudaMemsetAsync(zero[q], 0, zbytes[q], h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->ctrl, 0, kCtrlWords * 8, h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->scal, 0, kCgScalars * 8, h->stream);
         if (e == cudaSuccess && h->het) e = cudaMemsetAsync(h->coef, 0, 2 * Np * es, h->stream);
@@ -506,23 +509,91 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
     return cuda_check(h, e, "kv_read_field");
 }
 
-kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc) {
+kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, int ns) {
     if (!h) return KV_ERR_ARG;
     if (variant > 1 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
-        (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 16))
-        return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant or tile");
+        (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 16) || (ns > 0 && ns != 4 && ns != 6 && ns != 8))
+        return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant, tile or stage count");
     const int ntx = tx > 0 ? tx : h->tx, nty = ty > 0 ? ty : h->ty;
     if (ntx * nty / 4 < 64 || ntx * nty / 4 > 512)
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: tile %dx%d out of range", ntx, nty);
     cudaStreamSynchronize(h->stream);
+    const int old[5] = {h->variant, h->tx, h->ty, h->zc, h->ns_stages};
     if (variant >= 0) h->variant = variant;
     h->tx = ntx;
     h->ty = nty;
     if (zc > 0) h->zc = zc;
+    if (ns > 0) h->ns_stages = ns;
     h->tma_ready = 0;
     free_graphs(h);
-    if (h->precision == KV_FP32 && h->variant == 0) return step_prepare(h);
+    if (h->precision == KV_FP32 && h->variant == 0) {
+        kv_status st = step_prepare(h);
+        if (st != KV_OK) {  // keep the previous, valid configuration
+            h->variant = old[0];
+            h->tx = old[1];
+            h->ty = old[2];
+            h->zc = old[3];
+            h->ns_stages = old[4];
+            h->tma_ready = 0;
+            return st;
+        }
+    }
     return KV_OK;
+}
+
+kv_status kv_get_step_config(kv_handle *h, int *cfg) {
+    if (!h || !cfg) return KV_ERR_ARG;
+    cfg[0] = h->variant;
+    cfg[1] = h->tx;
+    cfg[2] = h->ty;
+    cfg[3] = h->zc;
+    cfg[4] = h->ns_stages;
+    return KV_OK;
+}
+
+kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
+    if (!h || trial_steps < 1) return set_error(h, KV_ERR_ARG, "kv_autotune_step: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    if (h->precision != KV_FP32) {
+        if (best_ms) *best_ms = 0.0;
+        return kv_reset(h);
+    }
+    struct Cand { int tx, ty, ns, zc; };
+    static const int tiles[][2] = {{32, 8}, {32, 16}, {64, 4}, {64, 8}, {64, 16}, {128, 2}, {128, 4}, {128, 8}};
+    static const int stages[] = {4, 6, 8};
+    static const int zcs[] = {16, 32, 64};
+    std::vector<Cand> cands;
+    for (auto &t : tiles)
+        for (int ns : stages)
+            for (int zc : zcs) cands.push_back({t[0], t[1], ns, zc});
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_error(h, KV_ERR_CUDA, "kv_autotune_step: cudaEventCreate failed");
+    const int saved[5] = {h->variant, h->tx, h->ty, h->zc, h->ns_stages};
+    double best = INFINITY;
+    Cand pick = {saved[1], saved[2], saved[4], saved[3]};
+    kv_status st = KV_OK;
+    for (const Cand &c : cands) {
+        if (kv_set_step_config(h, 0, c.tx, c.ty, c.zc, c.ns) != KV_OK) continue;  // e.g. too much smem
+        for (int i = 0; i < 2 && st == KV_OK; ++i) st = step_launch(h, i & 1);
+        cudaEventRecord(e0, h->stream);
+        for (int i = 0; i < trial_steps && st == KV_OK; ++i) st = step_launch(h, i & 1);
+        cudaEventRecord(e1, h->stream);
+        if (st != KV_OK) break;
+        if ((st = cuda_check(h, cudaEventSynchronize(e1), "kv_autotune_step")) != KV_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KV_OK) return st;
+    if ((st = kv_set_step_config(h, 0, pick.tx, pick.ty, pick.zc, pick.ns)) != KV_OK) return st;
+    if (best_ms) *best_ms = best / trial_steps;
+    return kv_reset(h);
 }
 
 }  // extern "C"

@@ -298,6 +298,322 @@ k_cg_upd(const T *__restrict__ p0, const T *__restrict__ p1, T *__restrict__ r, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged CG passes (FP32 handles).
+//
+// The CG vectors of a handle are one allocation [pA, r, pB, e] (4 x Np floats),
+// seen by TMA as a 4D tensor (x, y, z, field). A block owns a kCgTX x kCgTY
+// column and marches z; every plane it needs arrives by TMA into a ring of
+// kCgNS shared-memory stages, so several planes are in flight per block while
+// one is computed. Each thread computes four consecutive x nodes (a float4);
+// x neighbours come from warp shuffles, y and z neighbours from the staged
+// tiles. Per-node arithmetic is the same sequence as the plain kernels above.
+// Reductions: float-float per thread and across the block, double per block.
+// ---------------------------------------------------------------------------
+constexpr int kCgTX = 64, kCgTY = 8, kCgNS = 8, kCgTZc = 16;
+constexpr int kCgNT = kCgTX * kCgTY / 4;
+constexpr int kCgGX = kCgTX / 4;
+constexpr int kCgBXh = kCgTX + 8, kCgBYh = kCgTY + 2;
+constexpr int kCgHalo = kCgBXh * kCgBYh;                  // floats per halo field tile
+constexpr int kCgCtr = kCgTX * kCgTY;                     // floats per centre tile
+constexpr int kCgStageDir = 2 * kCgHalo;                  // (p_old, r) or (r, p_old)
+constexpr int kCgHaloPad = (kCgHalo + 31) / 32 * 32;
+constexpr int kCgStageUpd = kCgHaloPad + 2 * kCgCtr;      // p' halo, r and e centre
+static_assert((kCgStageDir * 4) % 128 == 0 && (kCgStageUpd * 4) % 128 == 0, "stage alignment");
+constexpr size_t kCgSmemDir = kCgNS * kCgStageDir * 4 + kCgNS * 8;
+constexpr size_t kCgSmemUpd = kCgNS * kCgStageUpd * 4 + kCgNS * 8;
+
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bh, float bl) {
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    const float t = __fadd_rn(__fadd_rn(e, lo), bl);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// Block total of a float-float accumulator, as a double in thread 0.
+__device__ __forceinline__ double block_total_ff(AccFF a) {
+    __shared__ float sh_hi[32], sh_lo[32];
+    float hi = a.hi, lo = a.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        ff_add(hi, lo, h2, l2);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        sh_hi[warp] = hi;
+        sh_lo[warp] = lo;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0) {
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < nw; ++w) ff_add(th, tl, sh_hi[w], sh_lo[w]);
+        tot = (double)th + (double)tl;
+    }
+    return tot;
+}
+
+// Per-block partial (thread 0's value) -> last block sums all partials.
+__device__ __forceinline__ bool finish_blocks(const CgParams &p, double tot, double &sum) {
+    __shared__ double sh[33];
+    __shared__ int s_last;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0) p.partials[bid] = tot;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t =
+            atomicAdd(reinterpret_cast<unsigned long long *>(&p.ctrl[kCgTicket]), 1ull);
+        s_last = (t == (unsigned long long)(p.nblocks - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < p.nblocks; b += blockDim.x) acc += __ldcg(&p.partials[b]);
+    sum = block_sum_d(acc, sh);
+    if (threadIdx.x == 0) p.ctrl[kCgTicket] = 0;
+    return true;
+}
+
+__device__ __forceinline__ void dir_finish(const CgParams &p, double pAp) {
+    p.scal[kPAP] = pAp;
+    if (!isfinite(pAp) || pAp <= 0.0)
+        p.ctrl[kCgStatus] = kCgBreakdown;
+    else
+        p.scal[kAlpha] = p.scal[kRR] / pAp;
+}
+
+__device__ __forceinline__ void upd_finish(const CgParams &p, double rr) {
+    const long long it = p.ctrl[kCgIters] + 1;
+    p.ctrl[kCgIters] = it;
+    p.scal[kRRLast] = rr;
+    const double bb = p.scal[kBB];
+    const double tol = p.scal[kTol], repl = p.scal[kInner];
+    if (!isfinite(rr)) {
+        p.ctrl[kCgStatus] = kCgNonfinite;
+    } else if (rr <= 0.25 * tol * tol * bb || rr <= repl * repl * p.scal[kRR0] ||
+               it >= p.ctrl[kCgMaxIter]) {
+        p.ctrl[kCgStatus] = kCgNeedTrue;
+    } else {
+        p.scal[kBeta] = rr / p.scal[kRR];
+        p.scal[kRR] = rr;
+    }
+}
+
+struct CgTile {
+    int x0, y0, k0, k1, kb, gx, gy;
+    __device__ CgTile(const CgParams &p) {
+        x0 = blockIdx.x * kCgTX;
+        y0 = 1 + blockIdx.y * kCgTY;
+        k0 = 1 + blockIdx.z * p.zc;
+        k1 = min(k0 + p.zc, p.nz - 1);
+        kb = k0 - 1;
+        gx = threadIdx.x % kCgGX;
+        gy = threadIdx.x / kCgGX;
+    }
+    __device__ int slot(int q) const { return (q - kb) % kCgNS; }
+    __device__ uint32_t parity(int q) const { return ((q - kb) / kCgNS) & 1; }
+};
+
+__device__ __forceinline__ float4 ld4(const float *a) { return *reinterpret_cast<const float4 *>(a); }
+
+// Drain every stage (bounded) after a wait gave up, then flag the timeout.
+__device__ __forceinline__ void ring_drain(const CgParams &p, const CgTile &t, uint32_t bar0,
+                                           bool ok) {
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
+        const int rel_max = t.k1 - t.kb;
+        for (int s = 0; s < kCgNS && s <= rel_max; ++s) {
+            const int rel_last = s + ((rel_max - s) / kCgNS) * kCgNS;
+            mbar_wait_bounded(bar0 + 8 * s, (rel_last / kCgNS) & 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCgNT)
+k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv, CgParams p) {
+    if (__ldcg(&p.ctrl[kCgStatus]) != kCgRunning) return;
+    const int par = (int)(__ldcg(&p.ctrl[kCgIters]) & 1);
+    const int ps = par, rs = 1 - par;                 // smem slots of p_old and r
+    float *__restrict__ pnew = cgv + (par ? 0 : 2) * p.Np;
+    const float beta = (float)__ldcg(&p.scal[kBeta]);
+    const float inv = (float)p.inv_dx2;
+    extern __shared__ __align__(128) float smem[];
+    const uint32_t bar0 = smem_u32(smem + kCgNS * kCgStageDir);
+    const CgTile t(p);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kCgNS; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int q) {
+        const uint32_t bar = bar0 + 8 * t.slot(q);
+        mbar_expect_tx(bar, kCgStageDir * 4);
+        tma_load_4d(smem_u32(smem + t.slot(q) * kCgStageDir), &tm_h2, t.x0 - 4, t.y0 - 1, q, par, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int q = t.kb; q <= min(t.k1, t.kb + kCgNS - 1); ++q) issue(q);
+
+    AccFF acc;
+    bool ok = true;
+    const int y = t.y0 + t.gy, x = t.x0 + 4 * t.gx;
+    const bool row_ok = (y <= p.ny - 2) && (x < p.px);
+    const bool m0 = x >= 1 && x <= p.nx - 2, m1 = x + 1 <= p.nx - 2, m2 = x + 2 <= p.nx - 2,
+               m3 = x + 3 <= p.nx - 2;
+    const int o = (t.gy + 1) * kCgBXh + 4 + 4 * t.gx;
+    const long long sz = (long long)p.px * p.ny;
+    for (int k = t.k0; k < t.k1; ++k) {
+        if (k == t.k0) {
+            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k - 1), t.parity(k - 1));
+            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k), t.parity(k));
+        }
+        ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k + 1), t.parity(k + 1));
+        const float *sc = smem + t.slot(k) * kCgStageDir;
+        const float *sm = smem + t.slot(k - 1) * kCgStageDir;
+        const float *sp = smem + t.slot(k + 1) * kCgStageDir;
+        auto pn4 = [&](const float *st, int off) {
+            const float4 pv = ld4(st + ps * kCgHalo + off), rv = ld4(st + rs * kCgHalo + off);
+            return make_float4(kv_fma(beta, pv.x, rv.x), kv_fma(beta, pv.y, rv.y),
+                               kv_fma(beta, pv.z, rv.z), kv_fma(beta, pv.w, rv.w));
+        };
+        const float4 c = pn4(sc, o), ym = pn4(sc, o - kCgBXh), yp = pn4(sc, o + kCgBXh);
+        const float4 zm = pn4(sm, o), zp = pn4(sp, o);
+        float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+        if (t.gx == 0) left = kv_fma(beta, sc[ps * kCgHalo + o - 1], sc[rs * kCgHalo + o - 1]);
+        if (t.gx == kCgGX - 1) right = kv_fma(beta, sc[ps * kCgHalo + o + 4], sc[rs * kCgHalo + o + 4]);
+        float4 sum;
+        sum.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+        sum.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+        sum.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+        sum.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+        if (row_ok) {
+            float4 out = c;
+            float4 Ap;
+            Ap.x = kv_fma(6.f, c.x, -sum.x) * inv;
+            Ap.y = kv_fma(6.f, c.y, -sum.y) * inv;
+            Ap.z = kv_fma(6.f, c.z, -sum.z) * inv;
+            Ap.w = kv_fma(6.f, c.w, -sum.w) * inv;
+            if (m0) acc.add_prod(c.x, Ap.x); else out.x = 0.f;
+            if (m1) acc.add_prod(c.y, Ap.y); else out.y = 0.f;
+            if (m2) acc.add_prod(c.z, Ap.z); else out.z = 0.f;
+            if (m3) acc.add_prod(c.w, Ap.w); else out.w = 0.f;
+            *reinterpret_cast<float4 *>(pnew + k * sz + (long long)y * p.px + x) = out;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int q = k - 1 + kCgNS;
+            if (q <= t.k1) {
+                fence_proxy_async();
+                issue(q);
+            }
+        }
+    }
+    ring_drain(p, t, bar0, ok);
+    const double tot = block_total_ff(acc);
+    double sum;
+    if (finish_blocks(p, tot, sum) && threadIdx.x == 0) dir_finish(p, sum);
+}
+
+__global__ void __launch_bounds__(kCgNT)
+k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ CUtensorMap tm_c1,
+             float *__restrict__ cgv, CgParams p) {
+    if (__ldcg(&p.ctrl[kCgStatus]) != kCgRunning) return;
+    const int par = (int)(__ldcg(&p.ctrl[kCgIters]) & 1);
+    const int pf = par ? 0 : 2;                      // field of p' (written by k_cg_dir_tma)
+    const float alpha = (float)__ldcg(&p.scal[kAlpha]);
+    const float inv = (float)p.inv_dx2;
+    float *__restrict__ rg = cgv + p.Np;
+    float *__restrict__ eg = cgv + 3 * p.Np;
+    extern __shared__ __align__(128) float smem[];
+    const uint32_t bar0 = smem_u32(smem + kCgNS * kCgStageUpd);
+    const CgTile t(p);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kCgNS; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int q) {
+        const uint32_t bar = bar0 + 8 * t.slot(q);
+        float *st = smem + t.slot(q) * kCgStageUpd;
+        const bool centre = q >= t.k0 && q < t.k1;
+        mbar_expect_tx(bar, (kCgHalo + (centre ? 2 * kCgCtr : 0)) * 4);
+        tma_load_4d(smem_u32(st), &tm_h1, t.x0 - 4, t.y0 - 1, q, pf, bar);
+        if (centre) {
+            tma_load_4d(smem_u32(st + kCgHaloPad), &tm_c1, t.x0, t.y0, q, 1, bar);
+            tma_load_4d(smem_u32(st + kCgHaloPad + kCgCtr), &tm_c1, t.x0, t.y0, q, 3, bar);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int q = t.kb; q <= min(t.k1, t.kb + kCgNS - 1); ++q) issue(q);
+
+    AccFF acc;
+    bool ok = true;
+    const int y = t.y0 + t.gy, x = t.x0 + 4 * t.gx;
+    const bool row_ok = (y <= p.ny - 2) && (x < p.px);
+    const bool m0 = x >= 1 && x <= p.nx - 2, m1 = x + 1 <= p.nx - 2, m2 = x + 2 <= p.nx - 2,
+               m3 = x + 3 <= p.nx - 2;
+    const int o = (t.gy + 1) * kCgBXh + 4 + 4 * t.gx;
+    const int oc = t.gy * kCgTX + 4 * t.gx;
+    const long long sz = (long long)p.px * p.ny;
+    for (int k = t.k0; k < t.k1; ++k) {
+        if (k == t.k0) {
+            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k - 1), t.parity(k - 1));
+            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k), t.parity(k));
+        }
+        ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k + 1), t.parity(k + 1));
+        const float *sc = smem + t.slot(k) * kCgStageUpd;
+        const float *sm = smem + t.slot(k - 1) * kCgStageUpd;
+        const float *sp = smem + t.slot(k + 1) * kCgStageUpd;
+        const float4 c = ld4(sc + o), ym = ld4(sc + o - kCgBXh), yp = ld4(sc + o + kCgBXh);
+        const float4 zm = ld4(sm + o), zp = ld4(sp + o);
+        float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+        if (t.gx == 0) left = sc[o - 1];
+        if (t.gx == kCgGX - 1) right = sc[o + 4];
+        float4 sum;
+        sum.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+        sum.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+        sum.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+        sum.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+        if (row_ok) {
+            const float4 r = ld4(sc + kCgHaloPad + oc), e = ld4(sc + kCgHaloPad + kCgCtr + oc);
+            float4 rn = r, en = e;
+            auto node = [&](bool m, float cv, float sv, float rv, float ev, float &ro, float &eo) {
+                if (!m) return;
+                const float Ap = kv_fma(6.f, cv, -sv) * inv;
+                eo = kv_fma(alpha, cv, ev);
+                ro = kv_fma(-alpha, Ap, rv);
+                acc.add_prod(ro, ro);
+            };
+            node(m0, c.x, sum.x, r.x, e.x, rn.x, en.x);
+            node(m1, c.y, sum.y, r.y, e.y, rn.y, en.y);
+            node(m2, c.z, sum.z, r.z, e.z, rn.z, en.z);
+            node(m3, c.w, sum.w, r.w, e.w, rn.w, en.w);
+            const long long g = k * sz + (long long)y * p.px + x;
+            *reinterpret_cast<float4 *>(rg + g) = rn;
+            *reinterpret_cast<float4 *>(eg + g) = en;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int q = k - 1 + kCgNS;
+            if (q <= t.k1) {
+                fence_proxy_async();
+                issue(q);
+            }
+        }
+    }
+    ring_drain(p, t, bar0, ok);
+    const double tot = block_total_ff(acc);
+    double sum;
+    if (finish_blocks(p, tot, sum) && threadIdx.x == 0) upd_finish(p, sum);
+}
+
 // f_S0 = f - D+ phi on every node (phi = 0 beyond the grid); F = S f_S0.
 template <typename T>
 __global__ void __launch_bounds__(kCgBX *kCgBY)
@@ -408,6 +724,23 @@ static kv_status sync_read(kv_handle *h) {
     return cuda_check(h, e, "projection poll");
 }
 
+// TMA views of the CG vectors and the kernels' shared-memory limits.
+static kv_status cg_tma_prepare(kv_handle *h) {
+    if (h->cg_tma_ready) return KV_OK;
+    kv_status st;
+    if ((st = encode_tensor_4d(h, &h->tm_cg_h2, h->cgv, 4, kCgBXh, kCgBYh, 2)) != KV_OK) return st;
+    if ((st = encode_tensor_4d(h, &h->tm_cg_h1, h->cgv, 4, kCgBXh, kCgBYh, 1)) != KV_OK) return st;
+    if ((st = encode_tensor_4d(h, &h->tm_cg_c1, h->cgv, 4, kCgTX, kCgTY, 1)) != KV_OK) return st;
+    cudaError_t e = cudaFuncSetAttribute(k_cg_dir_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCgSmemDir);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cg_upd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kCgSmemUpd);
+    if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(CG)");
+    h->cg_tma_ready = 1;
+    return KV_OK;
+}
+
 template <typename T>
 static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out,
                            kv_cg_stats *st) {
@@ -418,6 +751,17 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out
     CgParams p = cg_params(h, grid, zc);
     cudaStream_t s = h->stream;
     cudaError_t e;
+    // FP32: the two CG passes run as TMA-staged z-march kernels
+    const bool use_tma = (h->precision == KV_FP32);
+    const dim3 tgrid((h->px + kCgTX - 1) / kCgTX, (h->ny - 2 + kCgTY - 1) / kCgTY,
+                     (h->nz - 2 + kCgTZc - 1) / kCgTZc);
+    CgParams pt = cg_params(h, tgrid, kCgTZc);
+    if (use_tma) {
+        kv_status ts = cg_tma_prepare(h);
+        if (ts != KV_OK) return ts;
+        if ((long long)tgrid.x * tgrid.y * tgrid.z > h->partials_len)
+            return set_error(h, KV_ERR_ARG, "CG partials buffer too small");
+    }
     // reset the CG vectors and control words
     e = cudaMemsetAsync(h->r, 0, h->Np * sizeof(T), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p[0], 0, h->Np * sizeof(T), s);
@@ -463,8 +807,14 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out
             } else if (c == kCgRunning) {
                 T *p0 = (T *)h->p[0], *p1 = (T *)h->p[1];
                 for (int it = 0; it < chunk; ++it) {
-                    k_cg_dir<T><<<grid, nt, 0, s>>>((const T *)h->r, p0, p1, p);
-                    k_cg_upd<T><<<grid, nt, 0, s>>>(p0, p1, (T *)h->r, (T *)h->e, p);
+                    if (use_tma) {
+                        k_cg_dir_tma<<<tgrid, kCgNT, kCgSmemDir, s>>>(h->tm_cg_h2, (float *)h->cgv, pt);
+                        k_cg_upd_tma<<<tgrid, kCgNT, kCgSmemUpd, s>>>(h->tm_cg_h1, h->tm_cg_c1,
+                                                                      (float *)h->cgv, pt);
+                    } else {
+                        k_cg_dir<T><<<grid, nt, 0, s>>>((const T *)h->r, p0, p1, p);
+                        k_cg_upd<T><<<grid, nt, 0, s>>>(p0, p1, (T *)h->r, (T *)h->e, p);
+                    }
                     h->launches += 2;
                 }
             } else {
@@ -485,6 +835,10 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out
     h->launches++;
     if ((ks = sync_read(h)) != KV_OK) return ks;
     h->have_force = 1;
+    if (h->ctrl_host[kErrFlags] & 1) {
+        h->sticky = 1;
+        return set_error(h, KV_ERR_TIMEOUT, "a bounded device wait timed out in a CG kernel");
+    }
     if (st) {
         st->iters = (int)h->ctrl_host[kCgIters];
         st->refinements = (int)std::max(0ll, h->ctrl_host[kCgRefine] - 1);

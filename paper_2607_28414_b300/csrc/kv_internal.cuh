@@ -119,9 +119,12 @@ struct kv_handle {
     long long steps_host;
 
     // projection
-    void *r;               // [Np] residual (float or double)
+    void *cgv;             // [4][Np] CG vectors in one allocation: p[0], r, p[1], e
+    void *r;               // [Np] residual (float or double), inside cgv
     void *p[2];            // [Np] search direction, ping-pong by iteration parity
     void *e;               // [Np] correction accumulated since the last replacement
+    CUtensorMap tm_cg_h2, tm_cg_h1, tm_cg_c1;  // TMA views of cgv (FP32)
+    int cg_tma_ready;
     double *phi;           // [Np]
     double *b;             // [Np] right-hand side
     double *scal;          // kv::kCgScalars
@@ -133,8 +136,8 @@ struct kv_handle {
     double *scal_host;     // pinned mirror of the scalars
 
     // FP32 step kernel configuration and TMA descriptors
-    int variant, tx, ty, zc;
-    CUtensorMap tm_state[2], tm_coef, tm_F;
+    int variant, tx, ty, zc, ns_stages;
+    CUtensorMap tm_state[2], tm_coef;
     int tma_ready;
 
     // CUDA graph of a block of steps (one per starting buffer)
@@ -154,6 +157,10 @@ kv_status cuda_check(kv_handle *h, cudaError_t e, const char *what);
 // Step kernels (kv_step.cu)
 kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attributes
 kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
+
+// 4D float32 tensor map over [fields][nz][ny][px] with box (bx, by, 1, fields_box)
+kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by,
+                           int fields_box);
 
 // Projection kernels (kv_cg.cu)
 kv_status project(kv_handle *h, double tol, int max_iter, float *fs_out, kv_cg_stats *st);
@@ -229,3 +236,55 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh /* >= 33 doub
     __syncthreads();
     return r;
 }
+
+namespace kv {
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier and TMA (sm_90+ forms, valid on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 SM clocks (about a second at 2 GHz).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+}  // namespace kv

@@ -22,54 +22,6 @@
 namespace kv {
 
 // ---------------------------------------------------------------------------
-// PTX helpers: mbarrier and TMA (sm_90+ forms, valid on sm_103a)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after ~2^31 SM clocks (about a second at 2 GHz).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *tm, int c0, int c1,
-                                            int c2, int c3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
-
-// ---------------------------------------------------------------------------
 // Epilogue shared by the step kernels: the last block to finish records
 // u^{n+1} at the sensors and advances the step counter.
 // ---------------------------------------------------------------------------
@@ -147,9 +99,10 @@ k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict_
 // plane of all six state fields, with a 4-node x halo (keeps the TMA x start
 // 16-byte aligned) and a 1-node y halo, arrives in one 4D TMA box
 // (TX+8, TY+2, 1, 6) into a ring of NS shared-memory stages; the coefficient
-// (A', B') and projected-force (3 components) tiles of the centre plane ride in
-// the same stage. Planes k-1, k, k+1 are resident while plane k is computed and
-// up to NS-3 further planes are in flight. Each thread computes four
+// (A', B') tile of the centre plane rides in the same stage. Planes k-1, k, k+1
+// are resident while plane k is computed and NS-3 further planes are in flight.
+// The projected force (needed only on the few force steps) is read directly
+// from global memory as float4. Each thread computes four
 // consecutive x nodes (one float4) of one row; its x neighbours come from warp
 // shuffles (row edges from shared memory). Outputs go straight to global
 // memory as float4 stores.
@@ -163,18 +116,14 @@ struct TmaTile {
     static constexpr int FIELD = BX * BY;
     static constexpr int STATE = 6 * FIELD;
     static constexpr int COEF = HET ? 2 * TX * TY : 0;
-    static constexpr int FRC = 3 * TX * TY;
-    static constexpr int STAGE = (STATE + COEF + FRC + 31) / 32 * 32;  // floats, 128 B multiple
+    static constexpr int STAGE = (STATE + COEF + 31) / 32 * 32;  // floats, 128 B multiple
 };
 
-constexpr int kStages = 4;
-
-template <int TX, int TY, bool HET>
+template <int TX, int TY, int NS, bool HET>
 __global__ void __launch_bounds__(TX *TY / 4)
 k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
-           const __grid_constant__ CUtensorMap tm_F, float *__restrict__ out, StepParams p) {
+           const float *__restrict__ F, float *__restrict__ out, StepParams p) {
     using TT = TmaTile<TX, TY, HET>;
-    constexpr int NS = kStages;
     extern __shared__ __align__(128) float smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * TT::STAGE);
 
@@ -200,14 +149,11 @@ k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
         const int s = (q - kb) % NS;
         float *st = smem + s * TT::STAGE;
         const uint32_t bar = bar0 + 8 * s;
-        const bool centre = (q >= k0 && q < k1);
-        const bool wc = centre && HET;
-        const bool wf = centre && force;
-        const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0) + (wf ? TT::FRC * 4 : 0);
+        const bool wc = HET && (q >= k0 && q < k1);
+        const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0);
         mbar_expect_tx(bar, bytes);
         tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 1, q, 0, bar);
         if (wc) tma_load_4d(smem_u32(st + TT::STATE), &tm_coef, x0, y0, q, 0, bar);
-        if (wf) tma_load_4d(smem_u32(st + TT::STATE + TT::COEF), &tm_F, x0, y0, q, 0, bar);
     };
 
     if (tid == 0) {
@@ -272,9 +218,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
                 float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (force)
-                    F4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + TT::COEF +
-                                                           comp * TX * TY + gy * TX + 4 * gx);
+                if (force)  // force steps are few: the projected force is read directly
+                    F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
                 const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
                 float4 uo, dn;
                 kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g, F4.x, uo.x, dn.x);
@@ -375,46 +320,60 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn(kv_handle *h) {
     return fn;
 }
 
-static kv_status encode_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by) {
+kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by,
+                           int fields_box) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn(h);
     if (!fn) return KV_ERR_CUDA;
     cuuint64_t dims[4] = {(cuuint64_t)h->px, (cuuint64_t)h->ny, (cuuint64_t)h->nz,
                           (cuuint64_t)fields};
     cuuint64_t strides[3] = {(cuuint64_t)h->px * 4, (cuuint64_t)h->px * h->ny * 4,
                              (cuuint64_t)h->Np * 4};
-    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)fields};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)fields_box};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return set_error(h, KV_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) box %dx%dx1x%d", (int)r,
-                         bx, by, fields);
+                         bx, by, fields_box);
     return KV_OK;
 }
 
-typedef void (*TmaKernel)(const CUtensorMap, const CUtensorMap, const CUtensorMap, float *,
-                          StepParams);
+typedef void (*TmaKernel)(const CUtensorMap, const CUtensorMap, const float *, float *, StepParams);
 
-template <int TX, int TY>
-static bool pick(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
-    if (tx != TX || ty != TY) return false;
+template <int TX, int TY, int NS>
+static bool pick(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (tx != TX || ty != TY || ns != NS) return false;
     if (het) {
-        *k = k_step_tma<TX, TY, true>;
-        *smem = kStages * TmaTile<TX, TY, true>::STAGE * 4 + kStages * 8;
+        *k = k_step_tma<TX, TY, NS, true>;
+        *smem = NS * TmaTile<TX, TY, true>::STAGE * 4 + NS * 8;
     } else {
-        *k = k_step_tma<TX, TY, false>;
-        *smem = kStages * TmaTile<TX, TY, false>::STAGE * 4 + kStages * 8;
+        *k = k_step_tma<TX, TY, NS, false>;
+        *smem = NS * TmaTile<TX, TY, false>::STAGE * 4 + NS * 8;
     }
     *nt = TX * TY / 4;
     return true;
 }
 
-static bool tma_kernel_for(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
-    return pick<32, 8>(tx, ty, het, k, smem, nt) || pick<32, 16>(tx, ty, het, k, smem, nt) ||
-           pick<64, 4>(tx, ty, het, k, smem, nt) || pick<64, 8>(tx, ty, het, k, smem, nt) ||
-           pick<64, 16>(tx, ty, het, k, smem, nt) || pick<128, 2>(tx, ty, het, k, smem, nt) ||
-           pick<128, 4>(tx, ty, het, k, smem, nt) || pick<128, 8>(tx, ty, het, k, smem, nt);
+template <int NS>
+static bool pick_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    return pick<32, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<32, 16, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<64, 4, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<64, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<64, 16, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<128, 2, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<128, 4, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick<128, 8, NS>(tx, ty, NS, het, k, smem, nt);
+}
+
+static bool tma_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    switch (ns) {
+        case 4: return pick_tile<4>(tx, ty, het, k, smem, nt);
+        case 6: return pick_tile<6>(tx, ty, het, k, smem, nt);
+        case 8: return pick_tile<8>(tx, ty, het, k, smem, nt);
+        default: return false;
+    }
 }
 
 kv_status step_prepare(kv_handle *h) {
@@ -423,18 +382,19 @@ kv_status step_prepare(kv_handle *h) {
     TmaKernel k;
     size_t smem;
     int nt;
-    if (!tma_kernel_for(h->tx, h->ty, h->het != 0, &k, &smem, &nt))
-        return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d", h->tx, h->ty);
+    if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
+        return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d with %d stages", h->tx,
+                         h->ty, h->ns_stages);
     if (smem > 227 * 1024)
-        return set_error(h, KV_ERR_ARG, "tile %dx%d needs %zu bytes of shared memory", h->tx, h->ty,
-                         smem);
+        return set_error(h, KV_ERR_ARG, "tile %dx%d with %d stages needs %zu bytes of shared memory",
+                         h->tx, h->ty, h->ns_stages, smem);
     kv_status st;
     for (int b = 0; b < 2; ++b)
-        if ((st = encode_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 2)) != KV_OK)
+        if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 2, 6)) != KV_OK)
             return st;
-    if (h->het && (st = encode_4d(h, &h->tm_coef, h->coef, 2, h->tx, h->ty)) != KV_OK) return st;
+    if (h->het && (st = encode_tensor_4d(h, &h->tm_coef, h->coef, 2, h->tx, h->ty, 2)) != KV_OK)
+        return st;
     if (!h->het) h->tm_coef = h->tm_state[0];  // unused placeholder
-    if ((st = encode_4d(h, &h->tm_F, h->F, 3, h->tx, h->ty)) != KV_OK) return st;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(step)");
     h->tma_ready = 1;
@@ -473,11 +433,12 @@ kv_status step_launch(kv_handle *h, int from) {
         TmaKernel k;
         size_t smem;
         int nt;
-        tma_kernel_for(h->tx, h->ty, h->het != 0, &k, &smem, &nt);
+        tma_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt);
         dim3 grid((h->px + h->tx - 1) / h->tx, (h->ny - 2 + h->ty - 1) / h->ty,
                   (h->nz - 2 + h->zc - 1) / h->zc);
         StepParams p = make_params(h, grid.x * grid.y * grid.z);
-        k<<<grid, nt, smem, h->stream>>>(h->tm_state[from], h->tm_coef, h->tm_F, (float *)out, p);
+        k<<<grid, nt, smem, h->stream>>>(h->tm_state[from], h->tm_coef, (const float *)h->F,
+                                         (float *)out, p);
     } else {
         dim3 grid((h->nx + 127) / 128, h->ny - 2, h->nz - 2);
         StepParams p = make_params(h, grid.x * grid.y * grid.z);

@@ -90,7 +90,9 @@ def lib():
         L.kv_read_traces.argtypes = [H, vp, i, ctypes.POINTER(i)]
         L.kv_read_field.argtypes = [H, i, i, vp, i]
         L.kv_sync.argtypes = [H]
-        L.kv_set_step_config.argtypes = [H, i, i, i, i]
+        L.kv_set_step_config.argtypes = [H, i, i, i, i, i]
+        L.kv_get_step_config.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
+        L.kv_autotune_step.argtypes = [H, i, ctypes.POINTER(d)]
         L.kv_launch_count.argtypes = [H]
         L.kv_launch_count.restype = ctypes.c_longlong
         L.kv_destroy.argtypes = [H]
@@ -99,7 +101,8 @@ def lib():
         for name in ("kv_stable_dt", "kv_create", "kv_set_medium", "kv_set_envelope",
                      "kv_set_sensors", "kv_reset", "kv_set_initial_velocity", "kv_project_force",
                      "kv_clear_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
-                     "kv_set_step_config", "kv_destroy", "kv_project_force_noalloc"):
+                     "kv_set_step_config", "kv_get_step_config", "kv_autotune_step",
+                     "kv_destroy", "kv_project_force_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -269,8 +272,20 @@ def kv_sync(h):
     _check(lib().kv_sync(h), h)
 
 
-def kv_set_step_config(h, variant=-1, tx=0, ty=0, zc=0):
-    _check(lib().kv_set_step_config(h, int(variant), int(tx), int(ty), int(zc)), h)
+def kv_set_step_config(h, variant=-1, tx=0, ty=0, zc=0, ns=0):
+    _check(lib().kv_set_step_config(h, int(variant), int(tx), int(ty), int(zc), int(ns)), h)
+
+
+def kv_get_step_config(h):
+    cfg = (ctypes.c_int * 5)()
+    _check(lib().kv_get_step_config(h, cfg), h)
+    return dict(zip(("variant", "tx", "ty", "zc", "ns"), list(cfg)))
+
+
+def kv_autotune_step(h, trial_steps=8):
+    best = ctypes.c_double()
+    _check(lib().kv_autotune_step(h, int(trial_steps), ctypes.byref(best)), h)
+    return best.value
 
 
 def kv_launch_count(h):

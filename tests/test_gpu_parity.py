@@ -105,11 +105,37 @@ def test_tma_tiles_match_plain_kernel_bitwise(device, het):
     v0 = inputs.curl_gaussian_velocity(w.nx, w.ny, w.nz, w.dx, sigma=1e-3, envelope="xyz")
     ref_tr, ref_f = run_variant(w, {"variant": 1}, 60, v0)
     assert np.abs(ref_f).max() > 0
+    ran = 0
     for tx, ty in TILES:
-        for zc in (5, 64):
-            tr, f = run_variant(w, {"variant": 0, "tx": tx, "ty": ty, "zc": zc}, 60, v0)
-            assert np.array_equal(tr, ref_tr), (tx, ty, zc)
-            assert np.array_equal(f, ref_f), (tx, ty, zc)
+        for ns in (4, 6, 8):
+            for zc in (5, 64):
+                try:
+                    tr, f = run_variant(w, {"variant": 0, "tx": tx, "ty": ty, "zc": zc, "ns": ns}, 60, v0)
+                except kv.KvError as e:
+                    assert e.status == kv.KV_ERR_ARG and "shared memory" in str(e)
+                    continue
+                ran += 1
+                assert np.array_equal(tr, ref_tr), (tx, ty, ns, zc)
+                assert np.array_equal(f, ref_f), (tx, ty, ns, zc)
+    assert ran >= 36
+
+
+def test_autotuner_picks_a_valid_config_and_resets(device):
+    w = ragged_workload()
+    s = Solver(w, n_steps=20)
+    s.project()
+    ms = kv.kv_autotune_step(s.h, 4)
+    cfg = kv.kv_get_step_config(s.h)
+    assert ms > 0 and cfg["variant"] == 0 and cfg["ns"] in (4, 6, 8)
+    assert kv.kv_steps_taken(s.h) == 0
+    s.step()
+    tr = s.read_traces().cpu().numpy().copy()
+    s.close()
+    ref = Solver(w, n_steps=20, step_config={"variant": 1})
+    ref.project()
+    ref.step()
+    assert np.array_equal(tr, ref.read_traces().cpu().numpy())
+    ref.close()
 
 
 def test_graph_replay_matches_direct_launches(device):
@@ -368,6 +394,9 @@ def test_invalid_arguments_on_gpu(device):
         kv.kv_set_sensors(s.h, [[w.nx, 0, 0]], 5)
     with pytest.raises(kv.KvError):
         kv.kv_set_step_config(s.h, 0, 48, 8, 4)
+    with pytest.raises(kv.KvError):
+        kv.kv_set_step_config(s.h, 0, 64, 16, 4, 8)  # stages beyond a block's shared memory
+    assert kv.kv_get_step_config(s.h)["tx"] == 64
     with pytest.raises(kv.KvError) as e:
         kv.kv_set_medium(s.h, 4e3, 1000.0, 0.0)  # homogeneous into a heterogeneous handle
     assert e.value.status == kv.KV_ERR_ARG

@@ -42,18 +42,20 @@ def test_noalloc_projection_matches_handle_projection(device):
     force = (force[2] * 0.3, force[1], force[2])
     w = inputs.Workload("noalloc_61x47x53", *n, 2e-4, G, rho, eta, force, 2e-4, 1,
                         np.zeros((1, 3), np.int32), 1e-8)
-    ref, st_ref = reference_fs(w, device, 1e-8)
-    assert st_ref["rel_res_true"] < 1e-8
+    # both solves to 1e-10, so that two correct solutions agree well inside the
+    # f_S tolerance whatever their reduction order
+    ref, st_ref = reference_fs(w, device, 1e-10)
+    assert st_ref["rel_res_true"] < 1e-10
     f = [torch.from_numpy(a).to(device) for a in w.force]
     scale = np.abs(ref).max()
     for call in range(2):
         out = torch.full((3, w.nz, w.ny, w.nx), float("nan"), dtype=torch.float32, device=device)
-        st = kv.kv_project_force_noalloc(w.nx, w.ny, w.nz, w.dx, *f, 1e-8, out)
+        st = kv.kv_project_force_noalloc(w.nx, w.ny, w.nz, w.dx, *f, 1e-10, out)
         got = out.cpu().numpy()
         assert np.isfinite(got).all(), call
-        assert st["status"] == kv.KV_OK and st["rel_res_true"] < 1e-8, (call, st)
+        assert st["status"] == kv.KV_OK and st["rel_res_true"] < 1e-10, (call, st)
         assert np.abs(got - ref).max() <= FS_REL_TOL * scale, call
-        assert st["iters"] == st_ref["iters"], (call, st, st_ref)
+        assert abs(st["iters"] - st_ref["iters"]) <= 2, (call, st, st_ref)
 
 
 def test_noalloc_rejects_grids_beyond_the_limit(device):
