@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="inclusions256",
+                    choices=["inclusions256", "bone512", "sweep"],
+                    help="inclusions256: 256^3 inclusions, 2000 steps (the headline); bone512: "
+                         "512x512x384 bone shell, 5000 steps; sweep: 26 homogeneous cases on "
+                         "uneven grids, 1000 batched steps")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
     ap.add_argument("--step-config", default=None,
@@ -118,8 +123,10 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def workload(grid, n_steps):
+def workload(grid, n_steps, kind="inclusions256"):
     from paper_2607_28414_b300 import inputs
+    if kind == "bone512":
+        return inputs.bone_shell(n_steps=n_steps if n_steps != N_TIME_STEPS else 5000)
     return inputs.heterogeneous_inclusions(n=grid, n_steps=n_steps)
 
 
@@ -148,7 +155,7 @@ def run_reference(args, rank, world):
         return
     from paper_2607_28414_b300 import inputs
     import oracle as orc
-    w = workload(args.grid, args.time_steps)
+    w = workload(args.grid, args.time_steps, args.workload)
     dt = 0.5 * orc.stable_dt(w.G, w.rho, w.eta, w.dx)
     cg_iters = 400
     vals = []
@@ -158,7 +165,7 @@ def run_reference(args, rank, world):
             vals.append(v)
     value = float(np.mean(vals))
     ms = w.n_cells * w.n_steps / (value * 1e9) * 1e3
-    line = {"metric": "KV-FDTD Gcell-updates/s (projection + 2000 steps)", "value": value,
+    line = {"metric": f"KV-FDTD Gcell-updates/s (projection + {w.n_steps} steps)", "value": value,
             "unit": "Gcell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -172,6 +179,100 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, rank, world):
+    """Parameter sweep: 26 homogeneous cases (16 viscosities on 128x128x192, 10
+    moduli on cubes of 96..224 nodes), one projection per distinct grid shared
+    by the other cases on it, then 1000 steps of all cases in one launch per
+    step (CUDA graph). A pass = reset, 11 projections + 15 shares, 1000
+    batched steps, traces read."""
+    import torch
+    from paper_2607_28414_b300 import inputs, kv
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device)
+    torch.cuda.set_stream(stream)
+    n_steps = args.time_steps if args.time_steps != N_TIME_STEPS else 1000
+    cases = inputs.sweep_cases(n_steps=n_steps)
+    hs, forces, owner = [], [], {}
+    for w in cases:
+        dt = 0.5 * kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, w.G, w.rho, w.eta)
+        h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, w.G, w.rho, w.eta, stream=stream.cuda_stream)
+        kv.kv_set_envelope(h, inputs.push_envelope(n_steps, dt, w.t_push))
+        kv.kv_set_sensors(h, w.sensors, n_steps)
+        hs.append(h)
+        forces.append([torch.from_numpy(a).to(device) for a in w.force])
+    b = kv.kv_batch_create(hs)
+    N = sum(w.n_cells for w in cases)
+
+    def one_pass():
+        grids = {}
+        for i, (w, h) in enumerate(zip(cases, hs)):
+            kv.kv_reset(h)
+            key = (w.nx, w.ny, w.nz)
+            if key in grids:
+                kv.kv_share_force(h, hs[grids[key]])
+            else:
+                kv.kv_project_force(h, *forces[i], w.tol)
+                grids[key] = i
+        kv.kv_batch_step(b, n_steps)
+        out = torch.empty((n_steps, 256, 3), dtype=torch.float32, device=device)
+        for w, h in zip(cases, hs):
+            kv.kv_read_traces(h, out[:, :len(w.sensors)])
+        return len(grids)
+
+    # projections once so the autotuner runs forced steps too
+    one_pass()
+    tune_ms = kv.kv_batch_autotune(b, 4)
+    cfg = kv.kv_batch_get_config(b)
+    for _ in range(args.warmup):
+        one_pass()
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = kv.kv_batch_launch_count(b) + sum(kv.kv_launch_count(h) for h in hs)
+    e0.record(stream)
+    for _ in range(args.steps):
+        n_proj = one_pass()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    # step-only timing of the batched kernel
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for h in hs:
+        kv.kv_reset(h)
+    s0.record(stream)
+    kv.kv_batch_step(b, n_steps)
+    s1.record(stream)
+    torch.cuda.synchronize(device)
+    t_steps = s0.elapsed_time(s1) / 1e3
+    launches = kv.kv_batch_launch_count(b) + sum(kv.kv_launch_count(h) for h in hs) - l0
+    kv.kv_batch_destroy(b)
+    for h in hs:
+        kv.kv_destroy(h)
+    value = N * n_steps * args.steps / t / 1e9
+    bytes_per_step = 48.0 * N  # homogeneous: (u, d) read + write
+    achieved = bytes_per_step / (t_steps / n_steps) / 1e9
+    peak, peak_kind = peaks()
+    if rank == 0:
+        print(json.dumps({
+            "metric": f"KV-FDTD Gcell-updates/s (26-case sweep, projections + {n_steps} steps)",
+            "value": value, "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep_26_cases", "cells": N, "time_steps": n_steps,
+                       "projections_per_pass": n_proj, "batch_config": cfg,
+                       "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2"},
+            "kv_step_gcells": N * n_steps / t_steps / 1e9, "autotune_ms_per_step": tune_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_step_batch",
+                         "peak_kind": peak_kind, "bytes_model": "48 B/cell (homogeneous)"},
+            "gpu_launches": int(launches), "clocks": clk, "e2e": None, "cpu_baseline": None}),
+            flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -179,6 +280,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, rank, world)
         return
 
     import torch
@@ -194,7 +298,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = workload(args.grid, args.time_steps)
+    w = workload(args.grid, args.time_steps, args.workload)
     w.tol = args.cg_tol
     N = w.n_cells
     stream = torch.cuda.Stream(device)  # a non-default stream shared by torch events and libkv
@@ -315,16 +419,18 @@ def main():
     kv.kv_destroy(h)
     if rank == 0:
         line = {
-            "metric": "KV-FDTD Gcell-updates/s (projection + 2000 steps)",
+            "metric": f"KV-FDTD Gcell-updates/s (projection + {w.n_steps} steps)",
             "value": value, "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "dx_m": w.dx,
                        "time_steps": w.n_steps, "force_steps": n_force_steps, "cg_tol": w.tol,
-                       "medium": "8 seeded spherical inclusions (seed 102), speckled beam",
+                       "medium": ("8 seeded spherical inclusions (seed 102), speckled beam"
+                                  if args.workload == "inclusions256" else
+                                  "bone shell over smooth soft tissue (seed 105), speckled beam"),
                        "reductions": "f64", "parallelism": f"replicas{world}",
-                       "l2": "state 0.8 GB > 126 MB L2 (inputs larger than L2)"},
+                       "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2 (inputs larger than L2)"},
             "kv_step_gcells": step_gcells,
             "projection_ms": float(np.mean(cg_ms)), "cg_iters": int(np.median(cg_iters)),
             "step_config": step_cfg, "autotune_ms_per_step": tune_ms,

@@ -227,6 +227,41 @@ long long kv_launch_count(kv_handle *h);
 
 kv_status kv_destroy(kv_handle *h);
 
+/*
+ * Batched time stepping (parameter sweeps, Sec. 3.1 applied to many media at
+ * once). A batch refers to n existing FP32 handles -- all homogeneous or all
+ * heterogeneous, all created on the same stream -- of any grid sizes. Each
+ * kv_batch_step(b, n) advances every case by n steps with one kernel launch
+ * per step covering the tile grids of all cases (blocks of 32 steps replay
+ * from a CUDA graph); each case keeps its own state, coefficients, envelope,
+ * sensors, traces and step count, readable through its handle as usual. The
+ * cases must be at the same step parity (e.g. all freshly reset). The batch
+ * holds a device table of its cases (allocated in kv_batch_create, freed in
+ * kv_batch_destroy) and rebuilds it when a case's parameters change.
+ * kv_batch_set_config: tile (tx, ty), z chunk zc and stage count ns as in
+ * kv_set_step_config. kv_batch_autotune: times every supported configuration
+ * over trial_steps and keeps the fastest, then resets every case.
+ * kv_batch_get_config: cfg[4] = {tx, ty, zc, ns}. The handles must outlive the
+ * batch. Errors are reported in kv_last_error(NULL).
+ */
+typedef struct kv_batch kv_batch;
+kv_status kv_batch_create(kv_batch **out, int n, kv_handle *const *cases);
+kv_status kv_batch_set_config(kv_batch *b, int tx, int ty, int zc, int ns);
+kv_status kv_batch_get_config(kv_batch *b, int *cfg);
+kv_status kv_batch_autotune(kv_batch *b, int trial_steps, double *best_ms);
+kv_status kv_batch_step(kv_batch *b, int n);
+long long kv_batch_launch_count(kv_batch *b);
+kv_status kv_batch_destroy(kv_batch *b);
+
+/*
+ * Reuse one projection for another handle on the same grid (Sec. 3.3: the
+ * solenoidal projection depends on the force pattern only, not on the medium):
+ * dst's projected force becomes (dt_dst^2/rho_dst) f_S0 with f_S0 taken from
+ * src's stored F = (dt_src^2/rho_src) f_S0. Both FP32, same nx, ny, nz;
+ * src must hold a projected force. Synchronising.
+ */
+kv_status kv_share_force(kv_handle *dst, kv_handle *src);
+
 /* One-line description of the last error on h (or of the last failed
  * kv_create when h is NULL). Never NULL. */
 const char *kv_last_error(kv_handle *h);

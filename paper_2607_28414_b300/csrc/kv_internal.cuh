@@ -71,6 +71,18 @@ struct StepParams {
     int nblocks;         // blocks in the launch
 };
 
+// One case of a batched step (device table entry; tensor maps need 64-byte
+// alignment).
+struct alignas(64) BatchCase {
+    CUtensorMap tm_state[2];
+    CUtensorMap tm_coef;
+    const float *F;
+    float *state[2];
+    StepParams p;         // nblocks = this case's blocks
+    int gx, gy, gz;       // tile grid of this case
+    int block_begin;      // first block of this case in the batched launch
+};
+
 struct CgParams {
     int nx, ny, nz, px;
     long long Np;
@@ -157,6 +169,13 @@ kv_status cuda_check(kv_handle *h, cudaError_t e, const char *what);
 // Step kernels (kv_step.cu)
 kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attributes
 kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
+
+// Batched step (kv_step.cu)
+kv_status batch_kernel_for(int tx, int ty, int ns, bool het, void **kernel, size_t *smem, int *nt);
+kv_status batch_fill_case(kv_handle *h, struct BatchCase *bc, int tx, int ty, int zc, int begin,
+                          int *blocks);
+kv_status batch_launch(void *kernel, const struct BatchCase *table, int ncases, int total_blocks,
+                       int nt, size_t smem, int from, cudaStream_t s);
 
 // 4D float32 tensor map over [fields][nz][ny][px] with box (bx, by, 1, fields_box)
 kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by,

@@ -119,19 +119,21 @@ struct TmaTile {
     static constexpr int STAGE = (STATE + COEF + 31) / 32 * 32;  // floats, 128 B multiple
 };
 
+// One block's work: the TX x TY column (bx, by) over planes of z chunk bz.
+// tm_in / tm_coef: addresses of tensor maps in parameter or global memory.
 template <int TX, int TY, int NS, bool HET>
-__global__ void __launch_bounds__(TX *TY / 4)
-k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
-           const float *__restrict__ F, float *__restrict__ out, StepParams p) {
+__device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtensorMap *tm_coef,
+                                          const float *__restrict__ F, float *__restrict__ out,
+                                          const StepParams &p, int bx, int by, int bz) {
     using TT = TmaTile<TX, TY, HET>;
     extern __shared__ __align__(128) float smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * TT::STAGE);
 
     const int tid = threadIdx.x;
     const int gx = tid % TT::GX, gy = tid / TT::GX;
-    const int x0 = blockIdx.x * TX;
-    const int y0 = 1 + blockIdx.y * TY;
-    const int k0 = 1 + blockIdx.z * p.zc;
+    const int x0 = bx * TX;
+    const int y0 = 1 + by * TY;
+    const int k0 = 1 + bz * p.zc;
     const int k1 = min(k0 + p.zc, p.nz - 1);  // planes k0..k1-1 are computed
     const int kb = k0 - 1;                     // first staged plane
     const long long step = __ldcg(&p.ctrl[kStep]);
@@ -152,8 +154,8 @@ k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
         const bool wc = HET && (q >= k0 && q < k1);
         const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0);
         mbar_expect_tx(bar, bytes);
-        tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 1, q, 0, bar);
-        if (wc) tma_load_4d(smem_u32(st + TT::STATE), &tm_coef, x0, y0, q, 0, bar);
+        tma_load_4d(smem_u32(st), tm_in, x0 - 4, y0 - 1, q, 0, bar);
+        if (wc) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0, y0, q, 0, bar);
     };
 
     if (tid == 0) {
@@ -255,6 +257,29 @@ k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
         }
     }
     step_epilogue<float>(out, p, step);
+}
+
+template <int TX, int TY, int NS, bool HET>
+__global__ void __launch_bounds__(TX *TY / 4)
+k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
+           const float *__restrict__ F, float *__restrict__ out, StepParams p) {
+    step_tile<TX, TY, NS, HET>(&tm_in, &tm_coef, F, out, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched step: one launch advances every case of a batch by one step. Block
+// b belongs to the case whose [block_begin, block_begin + blocks) holds b; the
+// case's own tensor maps, coefficients, envelope, sensors and control block
+// come from the case table, and its last block runs that case's epilogue.
+template <int TX, int TY, int NS, bool HET>
+__global__ void __launch_bounds__(TX *TY / 4)
+k_step_batch(const BatchCase *__restrict__ cases, int ncases, int from) {
+    int c = 0;
+    while (c + 1 < ncases && (int)blockIdx.x >= cases[c + 1].block_begin) ++c;
+    const BatchCase &cs = cases[c];
+    const int local = blockIdx.x - cs.block_begin;
+    const int bx = local % cs.gx, by = (local / cs.gx) % cs.gy, bz = local / (cs.gx * cs.gy);
+    step_tile<TX, TY, NS, HET>(&cs.tm_state[from], &cs.tm_coef, cs.F, cs.state[1 - from], cs.p, bx,
+                               by, bz);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,6 +390,23 @@ static bool pick_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int 
            pick<128, 2, NS>(tx, ty, NS, het, k, smem, nt) ||
            pick<128, 4, NS>(tx, ty, NS, het, k, smem, nt) ||
            pick<128, 8, NS>(tx, ty, NS, het, k, smem, nt);
+}
+
+typedef void (*BatchKernel)(const BatchCase *, int, int);
+
+template <int TX, int TY, int NS>
+static bool bpick(int tx, int ty, int ns, bool het, BatchKernel *k) {
+    if (tx != TX || ty != TY || ns != NS) return false;
+    *k = het ? k_step_batch<TX, TY, NS, true> : k_step_batch<TX, TY, NS, false>;
+    return true;
+}
+
+template <int NS>
+static bool bpick_tile(int tx, int ty, bool het, BatchKernel *k) {
+    return bpick<32, 8, NS>(tx, ty, NS, het, k) || bpick<32, 16, NS>(tx, ty, NS, het, k) ||
+           bpick<64, 4, NS>(tx, ty, NS, het, k) || bpick<64, 8, NS>(tx, ty, NS, het, k) ||
+           bpick<64, 16, NS>(tx, ty, NS, het, k) || bpick<128, 2, NS>(tx, ty, NS, het, k) ||
+           bpick<128, 4, NS>(tx, ty, NS, het, k) || bpick<128, 8, NS>(tx, ty, NS, het, k);
 }
 
 static bool tma_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
@@ -491,5 +533,58 @@ kv_status launch_init_velocity(kv_handle *h, const float *v_pitched) {
             v_pitched, (float *)h->state[h->cur], h->nx, h->ny, h->nz, h->px, h->Np, h->dt);
     h->launches++;
     return cuda_check(h, cudaGetLastError(), "initial velocity launch");
+}
+
+// ---------------------------------------------------------------------------
+// Batched step support (kv_batch.cu)
+// ---------------------------------------------------------------------------
+kv_status batch_kernel_for(int tx, int ty, int ns, bool het, void **kernel, size_t *smem, int *nt) {
+    TmaKernel single;
+    if (!tma_kernel_for(tx, ty, ns, het, &single, smem, nt)) return KV_ERR_ARG;
+    BatchKernel k = nullptr;
+    bool ok = false;
+    switch (ns) {
+        case 4: ok = bpick_tile<4>(tx, ty, het, &k); break;
+        case 6: ok = bpick_tile<6>(tx, ty, het, &k); break;
+        case 8: ok = bpick_tile<8>(tx, ty, het, &k); break;
+    }
+    if (!ok || *smem > 227 * 1024) return KV_ERR_ARG;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    if (e != cudaSuccess) return KV_ERR_CUDA;
+    *kernel = (void *)k;
+    return KV_OK;
+}
+
+// Fill one batch table entry for handle h with tile (tx, ty), zc planes per
+// block, the first block index `begin`; returns the case's block count.
+kv_status batch_fill_case(kv_handle *h, BatchCase *bc, int tx, int ty, int zc, int begin, int *blocks) {
+    kv_status st;
+    for (int b = 0; b < 2; ++b)
+        if ((st = encode_tensor_4d(h, &bc->tm_state[b], h->state[b], 6, tx + 8, ty + 2, 6)) != KV_OK)
+            return st;
+    if (h->het) {
+        if ((st = encode_tensor_4d(h, &bc->tm_coef, h->coef, 2, tx, ty, 2)) != KV_OK) return st;
+    } else {
+        bc->tm_coef = bc->tm_state[0];
+    }
+    bc->F = (const float *)h->F;
+    bc->state[0] = (float *)h->state[0];
+    bc->state[1] = (float *)h->state[1];
+    bc->gx = (h->px + tx - 1) / tx;
+    bc->gy = (h->ny - 2 + ty - 1) / ty;
+    bc->gz = (h->nz - 2 + zc - 1) / zc;
+    bc->block_begin = begin;
+    *blocks = bc->gx * bc->gy * bc->gz;
+    StepParams p = make_params(h, *blocks);
+    p.zc = zc;
+    bc->p = p;
+    return KV_OK;
+}
+
+kv_status batch_launch(void *kernel, const BatchCase *table, int ncases, int total_blocks, int nt,
+                       size_t smem, int from, cudaStream_t s) {
+    BatchKernel k = (BatchKernel)kernel;
+    k<<<total_blocks, nt, smem, s>>>(table, ncases, from);
+    return cudaGetLastError() == cudaSuccess ? KV_OK : KV_ERR_CUDA;
 }
 }  // namespace kv

@@ -240,3 +240,84 @@ def heterogeneous_inclusions(n=256, dx=0.2 * MM, seed=102, n_steps=2000, t_push=
     sensors = line_sensors((1, n // 2, kf), 0, n - 1, 2)
     return Workload(name or f"heterogeneous_inclusions_{n}^3", n, n, n, dx, G, rho, eta, force,
                     t_push, n_steps, sensors, tol, extra={"inclusions": incl, "seed": seed})
+
+
+def smooth_field(rng, shape, dx, corr, lo, hi, coarse=8):
+    """Smooth random field with correlation length ~corr, affinely mapped to
+    [lo, hi]: Gaussian white noise on a lattice of spacing `coarse` nodes,
+    Gaussian-filtered (sigma = corr), trilinearly interpolated to `shape`."""
+    from scipy.ndimage import gaussian_filter, map_coordinates
+    cshape = tuple(max(4, s // coarse + 2) for s in shape)
+    w = gaussian_filter(rng.standard_normal(cshape), sigma=corr / (coarse * dx), mode="wrap")
+    w = (w - w.min()) / max(w.max() - w.min(), 1e-30)
+    axes = [np.arange(s, dtype=np.float64) / coarse for s in shape]
+    out = np.empty(shape, np.float32)
+    # interpolate plane by plane (z) to bound memory
+    zz = axes[0]
+    yy, xx = np.meshgrid(axes[1], axes[2], indexing="ij")
+    for k in range(shape[0]):
+        coords = np.stack([np.full_like(yy, zz[k]), yy, xx])
+        out[k] = map_coordinates(w, coords, order=1, mode="nearest")
+    return lo + (hi - lo) * out
+
+
+def bone_shell(nx=512, ny=512, nz=384, dx=0.15 * MM, seed=105, n_steps=5000, t_push=200e-6,
+               tol=1e-8, R=40 * MM, centre_above=30 * MM, focus_below=8 * MM, name=None):
+    """Large heterogeneous medium: a curved bone shell (spherical cap of inner
+    radius R, centre `centre_above` above the z = 0 face on the x-y centre line,
+    thickness 3-7 mm from a smooth random field over the angle; G = 50 kPa,
+    rho = 1900, eta = 2 Pa s) in soft tissue (G smooth in [1, 5] kPa, rho 1040,
+    eta smooth in [0.3, 1.0] Pa s). A speckled axial beam from the top face is
+    focused `focus_below` beneath the shell on the axis; sensors every second
+    node on the x line at the focal depth."""
+    rng = np.random.default_rng(seed)
+    shape = (nz, ny, nx)
+    G = smooth_field(rng, shape, dx, 5 * MM, 1e3, 5e3)
+    eta = smooth_field(rng, shape, dx, 5 * MM, 0.3, 1.0)
+    rho = np.full(shape, 1040.0, np.float32)
+    cx, cy, cz = (nx // 2) * dx, (ny // 2) * dx, -centre_above
+    # thickness over the cap: a smooth 2D field on (x, y), mapped to [3, 7] mm
+    thick2d = smooth_field(rng, (1, ny, nx), dx, 5 * MM, 3 * MM, 7 * MM)[0].astype(np.float64)
+    y = (np.arange(ny) * dx - cy)[:, None]
+    x = (np.arange(nx) * dx - cx)[None, :]
+    r_perp2 = x * x + y * y
+    for k in range(nz):
+        z = k * dx - cz
+        r = np.sqrt(r_perp2 + z * z)
+        bone = (r >= R) & (r <= R + thick2d)
+        G[k][bone] = 50e3
+        rho[k][bone] = 1900.0
+        eta[k][bone] = 2.0
+    z_shell_out = cz + R + float(thick2d[ny // 2, nx // 2])
+    focal_depth = z_shell_out + focus_below
+    force = beam_push(nx, ny, nz, dx, rng, focal_depth=focal_depth)
+    kf = int(round(focal_depth / dx))
+    sensors = line_sensors((1, ny // 2, kf), 0, nx - 1, 2)
+    return Workload(name or f"bone_shell_{nx}x{ny}x{nz}", nx, ny, nz, dx, G, rho, eta, force,
+                    t_push, n_steps, sensors, tol,
+                    extra={"seed": seed, "focal_depth_m": focal_depth, "shell_axis_m": z_shell_out})
+
+
+def sweep_cases(n_steps=1000, dx=0.2 * MM, eta_cases=16, g_cases=10, eta_grid=(128, 128, 192),
+                edge_range=(96, 224)):
+    """Parameter sweep: eta_cases homogeneous media with eta = linspace(0, 1.5)
+    Pa s at G = 4 kPa on one eta_grid (nx, ny, nz), plus g_cases cubes with
+    G = linspace(1, 10) kPa (eta = 0) whose edge grows with the wavelength,
+    n = round(e0 + (e1 - e0) (sqrt(G/1 kPa) - 1) / (sqrt(10) - 1)); rho = 1000;
+    each with the centred Gaussian push along z (sigma 1 mm lateral, 2 mm
+    axial, 200 us) and x-line sensors from the centre."""
+    cases = []
+    nx, ny, nz = eta_grid
+    for eta in np.linspace(0.0, 1.5, eta_cases):
+        c = centre_node(nx, ny, nz)
+        cases.append(Workload(f"sweep_eta{eta:.2f}_{nx}x{ny}x{nz}", nx, ny, nz, dx, 4e3, 1000.0,
+                              float(eta), gaussian_push(nx, ny, nz, dx, 1e3, 1 * MM, 2 * MM, c),
+                              200e-6, n_steps, line_sensors(c, 0, nx - 1, 1), 1e-8))
+    e0, e1 = edge_range
+    for G in np.linspace(1e3, 10e3, g_cases):
+        n = int(round(e0 + (e1 - e0) * (np.sqrt(G / 1e3) - 1.0) / (np.sqrt(10.0) - 1.0)))
+        c = centre_node(n, n, n)
+        cases.append(Workload(f"sweep_G{G / 1e3:.0f}kPa_{n}^3", n, n, n, dx, float(G), 1000.0, 0.0,
+                              gaussian_push(n, n, n, dx, 1e3, 1 * MM, 2 * MM, c), 200e-6, n_steps,
+                              line_sensors(c, 0, n - 1, 1), 1e-8))
+    return cases

@@ -98,11 +98,22 @@ def lib():
         L.kv_destroy.argtypes = [H]
         L.kv_project_force_noalloc.argtypes = [i, i, i, d, vp, vp, vp, d, i, vp,
                                                ctypes.POINTER(KvCgStats), vp]
+        L.kv_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+        L.kv_batch_set_config.argtypes = [vp, i, i, i, i]
+        L.kv_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.kv_batch_autotune.argtypes = [vp, i, ctypes.POINTER(d)]
+        L.kv_batch_step.argtypes = [vp, i]
+        L.kv_batch_launch_count.argtypes = [vp]
+        L.kv_batch_launch_count.restype = ctypes.c_longlong
+        L.kv_batch_destroy.argtypes = [vp]
+        L.kv_share_force.argtypes = [H, H]
         for name in ("kv_stable_dt", "kv_create", "kv_set_medium", "kv_set_envelope",
                      "kv_set_sensors", "kv_reset", "kv_set_initial_velocity", "kv_project_force",
                      "kv_clear_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
                      "kv_set_step_config", "kv_get_step_config", "kv_autotune_step",
-                     "kv_destroy", "kv_project_force_noalloc"):
+                     "kv_destroy", "kv_project_force_noalloc", "kv_batch_create",
+                     "kv_batch_set_config", "kv_batch_get_config", "kv_batch_autotune",
+                     "kv_batch_step", "kv_batch_destroy", "kv_share_force"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -295,6 +306,47 @@ def kv_launch_count(h):
 def kv_destroy(h):
     if h:
         lib().kv_destroy(h)
+
+
+def kv_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                             for h in handles])
+    b = ctypes.c_void_p()
+    _check(lib().kv_batch_create(ctypes.byref(b), len(handles), arr))
+    return b
+
+
+def kv_batch_set_config(b, tx, ty, zc, ns):
+    _check(lib().kv_batch_set_config(b, int(tx), int(ty), int(zc), int(ns)))
+
+
+def kv_batch_get_config(b):
+    cfg = (ctypes.c_int * 4)()
+    _check(lib().kv_batch_get_config(b, cfg))
+    return dict(zip(("tx", "ty", "zc", "ns"), list(cfg)))
+
+
+def kv_batch_autotune(b, trial_steps=4):
+    best = ctypes.c_double()
+    _check(lib().kv_batch_autotune(b, int(trial_steps), ctypes.byref(best)))
+    return best.value
+
+
+def kv_batch_step(b, n):
+    _check(lib().kv_batch_step(b, int(n)))
+
+
+def kv_batch_launch_count(b):
+    return int(lib().kv_batch_launch_count(b))
+
+
+def kv_batch_destroy(b):
+    if b:
+        lib().kv_batch_destroy(b)
+
+
+def kv_share_force(dst, src):
+    _check(lib().kv_share_force(dst, src), dst)
 
 
 def kv_last_error(h=None):

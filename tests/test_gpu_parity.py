@@ -401,3 +401,114 @@ def test_invalid_arguments_on_gpu(device):
         kv.kv_set_medium(s.h, 4e3, 1000.0, 0.0)  # homogeneous into a heterogeneous handle
     assert e.value.status == kv.KV_ERR_ARG
     s.close()
+
+
+def test_full_size_bone_shell(device):
+    """512 x 512 x 384 bone shell over soft tissue (dx = 0.15 mm), speckled
+    beam focused beneath the shell, CG to 1e-8: the oracle checks the GPU's
+    potential (true residual in FP64), its projected force node by node, and
+    20 time steps driven by the GPU's projected force."""
+    w = inputs.bone_shell()
+    dt = 0.5 * orc.stable_dt(w.G, w.rho, w.eta, w.dx)
+    n_steps = 20
+    s = Solver(w, dt=dt, n_steps=n_steps)
+    fs = torch.zeros((3, w.nz, w.ny, w.nx), dtype=torch.float32, device=device)
+    st = s.project(fs_out=fs)
+    assert st["status"] == kv.KV_OK and st["rel_res_true"] < 1e-8
+    phi = np.empty((w.nz, w.ny, w.nx), np.float64)
+    kv.kv_read_field(s.h, kv.FIELD_PHI, 0, phi)
+    b = -orc.div_minus(*w.force, w.dx)
+    res = np.linalg.norm(b - orc.apply_A(phi, w.dx)) / np.linalg.norm(b)
+    assert res < 1e-8 * 1.01
+    g = orc.grad_plus(phi, w.dx)
+    del phi
+    fs_np = fs.cpu().numpy()
+    for a in range(3):
+        expect = w.force[a].astype(np.float64) - g[a]
+        assert np.abs(fs_np[a] - expect).max() <= 1e-6 * (np.abs(expect).max() + 1e-30)
+    del g
+    s.step()
+    tr = s.read_traces().cpu().numpy()
+    s.close()
+    ref = orc.run(w.nx, w.ny, w.nz, w.dx, dt, w.G, w.rho, w.eta, n_steps, w.sensors,
+                  fs=[fs_np[a] for a in range(3)], g=inputs.push_envelope(n_steps, dt, w.t_push))
+    err = max_rel_l2(tr, ref)
+    print(f"bone shell 512x512x384: CG {st}, oracle residual {res:.3e}, 20-step trace rel-L2 {err:.3e}")
+    assert err <= FP32_TRACE_TOL
+
+
+# ---------------------------------------------------------------------------
+# Batched stepping of several handles (parameter sweeps)
+# ---------------------------------------------------------------------------
+
+def sweep_small():
+    return [c for c in inputs.sweep_cases(n_steps=70, eta_cases=3, g_cases=3, eta_grid=(44, 36, 52),
+                                          edge_range=(33, 61))]
+
+
+def test_batch_matches_individual_handles(device):
+    cases = sweep_small()
+    stream = torch.cuda.Stream(device)
+    ind, bat = [], []
+    for w in cases:
+        for lst in (ind, bat):
+            s = Solver(w, n_steps=70, stream=stream.cuda_stream)
+            s.project()
+            lst.append(s)
+    b = kv.kv_batch_create([s.h for s in bat])
+    kv.kv_batch_step(b, 70)  # 2 graph blocks of 32 + 6 launches
+    assert kv.kv_batch_launch_count(b) == 70
+    for s in ind:
+        s.step(70)
+    for a, c in zip(ind, bat):
+        assert kv.kv_steps_taken(c.h) == 70
+        ta = a.read_traces().cpu().numpy()
+        tc = c.read_traces().cpu().numpy()
+        assert np.abs(ta).max() > 0
+        assert np.array_equal(ta, tc), a.w.name
+    # another configuration of the batched kernel gives the same numbers
+    for c in bat:
+        c.reset()
+    kv.kv_batch_set_config(b, 128, 2, 5, 6)
+    kv.kv_batch_step(b, 70)
+    for a, c in zip(ind, bat):
+        assert np.array_equal(a.read_traces().cpu().numpy(), c.read_traces().cpu().numpy())
+    kv.kv_batch_destroy(b)
+    for s in ind + bat:
+        s.close()
+
+
+def test_batch_autotune_resets_cases(device):
+    cases = sweep_small()[:2]
+    stream = torch.cuda.Stream(device)
+    ss = [Solver(w, n_steps=20, stream=stream.cuda_stream) for w in cases]
+    for s in ss:
+        s.project()
+    b = kv.kv_batch_create([s.h for s in ss])
+    ms = kv.kv_batch_autotune(b, 2)
+    cfg = kv.kv_batch_get_config(b)
+    assert ms > 0 and cfg["ns"] in (4, 6, 8)
+    assert all(kv.kv_steps_taken(s.h) == 0 for s in ss)
+    kv.kv_batch_destroy(b)
+    for s in ss:
+        s.close()
+
+
+def test_share_force_matches_direct_projection(device):
+    w = sweep_small()[0]
+    w2 = sweep_small()[1]  # same grid, other viscosity
+    a = Solver(w, n_steps=5)
+    a.project(tol=1e-10)
+    b_direct = Solver(w2, n_steps=5)
+    b_direct.project(tol=1e-10)
+    b_shared = Solver(w2, n_steps=5)
+    kv.kv_share_force(b_shared.h, a.h)
+    n = (w2.nz, w2.ny, w2.nx)
+    for c in range(3):
+        x = np.empty(n, np.float32)
+        y = np.empty(n, np.float32)
+        kv.kv_read_field(b_direct.h, kv.FIELD_F, c, x)
+        kv.kv_read_field(b_shared.h, kv.FIELD_F, c, y)
+        assert np.abs(x - y).max() <= 1e-6 * np.abs(x).max() + 1e-30
+    for s in (a, b_direct, b_shared):
+        s.close()
