@@ -133,8 +133,9 @@ kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_fie
  *         evaluated in FP64),
  *   f_S0 = b0 - D+ phi (forward differences) on every node,
  * and stores F = (dt^2/rho) f_S0 for the time step. fx, fy, fz: dense fields.
- * max_iter <= 0 selects 20 * max(nx, ny, nz). mode: 0 = zero initial guess
- * (other values are reserved, KV_ERR_UNSUPPORTED). fs_out: NULL, or a device
+ * max_iter <= 0 selects 20 * max(nx, ny, nz). mode: 0 = zero initial guess,
+ * 1 = learned initial guess from the net attached with kv_attach_net (the
+ * stopping rule is the same); other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
  * pointer to 3*nx*ny*nz floats (component-major) that receives f_S0.
  * stats: NULL or filled. Returns KV_OK, KV_CG_MAXITER, KV_CG_BREAKDOWN or
  * KV_ERR_NONFINITE (the stats say which). A zero right-hand side gives
@@ -171,6 +172,53 @@ kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx, const floa
                                    const float *fy, const float *fz, double tol, int max_iter,
                                    float *fs_out, kv_cg_stats *stats, void *stream);
 
+/*
+ * Learned warm start of the projection. A small 3D U-Net (BF16 tensor-core
+ * convolutions with FP32 accumulation, trained on the GPU by these calls)
+ * maps the Poisson right-hand side b = -(D- . f) to an approximation of phi;
+ * kv_project_force(mode = 1) on a handle with an attached net starts the CG
+ * from that phi and stops on the same true residual as the zero start, so
+ * the result meets the same tolerance whatever the net predicts.
+ * Architecture: `levels` resolution levels with channels[l] in {16, 32, 64};
+ * per level two 3x3x3 conv + ReLU, 2x average pooling down, nearest 2x
+ * upsampling + conv + ReLU + skip addition + conv + ReLU up, a final conv.
+ * The input is b scaled to unit RMS; the target phi * s / dx^2 with the same
+ * scale s; the loss the mean squared error (Adam on FP32 master weights).
+ * kv_net_create allocates activations for grids up to max_n* (each axis);
+ * b, phi: dense nx*ny*nz float device arrays. stream: cudaStream_t or NULL.
+ * kv_net_get/set_params: kv_net_num_params floats on the host.
+ * kv_attach_net: use net for mode 1 of h (NULL detaches; the net must
+ * outlive its use). Errors are reported in kv_last_error(NULL).
+ */
+typedef struct kv_net kv_net;
+kv_status kv_net_create(kv_net **out, int levels, const int *channels, int max_nx, int max_ny,
+                        int max_nz, void *stream);
+kv_status kv_net_destroy(kv_net *n);
+long long kv_net_num_params(kv_net *n);
+kv_status kv_net_init(kv_net *n, unsigned long long seed);
+kv_status kv_net_get_params(kv_net *n, float *host);
+kv_status kv_net_set_params(kv_net *n, const float *host);
+kv_status kv_net_train_step(kv_net *n, int nx, int ny, int nz, double dx, const float *b,
+                            const float *phi, double lr, double *loss);
+kv_status kv_net_predict(kv_net *n, int nx, int ny, int nz, double dx, const float *b, float *phi);
+kv_status kv_attach_net(kv_handle *h, kv_net *net);
+
+/*
+ * Layer operations of the net (exposed for tests): channel-last BF16 tensors
+ * [nz][ny][nx][C], C in {16, 32, 64}; W[t][ci][co] BF16 with tap
+ * t = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padding of one voxel.
+ *   kv_nn_conv3d_fwd: out = bias + conv(x, W) (ReLU if relu), BF16 or FP32 out.
+ *   kv_nn_conv3d_flip: Wt[t][co][ci] = W[26-t][ci][co] (input gradient =
+ *     kv_nn_conv3d_fwd of the output gradient with Wt, cin/cout swapped).
+ *   kv_nn_conv3d_bwd_weight: gW[t][ci][co] += sum_v x[v+d(t)][ci] g[v][co],
+ *     gb[co] += sum_v g[v][co] (FP32, accumulating; gb may be NULL).
+ */
+kv_status kv_nn_conv3d_fwd(int nx, int ny, int nz, int cin, int cout, const void *x, const void *W,
+                           const float *bias, void *out, int out_f32, int relu, void *stream);
+kv_status kv_nn_conv3d_flip(int cin, int cout, const void *W, void *Wt, void *stream);
+kv_status kv_nn_conv3d_bwd_weight(int nx, int ny, int nz, int cin, int cout, const void *x,
+                                  const void *g, float *gW, float *gb, void *stream);
+
 /* Drop the projected force (the step then runs unforced). */
 kv_status kv_clear_force(kv_handle *h);
 
@@ -197,6 +245,7 @@ kv_status kv_read_traces(kv_handle *h, void *out, int where, int *n_written);
  * Copy one dense field out (element type as for traces; phi always double):
  *   which 0: u^n component comp     which 1: d^n = u^n - u^{n-1}, component comp
  *   which 2: phi (comp ignored)     which 3: F = dt^2 f_S0 / rho, component comp
+ *   which 4: b = -(D- . f) of the last projection (double, comp ignored)
  * out: nx*ny*nz elements on the host or device (where). Synchronising.
  */
 kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where);

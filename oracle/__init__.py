@@ -57,6 +57,8 @@ def lib():
         L.or_run.restype = i
         L.or_kv1d_run.argtypes = [i, d, d, d, d, d, d, d, d, i, ip, i, dp]
         L.or_kv1d_run.restype = i
+        L.or_conv3d_fwd.argtypes = [i, i, i, i, i, dp, dp, dp, dp]
+        L.or_conv3d_bwd.argtypes = [i, i, i, i, i, dp, dp, dp, dp, dp, dp]
         _LIB = L
         set_threads(int(os.environ.get("KV_ORACLE_THREADS", os.cpu_count() or 1)))
     return _LIB
@@ -341,3 +343,36 @@ def lockin_fit(rec, xs, dt, omega, n_periods):
     phase = np.unwrap(np.angle(U))
     pa, *_ = np.linalg.lstsq(A, phase, rcond=None)
     return float(-la[0]), float(omega / abs(pa[0]))
+
+
+# ---------------------------------------------------------------------------
+# 3D convolution (test reference for the learned warm start's kernels)
+# ---------------------------------------------------------------------------
+
+def conv3d_fwd(x, W, bias=None):
+    """Direct-loop 3x3x3 convolution, zero padding 1. x: (nz, ny, nx, cin),
+    W: (27, cin, cout) with tap t = (dz+1)*9 + (dy+1)*3 + (dx+1), bias: (cout,)."""
+    nz, ny, nx, cin = x.shape
+    cout = W.shape[2]
+    x, xp = _d(x)
+    W, wp = _d(W)
+    bp = _null()
+    if bias is not None:
+        bias, bp = _d(bias)
+    out, op = _d(np.zeros((nz, ny, nx, cout)))
+    lib().or_conv3d_fwd(nx, ny, nz, cin, cout, xp, wp, bp, op)
+    return out
+
+
+def conv3d_bwd(x, W, g):
+    """Gradients (d/dx, d/dW, d/dbias) of sum(g * conv3d_fwd(x, W, bias))."""
+    nz, ny, nx, cin = x.shape
+    cout = W.shape[2]
+    x, xp = _d(x)
+    W, wp = _d(W)
+    g, gp = _d(g)
+    gin, gip = _d(np.zeros_like(x))
+    gW, gwp = _d(np.zeros_like(W))
+    gb, gbp = _d(np.zeros(cout))
+    lib().or_conv3d_bwd(nx, ny, nz, cin, cout, xp, wp, gp, gip, gwp, gbp)
+    return gin, gW, gb

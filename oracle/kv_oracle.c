@@ -391,3 +391,77 @@ int or_kv1d_run(int n, double dx, double dt, double mu, double rho, double eta, 
     free(um); free(u0); free(up);
     return 0;
 }
+
+/*
+ * Direct-loop 3D convolution (test infrastructure for the learned warm start;
+ * no counterpart in the paper's method). Channel-last tensors [z][y][x][C],
+ * 3x3x3 taps t = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padding of one voxel,
+ * weights W[t][ci][co]:
+ *   out[v][co] = bias[co] + sum_{t, ci} in[v + d(t)][ci] W[t][ci][co]
+ * and the two gradients of a scalar loss with upstream gradient g = dL/dout:
+ *   gin[v][ci]  = sum_{t, co} g[v - d(t)][co] W[t][ci][co]
+ *   gW[t][ci][co] = sum_v in[v + d(t)][ci] g[v][co],   gb[co] = sum_v g[v][co]
+ */
+void or_conv3d_fwd(int nx, int ny, int nz, int cin, int cout, const double *in, const double *W,
+                   const double *bias, double *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                for (int co = 0; co < cout; ++co) {
+                    double s = bias ? bias[co] : 0.0;
+                    for (int t = 0; t < 27; ++t) {
+                        const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
+                        if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
+                        const double *a = in + (((size_t)zz * ny + yy) * nx + xx) * cin;
+                        for (int ci = 0; ci < cin; ++ci) s += a[ci] * W[((size_t)t * cin + ci) * cout + co];
+                    }
+                    out[(((size_t)z * ny + y) * nx + x) * cout + co] = s;
+                }
+}
+
+void or_conv3d_bwd(int nx, int ny, int nz, int cin, int cout, const double *in, const double *W,
+                   const double *g, double *gin, double *gW, double *gb)
+{
+    const size_t V = (size_t)nx * ny * nz;
+    if (gin) {
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x)
+                    for (int ci = 0; ci < cin; ++ci) {
+                        double s = 0.0;
+                        for (int t = 0; t < 27; ++t) {
+                            const int xx = x - (t % 3 - 1), yy = y - ((t / 3) % 3 - 1), zz = z - (t / 9 - 1);
+                            if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
+                            const double *gg = g + (((size_t)zz * ny + yy) * nx + xx) * cout;
+                            for (int co = 0; co < cout; ++co) s += gg[co] * W[((size_t)t * cin + ci) * cout + co];
+                        }
+                        gin[(((size_t)z * ny + y) * nx + x) * cin + ci] = s;
+                    }
+    }
+    if (gW) {
+#pragma omp parallel for schedule(static)
+        for (int t = 0; t < 27; ++t)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int co = 0; co < cout; ++co) {
+                    double s = 0.0;
+                    for (int z = 0; z < nz; ++z)
+                        for (int y = 0; y < ny; ++y)
+                            for (int x = 0; x < nx; ++x) {
+                                const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
+                                if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) continue;
+                                s += in[(((size_t)zz * ny + yy) * nx + xx) * cin + ci] *
+                                     g[(((size_t)z * ny + y) * nx + x) * cout + co];
+                            }
+                    gW[((size_t)t * cin + ci) * cout + co] = s;
+                }
+    }
+    if (gb)
+        for (int co = 0; co < cout; ++co) {
+            double s = 0.0;
+            for (size_t v = 0; v < V; ++v) s += g[v * cout + co];
+            gb[co] = s;
+        }
+}

@@ -395,7 +395,10 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
                            int max_iter, int mode, float *fs_out, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;
     if (h->sticky) return KV_ERR_STATE;
-    if (mode != 0) return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
+    if (mode != 0 && mode != 1)
+        return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
+    if (mode == 1 && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
+        return set_error(h, KV_ERR_STATE, "mode 1 needs a network attached with kv_attach_net that fits the grid");
     if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");
     const kv_field *f[3] = {&fx, &fy, &fz};
     for (auto *q : f)
@@ -409,7 +412,7 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
         if (f[q]->where != KV_SCALAR && (st = stage(h, *f[q], h->fstage + q * h->Np)) != KV_OK) return st;
     free_graphs(h);
     h->have_force = 0;
-    return project(h, tol, max_iter, fs_out, stats);
+    return project(h, tol, max_iter, mode, fs_out, stats);
 }
 
 kv_status kv_clear_force(kv_handle *h) {
@@ -490,8 +493,14 @@ kv_status kv_read_traces(kv_handle *h, void *out, int where, int *n_written) {
     return cuda_check(h, e, "kv_read_traces");
 }
 
+kv_status kv_attach_net(kv_handle *h, kv_net *net) {
+    if (!h) return KV_ERR_ARG;
+    h->net = net;
+    return KV_OK;
+}
+
 kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where) {
-    if (!h || !out || which < 0 || which > 3 || (which != 2 && (comp < 0 || comp > 2)) ||
+    if (!h || !out || which < 0 || which > 4 || (which < 2 || which == 3) && (comp < 0 || comp > 2) ||
         (where != KV_HOST && where != KV_DEVICE))
         return set_error(h, KV_ERR_ARG, "kv_read_field: invalid arguments");
     if (h->sticky) return KV_ERR_STATE;
@@ -502,6 +511,7 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
     if (which == 0) src = (const char *)h->state[h->cur] + (size_t)comp * h->Np * es;
     else if (which == 1) src = (const char *)h->state[h->cur] + (size_t)(3 + comp) * h->Np * es;
     else if (which == 2) { src = (const char *)h->phi; es = 8; }
+    else if (which == 4) { src = (const char *)h->b; es = 8; }
     else src = (const char *)h->F + (size_t)comp * h->Np * es;
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)h->nx * es, src, (size_t)h->px * es, (size_t)h->nx * es,
                                       (size_t)h->ny * h->nz, cudaMemcpyDefault, h->stream);

@@ -724,6 +724,26 @@ static kv_status sync_read(kv_handle *h) {
     return cuda_check(h, e, "projection poll");
 }
 
+// Pitched double <-> dense float (the learned warm start works on dense grids).
+__global__ void k_pitched_to_dense(const double *__restrict__ a, float *__restrict__ o, int nx, int ny,
+                                   int nz, int px) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const long long r = v / nx;
+        o[v] = (float)a[r * px + v % nx];
+    }
+}
+__global__ void k_dense_to_pitched(const float *__restrict__ a, double *__restrict__ o, int nx, int ny,
+                                   int nz, int px) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const long long r = v / nx;
+        const int i = (int)(v % nx), j = (int)(r % ny), k = (int)(r / ny);
+        const bool in = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+        o[r * px + i] = in ? (double)a[v] : 0.0;
+    }
+}
+
 // TMA views of the CG vectors and the kernels' shared-memory limits.
 static kv_status cg_tma_prepare(kv_handle *h) {
     if (h->cg_tma_ready) return KV_OK;
@@ -742,7 +762,7 @@ static kv_status cg_tma_prepare(kv_handle *h) {
 }
 
 template <typename T>
-static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out,
+static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, float *fs_out,
                            kv_cg_stats *st) {
     const auto t0 = std::chrono::steady_clock::now();
     const dim3 grid = cg_grid(h);
@@ -794,6 +814,18 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out
     const double bb = h->scal_host[kBB];
     int status = KV_OK;
     const int fold_blocks = 148 * 8;
+    if (mode == 1 && isfinite(bb) && bb > 0.0) {
+        // learned warm start: phi_0 = Net(b) on interior nodes; the CG below
+        // starts from it and stops on the same true residual as from zero
+        k_pitched_to_dense<<<fold_blocks, 256, 0, s>>>(h->b, kv_net_stage_b(h->net), h->nx, h->ny, h->nz, h->px);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_check(h, e, "warm start");
+        kv_status ns = kv_net_predict(h->net, h->nx, h->ny, h->nz, h->dx, kv_net_stage_b(h->net),
+                                      kv_net_stage_phi(h->net));
+        if (ns != KV_OK) return set_error(h, ns, "warm start: network inference failed");
+        k_dense_to_pitched<<<fold_blocks, 256, 0, s>>>(kv_net_stage_phi(h->net), h->phi, h->nx, h->ny, h->nz,
+                                                       h->px);
+        h->launches += 2;
+    }
     if (!isfinite(bb)) {
         status = KV_ERR_NONFINITE;
     } else if (bb > 0.0) {
@@ -858,9 +890,9 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, float *fs_out
     return KV_OK;
 }
 
-kv_status project(kv_handle *h, double tol, int max_iter, float *fs_out, kv_cg_stats *st) {
-    if (h->precision == KV_FP64) return project_t<double>(h, tol, max_iter, fs_out, st);
-    return project_t<float>(h, tol, max_iter, fs_out, st);
+kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_out, kv_cg_stats *st) {
+    if (h->precision == KV_FP64) return project_t<double>(h, tol, max_iter, mode, fs_out, st);
+    return project_t<float>(h, tol, max_iter, mode, fs_out, st);
 }
 
 }  // namespace kv

@@ -71,9 +71,9 @@ struct StepParams {
     int nblocks;         // blocks in the launch
 };
 
-// One case of a batched step (device table entry; tensor maps need 64-byte
-// alignment).
-struct alignas(64) BatchCase {
+// One case of a batched step (device table entry; CUtensorMap carries its own
+// 64-byte alignment).
+struct BatchCase {
     CUtensorMap tm_state[2];
     CUtensorMap tm_coef;
     const float *F;
@@ -156,10 +156,21 @@ struct kv_handle {
     cudaGraphExec_t graph[2];
     int graph_steps;
 
+    struct kv_net *net;    // learned warm start (kv_attach_net), not owned
+
     long long launches;
     int sticky;
     char err[512];
 };
+
+// Learned warm start (kv_net.cu)
+extern "C" {
+struct kv_net;
+kv_status kv_net_predict(struct kv_net *n, int nx, int ny, int nz, double dx, const float *b, float *phi);
+float *kv_net_stage_b(struct kv_net *n);
+float *kv_net_stage_phi(struct kv_net *n);
+int kv_net_fits(struct kv_net *n, int nx, int ny, int nz);
+}
 
 namespace kv {
 
@@ -182,7 +193,7 @@ kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields
                            int fields_box);
 
 // Projection kernels (kv_cg.cu)
-kv_status project(kv_handle *h, double tol, int max_iter, float *fs_out, kv_cg_stats *st);
+kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_out, kv_cg_stats *st);
 
 // Device stability limit over dense fields: kDtBlocks block minima in
 // `scratch` (kDtBlocks doubles; NULL = a temporary allocation), synchronising.

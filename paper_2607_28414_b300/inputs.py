@@ -321,3 +321,47 @@ def sweep_cases(n_steps=1000, dx=0.2 * MM, eta_cases=16, g_cases=10, eta_grid=(1
                               gaussian_push(n, n, n, dx, 1e3, 1 * MM, 2 * MM, c), 200e-6, n_steps,
                               line_sensors(c, 0, n - 1, 1), 1e-8))
     return cases
+
+
+def random_gaussian_forces_torch(n_fields, shape, dx, seed, device, speckle_sigma=0.3):
+    """Generator of force fields for the learned warm start: each field is a sum
+    of 1-4 anisotropic Gaussians (centre uniform in the middle half of the box,
+    uniformly random rotation from a unit quaternion, 1/e widths U[0.5, 4] mm per
+    axis, amplitude 1e3 * lognormal(0, 1) along a random unit direction) times
+    unit-mean lognormal speckle. Built with torch on `device` (input
+    construction only). Yields (fx, fy, fz) float32 tensors of shape (nz, ny, nx)."""
+    import torch
+    nx, ny, nz = shape
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    zc = (torch.arange(nz, device=device, dtype=torch.float32) * dx)[:, None, None]
+    yc = (torch.arange(ny, device=device, dtype=torch.float32) * dx)[None, :, None]
+    xc = (torch.arange(nx, device=device, dtype=torch.float32) * dx)[None, None, :]
+    L = torch.tensor([(nx - 1) * dx, (ny - 1) * dx, (nz - 1) * dx], device=device)
+    for _ in range(n_fields):
+        f = [torch.zeros((nz, ny, nx), device=device) for _ in range(3)]
+        k = int(torch.randint(1, 5, (1,), generator=g, device=device).item())
+        for _ in range(k):
+            c = (0.25 + 0.5 * torch.rand(3, generator=g, device=device)) * L
+            q = torch.randn(4, generator=g, device=device)
+            q = q / q.norm()
+            a, b_, cq, d = q.tolist()
+            R = torch.tensor([[a * a + b_ * b_ - cq * cq - d * d, 2 * (b_ * cq - a * d), 2 * (b_ * d + a * cq)],
+                              [2 * (b_ * cq + a * d), a * a - b_ * b_ + cq * cq - d * d, 2 * (cq * d - a * b_)],
+                              [2 * (b_ * d - a * cq), 2 * (cq * d + a * b_), a * a - b_ * b_ - cq * cq + d * d]],
+                             device=device)
+            sig = (0.5 + 3.5 * torch.rand(3, generator=g, device=device)) * MM
+            amp = 1e3 * float(torch.exp(torch.randn(1, generator=g, device=device)).item())
+            dvec = torch.randn(3, generator=g, device=device)
+            dvec = dvec / dvec.norm()
+            rx, ry, rz = xc - c[0], yc - c[1], zc - c[2]
+            e = 0.0
+            for ax in range(3):  # coordinate along the rotated axis ax
+                proj = R[0, ax] * rx + R[1, ax] * ry + R[2, ax] * rz
+                e = e + (proj / sig[ax]) ** 2
+            gauss = amp * torch.exp(-e)
+            for comp in range(3):
+                f[comp] = f[comp] + float(dvec[comp]) * gauss
+        speck = torch.exp(speckle_sigma * torch.randn((nz, ny, nx), generator=g, device=device)
+                          - 0.5 * speckle_sigma ** 2)
+        yield tuple((fc * speck).contiguous() for fc in f)

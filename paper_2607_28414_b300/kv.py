@@ -107,13 +107,29 @@ def lib():
         L.kv_batch_launch_count.restype = ctypes.c_longlong
         L.kv_batch_destroy.argtypes = [vp]
         L.kv_share_force.argtypes = [H, H]
+        L.kv_net_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(ctypes.c_int), i, i, i, vp]
+        L.kv_net_destroy.argtypes = [vp]
+        L.kv_net_num_params.argtypes = [vp]
+        L.kv_net_num_params.restype = ctypes.c_longlong
+        L.kv_net_init.argtypes = [vp, ctypes.c_ulonglong]
+        L.kv_net_get_params.argtypes = [vp, vp]
+        L.kv_net_set_params.argtypes = [vp, vp]
+        L.kv_net_train_step.argtypes = [vp, i, i, i, d, vp, vp, d, ctypes.POINTER(d)]
+        L.kv_net_predict.argtypes = [vp, i, i, i, d, vp, vp]
+        L.kv_attach_net.argtypes = [H, vp]
+        L.kv_nn_conv3d_fwd.argtypes = [i, i, i, i, i, vp, vp, vp, vp, i, i, vp]
+        L.kv_nn_conv3d_flip.argtypes = [i, i, vp, vp, vp]
+        L.kv_nn_conv3d_bwd_weight.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
         for name in ("kv_stable_dt", "kv_create", "kv_set_medium", "kv_set_envelope",
                      "kv_set_sensors", "kv_reset", "kv_set_initial_velocity", "kv_project_force",
                      "kv_clear_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
                      "kv_set_step_config", "kv_get_step_config", "kv_autotune_step",
                      "kv_destroy", "kv_project_force_noalloc", "kv_batch_create",
                      "kv_batch_set_config", "kv_batch_get_config", "kv_batch_autotune",
-                     "kv_batch_step", "kv_batch_destroy", "kv_share_force"):
+                     "kv_batch_step", "kv_batch_destroy", "kv_share_force", "kv_net_create",
+                     "kv_net_destroy", "kv_net_init", "kv_net_get_params", "kv_net_set_params",
+                     "kv_net_train_step", "kv_net_predict", "kv_attach_net", "kv_nn_conv3d_fwd",
+                     "kv_nn_conv3d_flip", "kv_nn_conv3d_bwd_weight"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -347,6 +363,85 @@ def kv_batch_destroy(b):
 
 def kv_share_force(dst, src):
     _check(lib().kv_share_force(dst, src), dst)
+
+
+def _dptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    return None if stream is None else ctypes.c_void_p(int(stream))
+
+
+def kv_net_create(channels, max_shape, stream=None):
+    """channels: per level (16/32/64); max_shape: (nx, ny, nz)."""
+    ch = (ctypes.c_int * len(channels))(*channels)
+    n = ctypes.c_void_p()
+    _check(lib().kv_net_create(ctypes.byref(n), len(channels), ch, int(max_shape[0]),
+                               int(max_shape[1]), int(max_shape[2]), _stream(stream)))
+    return n
+
+
+def kv_net_destroy(n):
+    if n:
+        lib().kv_net_destroy(n)
+
+
+def kv_net_num_params(n):
+    return int(lib().kv_net_num_params(n))
+
+
+def kv_net_init(n, seed=0):
+    _check(lib().kv_net_init(n, ctypes.c_ulonglong(seed)))
+
+
+def kv_net_get_params(n):
+    out = np.empty(kv_net_num_params(n), np.float32)
+    _check(lib().kv_net_get_params(n, out.ctypes.data))
+    return out
+
+
+def kv_net_set_params(n, params):
+    p = np.ascontiguousarray(params, np.float32)
+    assert p.size == kv_net_num_params(n)
+    _check(lib().kv_net_set_params(n, p.ctypes.data))
+
+
+def kv_net_train_step(n, shape, dx, b, phi, lr):
+    loss = ctypes.c_double()
+    _check(lib().kv_net_train_step(n, int(shape[0]), int(shape[1]), int(shape[2]), float(dx),
+                                   _dptr(b), _dptr(phi), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def kv_net_predict(n, shape, dx, b, phi_out):
+    _check(lib().kv_net_predict(n, int(shape[0]), int(shape[1]), int(shape[2]), float(dx), _dptr(b),
+                                _dptr(phi_out)))
+    return phi_out
+
+
+def kv_attach_net(h, n):
+    _check(lib().kv_attach_net(h, n), h)
+
+
+def kv_nn_conv3d_fwd(shape, cin, cout, x, W, bias, out, relu=False, stream=None):
+    _check(lib().kv_nn_conv3d_fwd(int(shape[0]), int(shape[1]), int(shape[2]), int(cin), int(cout),
+                                  _dptr(x), _dptr(W), None if bias is None else _dptr(bias),
+                                  _dptr(out), int(out.dtype.is_floating_point and out.element_size() == 4),
+                                  int(relu), _stream(stream)))
+
+
+def kv_nn_conv3d_flip(cin, cout, W, Wt, stream=None):
+    _check(lib().kv_nn_conv3d_flip(int(cin), int(cout), _dptr(W), _dptr(Wt), _stream(stream)))
+
+
+def kv_nn_conv3d_bwd_weight(shape, cin, cout, x, g, gW, gb=None, stream=None):
+    _check(lib().kv_nn_conv3d_bwd_weight(int(shape[0]), int(shape[1]), int(shape[2]), int(cin),
+                                         int(cout), _dptr(x), _dptr(g), _dptr(gW),
+                                         None if gb is None else _dptr(gb), _stream(stream)))
 
 
 def kv_last_error(h=None):

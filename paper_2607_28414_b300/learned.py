@@ -1,0 +1,132 @@
+"""Learned warm start of the projection: data, training and evaluation.
+
+Training pairs (b, phi) come from the library's own projection (CG to a true
+residual of 1e-10) on random Gaussian force fields; the net (kv_net_*) is
+trained by the library's tensor-core forward/backward kernels; evaluation
+compares kv_project_force with mode 0 (zero start) and mode 1 (learned start)
+at the same tolerance. This module only orchestrates calls through the binding.
+
+    python -m paper_2607_28414_b300.learned --train 2000 --train-n 128 --eval 200 --eval-n 256
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs, kv
+
+DX = 0.2 * inputs.MM
+
+
+def projection_handle(shape, dx=DX, stream=None):
+    """A handle whose only use is the projection (the medium does not enter it)."""
+    nx, ny, nz = shape
+    dt = 0.5 * kv.kv_stable_dt(nx, ny, nz, dx, 4e3, 1000.0, 0.0)
+    return kv.kv_create(nx, ny, nz, dx, dt, 4e3, 1000.0, 0.0, stream=stream)
+
+
+def make_pairs(shape, forces, tol=1e-10, dx=DX, device="cuda:0"):
+    """Stack (b, phi) float32 pairs [n, nz, ny, nx] on the device."""
+    import torch
+    nx, ny, nz = shape
+    h = projection_handle(shape, dx)
+    B, P, iters = [], [], []
+    try:
+        for f in forces:
+            st = kv.kv_project_force(h, *f, tol)
+            iters.append(st["iters"])
+            b = torch.empty((nz, ny, nx), dtype=torch.float64, device=device)
+            phi = torch.empty_like(b)
+            kv.kv_read_field(h, 4, 0, b)
+            kv.kv_read_field(h, kv.FIELD_PHI, 0, phi)
+            B.append(b.float())
+            P.append(phi.float())
+    finally:
+        kv.kv_destroy(h)
+    return torch.stack(B), torch.stack(P), iters
+
+
+def train(net, B, P, shape, epochs=3, lr=1e-3, dx=DX, seed=0, log=None):
+    """Adam over the pairs in a seeded random order; cosine learning-rate decay."""
+    import torch
+    n = B.shape[0]
+    rng = np.random.default_rng(seed)
+    steps = epochs * n
+    losses = []
+    k = 0
+    for ep in range(epochs):
+        order = rng.permutation(n)
+        for i in order:
+            lr_k = lr * 0.5 * (1.0 + np.cos(np.pi * k / max(1, steps)))
+            losses.append(kv.kv_net_train_step(net, shape, dx, B[i], P[i], lr_k))
+            k += 1
+        if log:
+            log(f"epoch {ep}: mean loss {np.mean(losses[-n:]):.4e}")
+    return losses
+
+
+def evaluate(net, shape, forces, tol=1e-8, dx=DX, device="cuda:0"):
+    """Projection of each field with mode 0 and mode 1 at the same tolerance."""
+    h = projection_handle(shape, dx)
+    kv.kv_attach_net(h, net)
+    rows = []
+    try:
+        for f in forces:
+            r = {}
+            for mode in (0, 1):
+                st = kv.kv_project_force(h, *f, tol, 0, mode)
+                r[mode] = (st["iters"], st["ms"], st["rel_res_true"])
+            rows.append(r)
+    finally:
+        kv.kv_destroy(h)
+    plain = np.array([[r[0][0], r[0][1], r[0][2]] for r in rows])
+    learned = np.array([[r[1][0], r[1][1], r[1][2]] for r in rows])
+    return {"plain_iters": float(plain[:, 0].mean()), "plain_ms": float(plain[:, 1].mean()),
+            "learned_iters": float(learned[:, 0].mean()), "learned_ms": float(learned[:, 1].mean()),
+            "max_rel_res_plain": float(plain[:, 2].max()), "max_rel_res_learned": float(learned[:, 2].max()),
+            "speedup_ms": float(plain[:, 1].mean() / learned[:, 1].mean()), "fields": len(rows)}
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--train-n", type=int, default=128)
+    ap.add_argument("--eval", type=int, default=200)
+    ap.add_argument("--eval-n", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--channels", default="16,32,64,64")
+    ap.add_argument("--seed", type=int, default=104)
+    ap.add_argument("--out", default=None, help="write the trained parameters (.npy)")
+    args = ap.parse_args()
+    device = torch.device("cuda:0")
+    tshape = (args.train_n,) * 3
+    eshape = (args.eval_n,) * 3
+    ch = [int(c) for c in args.channels.split(",")]
+    t0 = time.perf_counter()
+    B, P, it = make_pairs(tshape, inputs.random_gaussian_forces_torch(args.train, tshape, DX, args.seed, device))
+    t_data = time.perf_counter() - t0
+    net = kv.kv_net_create(ch, tuple(max(a, b) for a, b in zip(tshape, eshape)))
+    kv.kv_net_init(net, args.seed)
+    t0 = time.perf_counter()
+    losses = train(net, B, P, tshape, args.epochs, args.lr, log=print)
+    t_train = time.perf_counter() - t0
+    del B, P
+    res = evaluate(net, eshape, inputs.random_gaussian_forces_torch(args.eval, eshape, DX,
+                                                                    args.seed + 1_000_000, device))
+    res.update({"train_fields": args.train, "train_shape": tshape, "eval_shape": eshape,
+                "channels": ch, "epochs": args.epochs, "data_s": t_data, "train_s": t_train,
+                "train_cg_iters_mean": float(np.mean(it)), "final_loss": float(np.mean(losses[-50:])),
+                "first_loss": float(np.mean(losses[:50])), "params": kv.kv_net_num_params(net)})
+    if args.out:
+        np.save(args.out, kv.kv_net_get_params(net))
+    kv.kv_net_destroy(net)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,109 @@
+"""The learned warm start: tensor-core convolution kernels against the FP64
+oracle, training on the GPU, and the warm start inside the projection.
+
+Tolerances (BF16 operands, FP32 accumulation): with operands rounded to BF16
+on both sides, an FP32-accumulated convolution matches the FP64 reference to
+~1e-6 relative (FP32 output) and to BF16 rounding, 2^-8 relative, when its
+output is stored in BF16; gradients likewise. The gates are 1e-4 (FP32 output)
+and 5e-3 (BF16 output), relative to the largest reference magnitude.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2607_28414_b300 import inputs, kv, learned
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (21, 10, 7)  # not a multiple of the 16 x 4 x 2 voxel tile
+
+
+def bf16_tensor(rng, shape, device, scale=1.0):
+    a = torch.from_numpy((rng.standard_normal(shape) * scale).astype(np.float32)).to(device)
+    return a.to(torch.bfloat16)
+
+
+def to64(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 64), (64, 16), (64, 64)])
+def test_conv_forward_matches_oracle(device, cin, cout):
+    rng = np.random.default_rng(cin * 100 + cout)
+    nx, ny, nz = SHAPE
+    x = bf16_tensor(rng, (nz, ny, nx, cin), device)
+    W = bf16_tensor(rng, (27, cin, cout), device, 0.1)
+    b = torch.from_numpy(rng.standard_normal(cout).astype(np.float32)).to(device)
+    ref = orc.conv3d_fwd(to64(x), to64(W), b.cpu().numpy().astype(np.float64))
+    out32 = torch.empty((nz, ny, nx, cout), dtype=torch.float32, device=device)
+    kv.kv_nn_conv3d_fwd(SHAPE, cin, cout, x, W, b, out32)
+    scale = np.abs(ref).max()
+    assert np.abs(out32.cpu().numpy() - ref).max() <= 1e-4 * scale
+    out16 = torch.empty((nz, ny, nx, cout), dtype=torch.bfloat16, device=device)
+    kv.kv_nn_conv3d_fwd(SHAPE, cin, cout, x, W, b, out16, relu=True)
+    assert np.abs(to64(out16) - np.maximum(ref, 0)).max() <= 5e-3 * scale
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (64, 16)])
+def test_conv_gradients_match_oracle(device, cin, cout):
+    rng = np.random.default_rng(7 + cin + cout)
+    nx, ny, nz = SHAPE
+    x = bf16_tensor(rng, (nz, ny, nx, cin), device)
+    W = bf16_tensor(rng, (27, cin, cout), device, 0.1)
+    g = bf16_tensor(rng, (nz, ny, nx, cout), device)
+    gin_ref, gW_ref, gb_ref = orc.conv3d_bwd(to64(x), to64(W), to64(g))
+    Wt = torch.empty((27, cout, cin), dtype=torch.bfloat16, device=device)
+    kv.kv_nn_conv3d_flip(cin, cout, W, Wt)
+    gin = torch.empty((nz, ny, nx, cin), dtype=torch.float32, device=device)
+    kv.kv_nn_conv3d_fwd(SHAPE, cout, cin, g, Wt, None, gin)
+    assert np.abs(gin.cpu().numpy() - gin_ref).max() <= 1e-4 * np.abs(gin_ref).max()
+    gW = torch.zeros((27, cin, cout), dtype=torch.float32, device=device)
+    gb = torch.zeros(cout, dtype=torch.float32, device=device)
+    kv.kv_nn_conv3d_bwd_weight(SHAPE, cin, cout, x, g, gW, gb)
+    assert np.abs(gW.cpu().numpy() - gW_ref).max() <= 1e-4 * np.abs(gW_ref).max()
+    assert np.abs(gb.cpu().numpy() - gb_ref).max() <= 1e-4 * np.abs(gb_ref).max()
+
+
+def small_pairs(n, shape, seed, device):
+    return learned.make_pairs(shape, inputs.random_gaussian_forces_torch(n, shape, learned.DX, seed, device),
+                              tol=1e-10)
+
+
+def test_training_lowers_the_loss(device):
+    shape = (24, 24, 24)
+    B, P, _ = small_pairs(6, shape, 3, device)
+    net = kv.kv_net_create([16, 16], shape)
+    kv.kv_net_init(net, 1)
+    losses = learned.train(net, B, P, shape, epochs=12, lr=2e-3)
+    kv.kv_net_destroy(net)
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-6:]) < 0.5 * np.mean(losses[:6])
+
+
+def test_warm_start_reaches_the_same_residual_and_saves_iterations(device):
+    """Zero start and learned start stop on the same true residual (checked by
+    the oracle on the learned-start potential); after a short training the
+    learned start needs fewer CG iterations on held-out fields."""
+    shape = (40, 40, 40)
+    B, P, _ = small_pairs(48, shape, 5, device)
+    net = kv.kv_net_create([16, 32, 64], shape)
+    kv.kv_net_init(net, 2)
+    learned.train(net, B, P, shape, epochs=6, lr=2e-3)
+    held = list(inputs.random_gaussian_forces_torch(6, shape, learned.DX, 10_005, device))
+    res = learned.evaluate(net, shape, held, tol=1e-8)
+    print("warm start on 40^3:", res)
+    assert res["max_rel_res_learned"] < 1e-8 and res["max_rel_res_plain"] < 1e-8
+    assert res["learned_iters"] < res["plain_iters"]
+    # independent check of the learned-start potential by the oracle
+    h = learned.projection_handle(shape)
+    kv.kv_attach_net(h, net)
+    st = kv.kv_project_force(h, *held[0], 1e-8, 0, 1)
+    phi = np.empty(shape[::-1], np.float64)
+    kv.kv_read_field(h, kv.FIELD_PHI, 0, phi)
+    b = -orc.div_minus(*[f.cpu().numpy() for f in held[0]], learned.DX)
+    r = np.linalg.norm(b - orc.apply_A(phi, learned.DX)) / np.linalg.norm(b)
+    assert r < 1e-8 and r == pytest.approx(st["rel_res_true"], rel=1e-3)
+    kv.kv_destroy(h)
+    kv.kv_net_destroy(net)
