@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
     ap.add_argument("--step-config", default=None,
-                    help="tx,ty,zc,ns of the step kernel instead of autotuning (profiling runs)")
+                    help="[variant,]tx,ty,zc,ns of the step kernel instead of autotuning "
+                         "(profiling runs; variant 0 one step per sweep, 2 two steps per sweep)")
     ap.add_argument("--cg-tol", type=float, default=1e-8,
                     help="projection tolerance (1e-8 is the workload's; larger values only for "
                          "short profiling runs)")
@@ -308,8 +309,9 @@ def main():
     dt = 0.5 * kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *medium_d)
     h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, *medium_d, stream=stream.cuda_stream)
     if args.step_config:
-        tx, ty, zc, ns = (int(v) for v in args.step_config.split(","))
-        kv.kv_set_step_config(h, 0, tx, ty, zc, ns)
+        vals = [int(v) for v in args.step_config.split(",")]
+        variant, (tx, ty, zc, ns) = (vals[0], vals[1:]) if len(vals) == 5 else (0, vals)
+        kv.kv_set_step_config(h, variant, tx, ty, zc, ns)
         tune_ms = None
     else:
         tune_ms = kv.kv_autotune_step(h, 8)  # picks tile / stages / z chunk; resets the state

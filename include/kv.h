@@ -134,8 +134,11 @@ kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_fie
  *   f_S0 = b0 - D+ phi (forward differences) on every node,
  * and stores F = (dt^2/rho) f_S0 for the time step. fx, fy, fz: dense fields.
  * max_iter <= 0 selects 20 * max(nx, ny, nz). mode: 0 = zero initial guess,
- * 1 = learned initial guess from the net attached with kv_attach_net (the
- * stopping rule is the same); other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
+ * 1 = learned initial guess from the net attached with kv_attach_net, scaled
+ * by the minimal-residual factor alpha = (A phi0).b / |A phi0|^2 (its residual
+ * is never larger than the zero start's; the stopping rule is the same);
+ * 3 = start from the potential of the previous projection on this handle
+ * (zero if there is none); other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
  * pointer to 3*nx*ny*nz floats (component-major) that receives f_S0.
  * stats: NULL or filled. Returns KV_OK, KV_CG_MAXITER, KV_CG_BREAKDOWN or
  * KV_ERR_NONFINITE (the stats say which). A zero right-hand side gives
@@ -232,6 +235,17 @@ kv_status kv_clear_force(kv_handle *h);
  * After each step the sensors record u^{n+1}. Asynchronous.
  */
 kv_status kv_step(kv_handle *h, int n);
+
+/*
+ * General per-step projection (Sec. 3.2: a different body force at each time
+ * step, each projected on its own): project this step's force f^n (fields as
+ * in kv_project_force; mode 0: the CG starts from zero, as the paper's general
+ * solver; mode 3: from the previous step's potential; both stop on tol), then
+ * advance one step with f_S^n (envelope 1 for this step). The projected force stays stored afterwards. stats: NULL or the
+ * projection's statistics. Synchronising.
+ */
+kv_status kv_step_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol, int max_iter,
+                        int mode, kv_cg_stats *stats);
 
 /* Steps taken since the last reset (host-side count). */
 long long kv_steps_taken(kv_handle *h);

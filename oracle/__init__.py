@@ -376,3 +376,27 @@ def conv3d_bwd(x, W, g):
     gb, gbp = _d(np.zeros(cout))
     lib().or_conv3d_bwd(nx, ny, nz, cin, cout, xp, wp, gp, gip, gwp, gbp)
     return gin, gW, gb
+
+
+def xcorr_group_speed(traces, offsets, dt, ref=0):
+    """Group speed from cross-correlation of traces at increasing lateral
+    offsets (Sec. 4.4): the lag of each trace against the reference trace is
+    the argmax of their full cross-correlation, refined by a 3-point parabola;
+    the speed is the least-squares slope of offset against lag.
+    traces: [n_steps, ns]; offsets: (ns,) metres."""
+    tr = np.asarray(traces, np.float64)
+    n = tr.shape[0]
+    a = tr[:, ref] - tr[:, ref].mean()
+    lags = []
+    for s in range(tr.shape[1]):
+        b = tr[:, s] - tr[:, s].mean()
+        cc = np.correlate(b, a, mode="full")  # index n-1 is zero lag
+        m = int(np.argmax(cc))
+        shift = 0.0
+        if 0 < m < len(cc) - 1:
+            den = cc[m - 1] - 2 * cc[m] + cc[m + 1]
+            if den != 0:
+                shift = 0.5 * (cc[m - 1] - cc[m + 1]) / den
+        lags.append((m - (n - 1) + shift) * dt)
+    off = np.asarray(offsets, np.float64)
+    return linear_fit_speed(off - off[ref], np.asarray(lags))

@@ -350,9 +350,17 @@ kv_status kv_set_sensors(kv_handle *h, const int *ijk, int n, int capacity) {
     free_graphs(h);
     if (n == 0 || capacity == 0) return KV_OK;
     kv_status st;
-    if ((st = dalloc(h, &h->sens_dev, (size_t)n * 3 * 4)) != KV_OK) return st;
+    // device layout: [3n (i, j, k)] [nz + 1 plane offsets] [n sensor indices sorted by plane]
+    std::vector<int> tab((size_t)3 * n + h->nz + 1 + n);
+    memcpy(tab.data(), ijk, (size_t)3 * n * 4);
+    int *off = tab.data() + 3 * n, *ord = off + h->nz + 1;
+    for (int s = 0; s < n; ++s) off[ijk[3 * s + 2] + 1]++;
+    for (int k = 0; k < h->nz; ++k) off[k + 1] += off[k];
+    std::vector<int> fill(off, off + h->nz);
+    for (int s = 0; s < n; ++s) ord[fill[ijk[3 * s + 2]]++] = s;
+    if ((st = dalloc(h, &h->sens_dev, tab.size() * 4)) != KV_OK) return st;
     if ((st = dalloc(h, &h->traces, (size_t)capacity * n * 3 * h->esize)) != KV_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(h->sens_dev, ijk, (size_t)n * 3 * 4, cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(h->sens_dev, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->traces, 0, (size_t)capacity * n * 3 * h->esize, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if ((st = cuda_check(h, e, "kv_set_sensors")) != KV_OK) return st;
@@ -395,7 +403,7 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
                            int max_iter, int mode, float *fs_out, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;
     if (h->sticky) return KV_ERR_STATE;
-    if (mode != 0 && mode != 1)
+    if (mode != 0 && mode != 1 && mode != 3)
         return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
     if (mode == 1 && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
         return set_error(h, KV_ERR_STATE, "mode 1 needs a network attached with kv_attach_net that fits the grid");
@@ -412,34 +420,87 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
         if (f[q]->where != KV_SCALAR && (st = stage(h, *f[q], h->fstage + q * h->Np)) != KV_OK) return st;
     free_graphs(h);
     h->have_force = 0;
+    h->g_const_on = 0;
     return project(h, tol, max_iter, mode, fs_out, stats);
+}
+
+kv_status kv_step_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol, int max_iter,
+                        int mode, kv_cg_stats *stats) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    if (mode != 0 && mode != 3) return set_error(h, KV_ERR_ARG, "kv_step_force: mode must be 0 or 3");
+    if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");
+    const kv_field *f[3] = {&fx, &fy, &fz};
+    for (auto *q : f)
+        if (!field_ok(*q) || (q->where == KV_SCALAR && q->value != 0.0))
+            return set_error(h, KV_ERR_ARG, "force components must be arrays or 0");
+    if (max_iter <= 0) max_iter = 20 * std::max(h->nx, std::max(h->ny, h->nz));
+    kv_status st = cuda_check(h, cudaMemsetAsync(h->fstage, 0, 3 * (size_t)h->Np * 4, h->stream),
+                              "kv_step_force");
+    if (st != KV_OK) return st;
+    for (int q = 0; q < 3; ++q)
+        if (f[q]->where != KV_SCALAR && (st = stage(h, *f[q], h->fstage + q * h->Np)) != KV_OK) return st;
+    free_graphs(h);
+    h->have_force = 0;
+    // this step's force, projected on its own (mode 3: from the previous potential)
+    if ((st = project(h, tol, max_iter, mode, nullptr, stats)) != KV_OK) return st;
+    h->g_const_on = 1;
+    st = step_launch(h, h->cur);
+    h->g_const_on = 0;
+    if (st != KV_OK) return st;
+    h->cur = 1 - h->cur;
+    h->steps_host++;
+    return KV_OK;
 }
 
 kv_status kv_clear_force(kv_handle *h) {
     if (!h) return KV_ERR_ARG;
     h->have_force = 0;
+    h->g_const_on = 0;
     free_graphs(h);
     return KV_OK;
 }
+
+namespace {
+// Direct launches of n steps in the handle's current variant (no graph).
+kv_status launch_steps_direct(kv_handle *h, int n) {
+    kv_status st;
+    if (h->precision == KV_FP32 && h->variant == 2) {
+        for (; n >= 2; n -= 2) {
+            if ((st = step2_launch(h, h->cur)) != KV_OK) return st;
+            h->cur = 1 - h->cur;
+            h->steps_host += 2;
+        }
+    }
+    for (; n > 0; --n) {
+        if ((st = step_launch(h, h->cur)) != KV_OK) return st;
+        h->cur = 1 - h->cur;
+        h->steps_host++;
+    }
+    return KV_OK;
+}
+}  // namespace
 
 kv_status kv_step(kv_handle *h, int n) {
     if (!h || n < 0) return set_error(h, KV_ERR_ARG, "kv_step: invalid arguments");
     if (h->sticky) return KV_ERR_STATE;
     kv_status st;
-    const int G = h->graph_steps;
-    if (n >= G && G > 0 && (G % 2) == 0) {
+    const bool two = h->precision == KV_FP32 && h->variant == 2;
+    const int G = h->graph_steps;  // steps per graph; buffer swaps per graph stay even
+    if (n >= G && G > 0 && G % 4 == 0) {
         if (!h->graph[h->cur]) {
-            if (h->precision == KV_FP32 && h->variant == 0 && !h->tma_ready &&
+            if (h->precision == KV_FP32 && h->variant != 1 && !h->tma_ready &&
                 (st = step_prepare(h)) != KV_OK)
                 return st;
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
             if ((st = cuda_check(h, e, "graph capture")) != KV_OK) return st;
             const long long before = h->launches;
-            for (int i = 0; i < G; ++i) {
-                st = step_launch(h, (h->cur + i) & 1);
-                if (st != KV_OK) break;
-            }
+            const int cur0 = h->cur;
+            const long long steps0 = h->steps_host;
+            st = launch_steps_direct(h, G);
+            h->cur = cur0;  // the capture only records the launches
+            h->steps_host = steps0;
             h->launches = before;
             e = cudaStreamEndCapture(h->stream, &graph);
             if (st != KV_OK) {
@@ -454,17 +515,12 @@ kv_status kv_step(kv_handle *h, int n) {
         while (n >= G) {
             if ((st = cuda_check(h, cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch")) != KV_OK)
                 return st;
-            h->launches += G;
+            h->launches += two ? G / 2 : G;
             h->steps_host += G;
             n -= G;
         }
     }
-    for (int i = 0; i < n; ++i) {
-        if ((st = step_launch(h, h->cur)) != KV_OK) return st;
-        h->cur = 1 - h->cur;
-        h->steps_host++;
-    }
-    return KV_OK;
+    return launch_steps_direct(h, n);
 }
 
 long long kv_steps_taken(kv_handle *h) { return h ? h->steps_host : 0; }
@@ -521,11 +577,12 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
 
 kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, int ns) {
     if (!h) return KV_ERR_ARG;
-    if (variant > 1 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
+    if (variant > 2 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
         (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 16) || (ns > 0 && ns != 4 && ns != 6 && ns != 8))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant, tile or stage count");
     const int ntx = tx > 0 ? tx : h->tx, nty = ty > 0 ? ty : h->ty;
-    if (ntx * nty / 4 < 64 || ntx * nty / 4 > 512)
+    const int nvar = variant >= 0 ? variant : h->variant;
+    if (nvar != 2 && (ntx * nty / 4 < 64 || ntx * nty / 4 > 512))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: tile %dx%d out of range", ntx, nty);
     cudaStreamSynchronize(h->stream);
     const int old[5] = {h->variant, h->tx, h->ty, h->zc, h->ns_stages};
@@ -536,7 +593,7 @@ kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, 
     if (ns > 0) h->ns_stages = ns;
     h->tma_ready = 0;
     free_graphs(h);
-    if (h->precision == KV_FP32 && h->variant == 0) {
+    if (h->precision == KV_FP32 && h->variant != 1) {
         kv_status st = step_prepare(h);
         if (st != KV_OK) {  // keep the previous, valid configuration
             h->variant = old[0];
@@ -568,28 +625,31 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
         if (best_ms) *best_ms = 0.0;
         return kv_reset(h);
     }
-    struct Cand { int tx, ty, ns, zc; };
+    struct Cand { int variant, tx, ty, ns, zc; };
     static const int tiles[][2] = {{32, 8}, {32, 16}, {64, 4}, {64, 8}, {64, 16}, {128, 2}, {128, 4}, {128, 8}};
-    static const int stages[] = {4, 6, 8};
+    static const int tiles2[][2] = {{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}};
     static const int zcs[] = {16, 32, 64};
     std::vector<Cand> cands;
     for (auto &t : tiles)
-        for (int ns : stages)
-            for (int zc : zcs) cands.push_back({t[0], t[1], ns, zc});
+        for (int ns : {4, 6, 8})
+            for (int zc : zcs) cands.push_back({0, t[0], t[1], ns, zc});
+    for (auto &t : tiles2)
+        for (int ns : {4, 6})
+            for (int zc : zcs) cands.push_back({2, t[0], t[1], ns, zc});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(h, KV_ERR_CUDA, "kv_autotune_step: cudaEventCreate failed");
     const int saved[5] = {h->variant, h->tx, h->ty, h->zc, h->ns_stages};
     double best = INFINITY;
-    Cand pick = {saved[1], saved[2], saved[4], saved[3]};
+    Cand pick = {saved[0], saved[1], saved[2], saved[4], saved[3]};
     kv_status st = KV_OK;
+    const int trial = trial_steps + (trial_steps & 1);  // even: whole two-step launches
     for (const Cand &c : cands) {
-        if (kv_set_step_config(h, 0, c.tx, c.ty, c.zc, c.ns) != KV_OK) continue;  // e.g. too much smem
-        for (int i = 0; i < 2 && st == KV_OK; ++i) st = step_launch(h, i & 1);
+        if (kv_set_step_config(h, c.variant, c.tx, c.ty, c.zc, c.ns) != KV_OK) continue;
+        if ((st = launch_steps_direct(h, 2)) != KV_OK) break;
         cudaEventRecord(e0, h->stream);
-        for (int i = 0; i < trial_steps && st == KV_OK; ++i) st = step_launch(h, i & 1);
+        if ((st = launch_steps_direct(h, trial)) != KV_OK) break;
         cudaEventRecord(e1, h->stream);
-        if (st != KV_OK) break;
         if ((st = cuda_check(h, cudaEventSynchronize(e1), "kv_autotune_step")) != KV_OK) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -601,8 +661,8 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != KV_OK) return st;
-    if ((st = kv_set_step_config(h, 0, pick.tx, pick.ty, pick.zc, pick.ns)) != KV_OK) return st;
-    if (best_ms) *best_ms = best / trial_steps;
+    if ((st = kv_set_step_config(h, pick.variant, pick.tx, pick.ty, pick.zc, pick.ns)) != KV_OK) return st;
+    if (best_ms) *best_ms = best / trial;
     return kv_reset(h);
 }
 

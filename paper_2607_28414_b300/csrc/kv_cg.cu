@@ -724,6 +724,39 @@ static kv_status sync_read(kv_handle *h) {
     return cuda_check(h, e, "projection poll");
 }
 
+// Minimal-residual scaling of a warm start phi0: alpha = (A phi0).b / |A phi0|^2
+// minimises |b - alpha A phi0|, so the starting residual is never larger than
+// the zero start's (alpha = 0).
+__global__ void __launch_bounds__(kCgBX *kCgBY)
+k_warm_dots(const double *__restrict__ phi, const double *__restrict__ b, CgParams p) {
+    int i, j;
+    node_of(i, j);
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz);
+    double a = 0.0, c = 0.0;
+    if (i < p.nx && j < p.ny) {
+        for (int k = k0; k < k1; ++k) {
+            if (!is_interior(i, j, k, p.nx, p.ny, p.nz)) continue;
+            const long long q = k * sz + j * sy + i;
+            const double s = ((phi[q - 1] + phi[q + 1]) + (phi[q - sy] + phi[q + sy])) +
+                             (phi[q - sz] + phi[q + sz]);
+            const double Ap = (6.0 * phi[q] - s) * p.inv_dx2;
+            a += Ap * b[q];
+            c += Ap * Ap;
+        }
+    }
+    double v[2] = {a, c}, sm[2];
+    if (last_block_sums<2>(p, v, sm) && threadIdx.x == 0) {
+        p.scal[kWarmA] = sm[0];
+        p.scal[kWarmC] = sm[1];
+    }
+}
+
+__global__ void k_scale(double *__restrict__ phi, long long Np, double alpha) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < Np; c += (long long)gridDim.x * blockDim.x)
+        phi[c] *= alpha;
+}
+
 // Pitched double <-> dense float (the learned warm start works on dense grids).
 __global__ void k_pitched_to_dense(const double *__restrict__ a, float *__restrict__ o, int nx, int ny,
                                    int nz, int px) {
@@ -787,7 +820,8 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p[0], 0, h->Np * sizeof(T), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p[1], 0, h->Np * sizeof(T), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->e, 0, h->Np * sizeof(T), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s);
+    if (e == cudaSuccess && !(mode == 3 && h->phi_valid))  // mode 3 starts from the previous phi
+        e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s);
     if (e != cudaSuccess) return cuda_check(h, e, "projection memset");
     long long *ci = h->ctrl_host;
     double *si = h->scal_host;
@@ -824,7 +858,18 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
         if (ns != KV_OK) return set_error(h, ns, "warm start: network inference failed");
         k_dense_to_pitched<<<fold_blocks, 256, 0, s>>>(kv_net_stage_phi(h->net), h->phi, h->nx, h->ny, h->nz,
                                                        h->px);
-        h->launches += 2;
+        k_warm_dots<<<grid, nt, 0, s>>>(h->phi, h->b, p);
+        h->launches += 3;
+        if ((ks = sync_read(h)) != KV_OK) return ks;
+        const double wa = h->scal_host[kWarmA], wc = h->scal_host[kWarmC];
+        const double alpha = (isfinite(wa) && isfinite(wc) && wc > 0.0) ? wa / wc : 0.0;
+        k_scale<<<fold_blocks, 256, 0, s>>>(h->phi, h->Np, alpha);
+        h->launches++;
+        h->warm_alpha = alpha;
+    }
+    if (bb == 0.0) {  // zero right-hand side: phi = 0 whatever the start
+        if ((e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s)) != cudaSuccess)
+            return cuda_check(h, e, "projection memset");
     }
     if (!isfinite(bb)) {
         status = KV_ERR_NONFINITE;
@@ -867,6 +912,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     h->launches++;
     if ((ks = sync_read(h)) != KV_OK) return ks;
     h->have_force = 1;
+    h->phi_valid = (status == KV_OK);
     if (h->ctrl_host[kErrFlags] & 1) {
         h->sticky = 1;
         return set_error(h, KV_ERR_TIMEOUT, "a bounded device wait timed out in a CG kernel");

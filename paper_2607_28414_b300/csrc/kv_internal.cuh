@@ -53,6 +53,8 @@ enum CgScalar {
     kTol = 7,     // tolerance on sqrt(true2 / bb)
     kInner = 8,   // inner-cycle reduction factor on ||r||
     kRRLast = 9,  // last recursive r.r (statistics)
+    kWarmA = 10,  // (A phi0).b of a warm start
+    kWarmC = 11,  // |A phi0|^2 of a warm start
     kCgScalars = 16
 };
 
@@ -62,8 +64,12 @@ struct StepParams {
     double A, B;         // homogeneous coefficients (dt^2 G/(rho dx^2), dt eta/(rho dx^2))
     const float *g;      // envelope table on the device
     int n_g;
+    int g_const_on;      // 1: use g_const for every step instead of the table
+    float g_const;
     long long *ctrl;     // control block
     const int *sensors;  // 3 * ns node indices
+    const int *sens_off; // nz + 1 offsets into sens_ord: sensors of plane k
+    const int *sens_ord; // sensor indices sorted by plane
     int ns;
     void *traces;        // [cap][ns][3]
     int cap;
@@ -157,6 +163,9 @@ struct kv_handle {
     int graph_steps;
 
     struct kv_net *net;    // learned warm start (kv_attach_net), not owned
+    double warm_alpha;     // scaling applied to the last learned start
+    int g_const_on;        // steps use g = 1 (kv_step_force)
+    int phi_valid;         // phi holds the last projection's potential
 
     long long launches;
     int sticky;
@@ -180,6 +189,7 @@ kv_status cuda_check(kv_handle *h, cudaError_t e, const char *what);
 // Step kernels (kv_step.cu)
 kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attributes
 kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
+kv_status step2_launch(kv_handle *h, int from_buffer); // two steps (variant 2), one buffer swap
 
 // Batched step (kv_step.cu)
 kv_status batch_kernel_for(int tx, int ty, int ns, bool het, void **kernel, size_t *smem, int *nt);

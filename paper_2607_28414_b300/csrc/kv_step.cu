@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128)
 k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ coef,
              const T *__restrict__ F, StepParams p) {
     const long long step = __ldcg(&p.ctrl[kStep]);
-    const T g = (step < p.n_g) ? T(p.g[step]) : T(0);
+    const T g = p.g_const_on ? T(p.g_const) : (step < p.n_g) ? T(p.g[step]) : T(0);
     const bool force = (g != T(0));
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = 1 + blockIdx.y;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
     const int k1 = min(k0 + p.zc, p.nz - 1);  // planes k0..k1-1 are computed
     const int kb = k0 - 1;                     // first staged plane
     const long long step = __ldcg(&p.ctrl[kStep]);
-    const float g = (step < p.n_g) ? p.g[step] : 0.f;
+    const float g = p.g_const_on ? p.g_const : (step < p.n_g) ? p.g[step] : 0.f;
     const bool force = (g != 0.f);
     const uint32_t bar0 = smem_u32(bars);
 
@@ -283,6 +283,272 @@ k_step_batch(const BatchCase *__restrict__ cases, int ncases, int from) {
 }
 
 // ---------------------------------------------------------------------------
+// Two steps per sweep (temporal blocking), FP32.
+//
+// Each z-march iteration k first computes the intermediate state (u, d)^{n+1}
+// of plane k+1 over the block's tile plus a one-node ring (rows y0-1..y0+TY,
+// columns x0-4..x0+TX+3 in float4 groups) into a 3-plane shared-memory ring,
+// then the final state (u, d)^{n+2} of plane k over the tile, written to global
+// memory. The state at step n arrives by TMA with a 2-row y halo and the
+// aligned 4-column x halo. Every node of both levels goes through kv_update
+// with the same neighbour order as the single-step kernels, so two steps here
+// are bit-identical to two single steps. Intermediate nodes outside the grid or
+// on the Dirichlet layer are 0. The sensors of the intermediate step are
+// recorded by the block that owns their node (per-plane sensor index); the
+// last block records the final step and advances the step counter by two.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, bool HET>
+struct Tile2 {
+    static constexpr int BX = TX + 8;
+    static constexpr int BYI = TY + 4;
+    static constexpr int BYM = TY + 2;
+    static constexpr int IN_F = BX * BYI;
+    static constexpr int MID_F = BX * BYM;
+    static constexpr int IN_STATE = 6 * IN_F;
+    static constexpr int IN_COEF = HET ? 2 * MID_F : 0;
+    static constexpr int IN_STAGE = (IN_STATE + IN_COEF + 31) / 32 * 32;
+    static constexpr int MID_STAGE = (6 * MID_F + 31) / 32 * 32;
+    static constexpr int GXI = BX / 4;
+    static constexpr int MID_GROUPS = GXI * BYM;
+    static constexpr int GX = TX / 4;
+    static constexpr int OUT_GROUPS = GX * TY;
+    static constexpr int NT = 128;
+};
+
+template <typename T>
+__device__ __forceinline__ void step_epilogue_n(const T *out, const StepParams &p, long long step, int nsteps) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t =
+            atomicAdd(reinterpret_cast<unsigned long long *>(&p.ctrl[kStepTicket]), 1ull);
+        s_last = (t == (unsigned long long)(p.nblocks - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const long long row = step + nsteps - 1;
+    if (row < p.cap) {
+        T *tr = reinterpret_cast<T *>(p.traces) + (size_t)row * p.ns * 3;
+        for (int s = threadIdx.x; s < p.ns; s += blockDim.x) {
+            const int i = p.sensors[3 * s], j = p.sensors[3 * s + 1], k = p.sensors[3 * s + 2];
+            const size_t c = ((size_t)k * p.ny + j) * p.px + i;
+            for (int comp = 0; comp < 3; ++comp) tr[3 * s + comp] = __ldcg(out + comp * p.Np + c);
+        }
+    } else if (threadIdx.x == 0 && p.ns > 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 2ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        p.ctrl[kStepTicket] = 0;
+        p.ctrl[kStep] = step + nsteps;
+    }
+}
+
+template <int TX, int TY, int NS, bool HET>
+__global__ void __launch_bounds__(128)
+k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
+            const float *__restrict__ F, float *__restrict__ out, StepParams p) {
+    using T2 = Tile2<TX, TY, HET>;
+    extern __shared__ __align__(128) float smem[];
+    float *inr = smem;                                 // NS input stages
+    float *mid = smem + NS * T2::IN_STAGE;             // 3 intermediate planes
+    uint64_t *bars = reinterpret_cast<uint64_t *>(mid + 3 * T2::MID_STAGE);
+    const uint32_t bar0 = smem_u32(bars);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
+    const int k0 = 1 + blockIdx.z * p.zc;
+    const int k1 = min(k0 + p.zc, p.nz - 1);  // output planes k0..k1-1
+    const int qb = k0 - 2;                     // first staged input plane (may be -1)
+    const long long step = __ldcg(&p.ctrl[kStep]);
+    const float g0 = p.g_const_on ? p.g_const : (step < p.n_g) ? p.g[step] : 0.f;
+    const float g1 = p.g_const_on ? p.g_const : (step + 1 < p.n_g) ? p.g[step + 1] : 0.f;
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto slot = [&](int q) { return (q - qb) % NS; };
+    auto par = [&](int q) { return (uint32_t)(((q - qb) / NS) & 1); };
+    auto issue = [&](int q) {
+        const uint32_t bar = bar0 + 8 * slot(q);
+        float *st = inr + slot(q) * T2::IN_STAGE;
+        mbar_expect_tx(bar, (T2::IN_STATE + T2::IN_COEF) * 4);
+        tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 2, q, 0, bar);
+        if (HET) tma_load_4d(smem_u32(st + T2::IN_STATE), &tm_coef, x0 - 4, y0 - 1, q, 0, bar);
+    };
+    int next_issue = qb;
+    if (tid == 0)
+        for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue(next_issue);
+    bool ok = true;
+
+    // intermediate plane j (needs input planes j-1, j, j+1 staged)
+    auto compute_mid = [&](int j) {
+        float *mj = mid + ((j - (k0 - 1)) % 3) * T2::MID_STAGE;
+        const bool plane_in = (j >= 1 && j <= p.nz - 2);
+        const float *sc = inr + slot(j) * T2::IN_STAGE;
+        const float *sm = plane_in ? inr + slot(j - 1) * T2::IN_STAGE : sc;
+        const float *sp = plane_in ? inr + slot(j + 1) * T2::IN_STAGE : sc;
+        for (int gi = tid; gi < T2::MID_GROUPS; gi += T2::NT) {
+            const int r = gi / T2::GXI, cg = gi % T2::GXI;
+            const int y = y0 - 1 + r, x = x0 - 4 + 4 * cg;
+            const int oi = (r + 1) * T2::BX + 4 * cg;  // input tile offset of this group
+            const int om = r * T2::BX + 4 * cg;        // intermediate / coefficient tile offset
+            const bool row_in = plane_in && y >= 1 && y <= p.ny - 2;
+            bool m[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) m[e] = row_in && (x + e >= 1) && (x + e <= p.nx - 2);
+            float4 A4, B4;
+            if (HET) {
+                A4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + om);
+                B4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + T2::MID_F + om);
+            } else {
+                A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+                B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+            }
+            float4 ctr[6], sum[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const float *fc = sc + f * T2::IN_F + oi;
+                const float4 c = *reinterpret_cast<const float4 *>(fc);
+                const float4 ym = *reinterpret_cast<const float4 *>(fc - T2::BX);
+                const float4 yp = *reinterpret_cast<const float4 *>(fc + T2::BX);
+                const float4 zm = *reinterpret_cast<const float4 *>(sm + f * T2::IN_F + oi);
+                const float4 zp = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
+                const float left = (cg == 0) ? 0.f : fc[-1];
+                const float right = (cg == T2::GXI - 1) ? 0.f : fc[4];
+                float4 s4;
+                s4.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+                s4.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+                s4.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+                s4.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+                ctr[f] = c;
+                sum[f] = s4;
+            }
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                float Fv[4] = {0.f, 0.f, 0.f, 0.f};
+                if (g0 != 0.f) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (m[e]) Fv[e] = F[comp * p.Np + (long long)j * sz + (long long)y * sy + x + e];
+                }
+                const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
+                float4 uo, dn;
+                kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g0, Fv[0], uo.x, dn.x);
+                kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g0, Fv[1], uo.y, dn.y);
+                kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g0, Fv[2], uo.z, dn.z);
+                kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g0, Fv[3], uo.w, dn.w);
+                if (!m[0]) uo.x = dn.x = 0.f;
+                if (!m[1]) uo.y = dn.y = 0.f;
+                if (!m[2]) uo.z = dn.z = 0.f;
+                if (!m[3]) uo.w = dn.w = 0.f;
+                *reinterpret_cast<float4 *>(mj + comp * T2::MID_F + om) = uo;
+                *reinterpret_cast<float4 *>(mj + (3 + comp) * T2::MID_F + om) = dn;
+            }
+        }
+    };
+
+    for (int k = k0; k < k1; ++k) {
+        if (k == k0) {
+            for (int q = qb; q <= k0 + 1; ++q) ok &= mbar_wait_bounded(bar0 + 8 * slot(q), par(q));
+            compute_mid(k0 - 1);
+            compute_mid(k0);
+            __syncthreads();  // planes k0-2 and k0-1 are free: the oldest needed is k0
+            if (tid == 0) {
+                fence_proxy_async();
+                for (; next_issue <= min(k1 + 1, k0 + NS - 1); ++next_issue) issue(next_issue);
+            }
+        }
+        ok &= mbar_wait_bounded(bar0 + 8 * slot(k + 2), par(k + 2));
+        compute_mid(k + 1);
+        __syncthreads();
+        // sensors of the intermediate step owned by this block (plane k)
+        if (p.ns > 0 && step < p.cap) {
+            const float *mk = mid + ((k - (k0 - 1)) % 3) * T2::MID_STAGE;
+            float *tr = reinterpret_cast<float *>(p.traces) + (size_t)step * p.ns * 3;
+            for (int q = p.sens_off[k] + tid; q < p.sens_off[k + 1]; q += T2::NT) {
+                const int s = p.sens_ord[q];
+                const int i = p.sensors[3 * s], jj = p.sensors[3 * s + 1];
+                if (i >= x0 && i < x0 + TX && jj >= y0 && jj < y0 + TY && jj <= p.ny - 2)
+                    for (int comp = 0; comp < 3; ++comp)
+                        tr[3 * s + comp] = mk[comp * T2::MID_F + (jj - y0 + 1) * T2::BX + (i - x0 + 4)];
+            }
+        }
+        // final step of plane k from intermediate planes k-1, k, k+1
+        const float *mc = mid + ((k - (k0 - 1)) % 3) * T2::MID_STAGE;
+        const float *mm = mid + ((k - 1 - (k0 - 1)) % 3) * T2::MID_STAGE;
+        const float *mp = mid + ((k + 1 - (k0 - 1)) % 3) * T2::MID_STAGE;
+        const float *cs = inr + slot(k) * T2::IN_STAGE + T2::IN_STATE;  // coefficients of plane k
+        for (int go = tid; go < T2::OUT_GROUPS; go += T2::NT) {
+            const int r = go / T2::GX, gx = go % T2::GX;
+            const int y = y0 + r, x = x0 + 4 * gx;
+            if (y > p.ny - 2 || x >= p.px) continue;
+            const int om = (r + 1) * T2::BX + 4 + 4 * gx;
+            float4 A4, B4;
+            if (HET) {
+                A4 = *reinterpret_cast<const float4 *>(cs + om);
+                B4 = *reinterpret_cast<const float4 *>(cs + T2::MID_F + om);
+            } else {
+                A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+                B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+            }
+            const bool m0 = (x >= 1) && (x <= p.nx - 2), m1 = (x + 1 <= p.nx - 2);
+            const bool m2 = (x + 2 <= p.nx - 2), m3 = (x + 3 <= p.nx - 2);
+            float4 ctr[6], sum[6];
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const float *fc = mc + f * T2::MID_F + om;
+                const float4 c = *reinterpret_cast<const float4 *>(fc);
+                const float4 ym = *reinterpret_cast<const float4 *>(fc - T2::BX);
+                const float4 yp = *reinterpret_cast<const float4 *>(fc + T2::BX);
+                const float4 zm = *reinterpret_cast<const float4 *>(mm + f * T2::MID_F + om);
+                const float4 zp = *reinterpret_cast<const float4 *>(mp + f * T2::MID_F + om);
+                const float left = fc[-1], right = fc[4];
+                float4 s4;
+                s4.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+                s4.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+                s4.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+                s4.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+                ctr[f] = c;
+                sum[f] = s4;
+            }
+            const long long gbase = k * sz + (long long)y * sy + x;
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g1 != 0.f) F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
+                const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
+                float4 uo, dn;
+                kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g1, F4.x, uo.x, dn.x);
+                kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g1, F4.y, uo.y, dn.y);
+                kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g1, F4.z, uo.z, dn.z);
+                kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g1, F4.w, uo.w, dn.w);
+                if (!m0) uo.x = dn.x = 0.f;
+                if (!m1) uo.y = dn.y = 0.f;
+                if (!m2) uo.z = dn.z = 0.f;
+                if (!m3) uo.w = dn.w = 0.f;
+                *reinterpret_cast<float4 *>(out + comp * p.Np + gbase) = uo;
+                *reinterpret_cast<float4 *>(out + (3 + comp) * p.Np + gbase) = dn;
+            }
+        }
+        __syncthreads();  // input plane k and intermediate plane k-1 are free
+        if (tid == 0) {
+            fence_proxy_async();
+            for (; next_issue <= min(k1 + 1, k + NS); ++next_issue) issue(next_issue);
+        }
+    }
+    if (__syncthreads_or(!ok) && tid == 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
+        for (int q = qb; q < next_issue; ++q) mbar_wait_bounded(bar0 + 8 * slot(q), par(q));
+    }
+    step_epilogue_n<float>(out, p, step, 2);
+}
+
+// ---------------------------------------------------------------------------
 // Small kernels: medium fold, initial velocity
 // ---------------------------------------------------------------------------
 // Grid: (ceil(px/128), ny, nz), block 128.
@@ -409,6 +675,35 @@ static bool bpick_tile(int tx, int ty, bool het, BatchKernel *k) {
            bpick<128, 4, NS>(tx, ty, NS, het, k) || bpick<128, 8, NS>(tx, ty, NS, het, k);
 }
 
+template <int TX, int TY, int NS>
+static bool pick2(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (tx != TX || ty != TY || ns != NS) return false;
+    if (het) {
+        *k = k_step2_tma<TX, TY, NS, true>;
+        *smem = (NS * Tile2<TX, TY, true>::IN_STAGE + 3 * Tile2<TX, TY, true>::MID_STAGE) * 4 + NS * 8;
+    } else {
+        *k = k_step2_tma<TX, TY, NS, false>;
+        *smem = (NS * Tile2<TX, TY, false>::IN_STAGE + 3 * Tile2<TX, TY, false>::MID_STAGE) * 4 + NS * 8;
+    }
+    *nt = 128;
+    return true;
+}
+
+template <int NS>
+static bool pick2_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    return pick2<32, 4, NS>(tx, ty, NS, het, k, smem, nt) || pick2<32, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick2<64, 4, NS>(tx, ty, NS, het, k, smem, nt) || pick2<64, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick2<128, 4, NS>(tx, ty, NS, het, k, smem, nt);
+}
+
+static bool tma2_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    switch (ns) {
+        case 4: return pick2_tile<4>(tx, ty, het, k, smem, nt);
+        case 6: return pick2_tile<6>(tx, ty, het, k, smem, nt);
+        default: return false;
+    }
+}
+
 static bool tma_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
     switch (ns) {
         case 4: return pick_tile<4>(tx, ty, het, k, smem, nt);
@@ -420,10 +715,29 @@ static bool tma_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_
 
 kv_status step_prepare(kv_handle *h) {
     h->tma_ready = 0;
-    if (h->precision != KV_FP32 || h->variant != 0) return KV_OK;
+    if (h->precision != KV_FP32 || h->variant == 1) return KV_OK;
     TmaKernel k;
     size_t smem;
     int nt;
+    if (h->variant == 2) {
+        if (!tma2_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
+            return set_error(h, KV_ERR_ARG, "no two-step kernel for tile %dx%d with %d stages", h->tx, h->ty,
+                             h->ns_stages);
+        if (smem > 227 * 1024)
+            return set_error(h, KV_ERR_ARG, "two-step tile %dx%d with %d stages needs %zu bytes of shared memory",
+                             h->tx, h->ty, h->ns_stages, smem);
+        kv_status st;
+        for (int b = 0; b < 2; ++b)
+            if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 4, 6)) != KV_OK)
+                return st;
+        if (h->het && (st = encode_tensor_4d(h, &h->tm_coef, h->coef, 2, h->tx + 8, h->ty + 2, 2)) != KV_OK)
+            return st;
+        if (!h->het) h->tm_coef = h->tm_state[0];
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(step2)");
+        h->tma_ready = 1;
+        return KV_OK;
+    }
     if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
         return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d with %d stages", h->tx,
                          h->ty, h->ns_stages);
@@ -454,14 +768,36 @@ static StepParams make_params(kv_handle *h, int nblocks) {
     p.B = h->B_s;
     p.g = h->g_dev;
     p.n_g = h->have_force ? h->n_g : 0;
+    p.g_const_on = h->have_force && h->g_const_on;
+    p.g_const = 1.f;
     p.ctrl = h->ctrl;
     p.sensors = h->sens_dev;
+    p.sens_off = h->sens_dev ? h->sens_dev + 3 * h->ns : nullptr;
+    p.sens_ord = h->sens_dev ? h->sens_dev + 3 * h->ns + h->nz + 1 : nullptr;
     p.ns = h->ns;
     p.traces = h->traces;
     p.cap = h->cap;
     p.zc = h->zc;
     p.nblocks = nblocks;
     return p;
+}
+
+// Two steps from state[from] into state[1 - from] (variant 2).
+kv_status step2_launch(kv_handle *h, int from) {
+    if (!h->tma_ready) {
+        kv_status st = step_prepare(h);
+        if (st != KV_OK) return st;
+    }
+    TmaKernel k;
+    size_t smem;
+    int nt;
+    tma2_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt);
+    dim3 grid((h->px + h->tx - 1) / h->tx, (h->ny - 2 + h->ty - 1) / h->ty, (h->nz - 2 + h->zc - 1) / h->zc);
+    StepParams p = make_params(h, grid.x * grid.y * grid.z);
+    k<<<grid, nt, smem, h->stream>>>(h->tm_state[from], h->tm_coef, (const float *)h->F,
+                                     (float *)h->state[1 - from], p);
+    h->launches++;
+    return cuda_check(h, cudaGetLastError(), "step2 launch");
 }
 
 kv_status step_launch(kv_handle *h, int from) {

@@ -365,3 +365,30 @@ def random_gaussian_forces_torch(n_fields, shape, dx, seed, device, speckle_sigm
         speck = torch.exp(speckle_sigma * torch.randn((nz, ny, nx), generator=g, device=device)
                           - 0.5 * speckle_sigma ** 2)
         yield tuple((fc * speck).contiguous() for fc in f)
+
+
+def qiba_phantom(G, nx=240, ny=200, nz=200, dx=0.25 * MM, x_f=30 * MM, sigma=(4.3 * MM, 0.62 * MM, 1.1 * MM),
+                 t_push=167e-6, n_steps=None, offsets=(4 * MM, 14 * MM), name=None):
+    """QIBA-shaped elastic phantom (Sec. 4.4): homogeneous G, rho = 1000, eta = 0;
+    Gaussian body force along x (axial) b = A exp(-((x - x_f)/sx)^2 - (y/sy)^2 -
+    (z/sz)^2) with 1/e widths (4.3, 0.62, 1.1) mm, focus at x_f = 30 mm on the
+    y-z centre line, pushed for 167 us; sensors every node along y (lateral) at
+    the focal depth from offsets[0] to offsets[1]. n_steps defaults to the time
+    the shear wave needs to pass the farthest sensor plus its width."""
+    cj, ck = ny // 2, nz // 2
+    i_f = int(round(x_f / dx))
+    x = ((np.arange(nx) - i_f) * dx)[None, None, :]
+    y = ((np.arange(ny) - cj) * dx)[None, :, None]
+    z = ((np.arange(nz) - ck) * dx)[:, None, None]
+    bx = 1e3 * np.exp(-(x / sigma[0]) ** 2 - (y / sigma[1]) ** 2 - (z / sigma[2]) ** 2)
+    bx = np.ascontiguousarray(np.broadcast_to(bx, (nz, ny, nx)), dtype=np.float32)
+    zero = np.zeros((nz, ny, nx), np.float32)
+    j0, j1 = cj + int(round(offsets[0] / dx)), cj + int(round(offsets[1] / dx))
+    sensors = line_sensors((i_f, j0, ck), 1, j1 + 1, 1)
+    c = np.sqrt(G / 1000.0)
+    if n_steps is None:
+        n_steps = 0  # set by the caller from dt: (offsets[1] + 6 mm) / c + t_push
+    w = Workload(name or f"qiba_G{G / 1e3:.0f}kPa_{nx}x{ny}x{nz}", nx, ny, nz, dx, float(G), 1000.0, 0.0,
+                 (bx, zero, zero.copy()), t_push, n_steps, sensors, 1e-8,
+                 extra={"offsets_m": (np.arange(j0, j1 + 1) - cj) * dx, "t_window_s": (offsets[1] + 6 * MM) / c + t_push})
+    return w

@@ -84,6 +84,7 @@ def lib():
         L.kv_set_initial_velocity.argtypes = [H, F, F, F]
         L.kv_project_force.argtypes = [H, F, F, F, d, i, i, vp, ctypes.POINTER(KvCgStats)]
         L.kv_clear_force.argtypes = [H]
+        L.kv_step_force.argtypes = [H, F, F, F, d, i, i, ctypes.POINTER(KvCgStats)]
         L.kv_step.argtypes = [H, i]
         L.kv_steps_taken.argtypes = [H]
         L.kv_steps_taken.restype = ctypes.c_longlong
@@ -122,7 +123,7 @@ def lib():
         L.kv_nn_conv3d_bwd_weight.argtypes = [i, i, i, i, i, vp, vp, vp, vp, vp]
         for name in ("kv_stable_dt", "kv_create", "kv_set_medium", "kv_set_envelope",
                      "kv_set_sensors", "kv_reset", "kv_set_initial_velocity", "kv_project_force",
-                     "kv_clear_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
+                     "kv_clear_force", "kv_step_force", "kv_step", "kv_read_traces", "kv_read_field", "kv_sync",
                      "kv_set_step_config", "kv_get_step_config", "kv_autotune_step",
                      "kv_destroy", "kv_project_force_noalloc", "kv_batch_create",
                      "kv_batch_set_config", "kv_batch_get_config", "kv_batch_autotune",
@@ -263,6 +264,16 @@ def kv_project_force_noalloc(nx, ny, nz, dx, fx, fy, fz, tol, fs_out, max_iter=0
                                         ptrs[2], float(tol), int(max_iter), ptrs[3],
                                         ctypes.byref(st), s)
     _check(rc, None)
+    return st.as_dict()
+
+
+def kv_step_force(h, fx, fy, fz, tol, max_iter=0, mode=3):
+    """One step with this step's force projected on its own (mode 0: CG from
+    zero, mode 3: from the previous potential); returns the projection's stats."""
+    keep = []
+    st = KvCgStats()
+    _check(lib().kv_step_force(h, field(fx, keep), field(fy, keep), field(fz, keep), float(tol),
+                               int(max_iter), int(mode), ctypes.byref(st)), h)
     return st.as_dict()
 
 

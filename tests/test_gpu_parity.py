@@ -120,13 +120,53 @@ def test_tma_tiles_match_plain_kernel_bitwise(device, het):
     assert ran >= 36
 
 
+TILES2 = [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4)]
+
+
+@pytest.mark.parametrize("het", [True, False])
+@pytest.mark.parametrize("n_steps", [60, 61])
+def test_two_step_kernel_matches_plain_kernel_bitwise(device, het, n_steps):
+    """Temporal blocking (two steps per sweep, variant 2) reproduces single
+    steps bit for bit, including the intermediate step's sensor records and an
+    odd step count (the last step single)."""
+    w = ragged_workload(het=het)
+    v0 = inputs.curl_gaussian_velocity(w.nx, w.ny, w.nz, w.dx, sigma=1e-3, envelope="xyz")
+    ref_tr, ref_f = run_variant(w, {"variant": 1}, n_steps, v0)
+    for tx, ty in TILES2:
+        for ns in (4, 6):
+            for zc in (3, 64):
+                try:
+                    tr, f = run_variant(w, {"variant": 2, "tx": tx, "ty": ty, "zc": zc, "ns": ns},
+                                        n_steps, v0)
+                except kv.KvError as e:
+                    assert e.status == kv.KV_ERR_ARG and "shared memory" in str(e)
+                    continue
+                assert np.array_equal(tr, ref_tr), (tx, ty, ns, zc)
+                assert np.array_equal(f, ref_f), (tx, ty, ns, zc)
+
+
+def test_two_step_graph_replay_matches_direct(device):
+    w = ragged_workload()
+    a = Solver(w, n_steps=75, step_config={"variant": 2, "tx": 64, "ty": 4, "zc": 16, "ns": 4})
+    a.project()
+    a.step(75)  # one graph of 32 steps (16 two-step launches) + 21 pairs + 1 single
+    ta = a.read_traces().cpu().numpy().copy()
+    b = Solver(w, n_steps=75, step_config={"variant": 1})
+    b.project()
+    b.step(75)
+    assert np.array_equal(ta, b.read_traces().cpu().numpy())
+    assert kv.kv_steps_taken(a.h) == 75
+    a.close()
+    b.close()
+
+
 def test_autotuner_picks_a_valid_config_and_resets(device):
     w = ragged_workload()
     s = Solver(w, n_steps=20)
     s.project()
     ms = kv.kv_autotune_step(s.h, 4)
     cfg = kv.kv_get_step_config(s.h)
-    assert ms > 0 and cfg["variant"] == 0 and cfg["ns"] in (4, 6, 8)
+    assert ms > 0 and cfg["variant"] in (0, 2) and cfg["ns"] in (4, 6, 8)
     assert kv.kv_steps_taken(s.h) == 0
     s.step()
     tr = s.read_traces().cpu().numpy().copy()
@@ -344,8 +384,11 @@ def test_cg_status_paths(device):
     st = kv.kv_project_force(s.h, *bad, 1e-8, 0, 0, None, check=False)
     assert st["rc"] == kv.KV_ERR_NONFINITE
     with pytest.raises(kv.KvError) as e:
-        kv.kv_project_force(s.h, *s.force, 1e-8, 0, 1)
+        kv.kv_project_force(s.h, *s.force, 1e-8, 0, 2)
     assert e.value.status == kv.KV_ERR_UNSUPPORTED
+    with pytest.raises(kv.KvError) as e:  # learned start without an attached net
+        kv.kv_project_force(s.h, *s.force, 1e-8, 0, 1)
+    assert e.value.status == kv.KV_ERR_STATE
     # the handle is still usable after these statuses
     st = s.project()
     assert st["status"] == kv.KV_OK and st["rel_res_true"] < 1e-8

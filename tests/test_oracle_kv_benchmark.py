@@ -103,3 +103,15 @@ def test_shear_speed_recovered_within_0p1_percent():
     _, c_d = orc.kv_discrete(w, MU, RHO, 0.0, dx, dt)
     assert c_m == pytest.approx(c_d, rel=2e-4)
     assert c_m == pytest.approx(c0, rel=1e-3)
+
+
+def test_xcorr_group_speed_recovers_a_known_speed():
+    """Shifted copies of a pulse travelling at a known speed give that speed
+    back (sub-sample lags through the parabolic refinement)."""
+    dt = 2e-5
+    t = np.arange(800) * dt
+    c = 2.37
+    offs = np.linspace(4e-3, 14e-3, 21)
+    tr = np.stack([np.exp(-((t - 2e-3 - o / c) / 6e-4) ** 2) * np.sin(2 * np.pi * 400 * (t - o / c))
+                   for o in offs], axis=1)
+    assert orc.xcorr_group_speed(tr, offs, dt) == pytest.approx(c, rel=2e-3)
