@@ -53,7 +53,7 @@ def lib():
         L.or_cg.restype = i
         L.or_project.argtypes = [i, i, i, d, dp, d, i, dp, dp, dp]
         L.or_project.restype = i
-        L.or_run.argtypes = [i, i, i, d, d, dp, dp, dp, dp, dp, i, dp, dp, dp, i, ip, i, dp, dp, dp]
+        L.or_run.argtypes = [i, i, i, d, d, dp, dp, dp, dp, dp, i, dp, dp, dp, i, ip, i, dp, dp, dp, i]
         L.or_run.restype = i
         L.or_kv1d_run.argtypes = [i, d, d, d, d, d, d, d, d, i, ip, i, dp]
         L.or_kv1d_run.restype = i
@@ -169,13 +169,16 @@ def _medium(x, shape):
 
 
 def run(nx, ny, nz, dx, dt, G, rho, eta, n_steps, sensors, fs=None, g=None, v0=None,
-        u_in=None, uprev_in=None, want_state=False):
+        u_in=None, uprev_in=None, want_state=False, divform=False):
     """Sec. 3.1 + 3.3: n_steps of the 3-level leapfrog recurrence.
 
     G, rho, eta: scalars or (nz, ny, nx) maps. fs: (fsx, fsy, fsz) projected force
     pattern or None. g: envelope table g(t_n). v0: initial velocity (3 arrays).
     sensors: (ns, 3) node indices (i, j, k). Returns traces [n_steps, ns, 3]
     (entry n = u^{n+1}) and, with want_state, (u^{n_steps}, u^{n_steps-1}).
+    divform: the divergence-form operator (1/rho) div(G grad u) + (1/rho)
+    div(eta grad udot) with face-averaged coefficients instead of Sec. 3.1's
+    pointwise (G/rho) L u + (eta/rho) L udot.
     """
     shape = (nz, ny, nx)
     mu_a, mup = _d(_medium(G, shape))
@@ -211,7 +214,7 @@ def run(nx, ny, nz, dx, dt, G, rho, eta, n_steps, sensors, fs=None, g=None, v0=N
     else:
         uop = upop = _null()
     rc = lib().or_run(nx, ny, nz, dx, dt, mup, rhop, etap, fsp, gp, n_g, v0p, uinp, uprp,
-                      int(n_steps), sp, ns, tp, uop, upop)
+                      int(n_steps), sp, ns, tp, uop, upop, int(bool(divform)))
     if rc != 0:
         raise MemoryError("oracle run failed to allocate")
     if want_state:

@@ -282,12 +282,36 @@ int or_project(int nx, int ny, int nz, double dx, const double *f /*3N*/, double
  * sensors: 3*ns node indices (i, j, k). traces: [n_steps][ns][3], entry n holds
  * u^{n+1} at each sensor. u_out / uprev_out (3N each, nullable) receive
  * u^{n_steps} and u^{n_steps-1}. u_in / uprev_in (3N each, nullable) override
- * the start state (u^0, u^{-1}) for restart tests.
+ * the start state (u^0, u^{-1}) for restart tests. divform != 0 replaces
+ * (mu/rho) L u and (eta/rho) L udot by (1/rho) K_mu u and (1/rho) K_eta udot.
  */
+/* Divergence-form operator (variant of Sec. 3.1 for heterogeneous media):
+ * (K_kappa q)_i = sum over the six faces of kappa_f (q_nb - q_i) / dx^2 with the
+ * face coefficient kappa_f = (kappa_i + kappa_nb) / 2; interior nodes only. */
+static void div_form(int nx, int ny, int nz, double dx, const double *kap, const double *q, double *out)
+{
+    const double inv = 1.0 / (dx * dx);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IDX(i, j, k);
+                if (!is_interior(i, j, k, nx, ny, nz)) {
+                    out[c] = 0.0;
+                    continue;
+                }
+                const size_t nb[6] = {IDX(i - 1, j, k), IDX(i + 1, j, k), IDX(i, j - 1, k),
+                                      IDX(i, j + 1, k), IDX(i, j, k - 1), IDX(i, j, k + 1)};
+                double s = 0.0;
+                for (int f = 0; f < 6; ++f) s += 0.5 * (kap[c] + kap[nb[f]]) * (q[nb[f]] - q[c]);
+                out[c] = s * inv;
+            }
+}
+
 int or_run(int nx, int ny, int nz, double dx, double dt, const double *mu, const double *rho,
            const double *eta, const double *fs, const double *g, int n_g, const double *v0,
            const double *u_in, const double *uprev_in, int n_steps, const int *sensors, int ns,
-           double *traces, double *u_out, double *uprev_out)
+           double *traces, double *u_out, double *uprev_out, int divform)
 {
     size_t N = (size_t)nx * ny * nz;
     double *um = (double *)calloc(3 * N, sizeof(double)); /* u^{n-1} */
@@ -316,8 +340,13 @@ int or_run(int nx, int ny, int nz, double dx, double dt, const double *mu, const
             const double *uc = u0 + comp * N;
             const double *ucm = um + comp * N;
             double *ucp = up + comp * N;
-            or_laplacian(nx, ny, nz, dx, uc, lu);
-            or_laplacian(nx, ny, nz, dx, w + comp * N, lw);
+            if (divform) {  /* lu = K_mu u, lw = K_eta udot (coefficients inside) */
+                div_form(nx, ny, nz, dx, mu, uc, lu);
+                div_form(nx, ny, nz, dx, eta, w + comp * N, lw);
+            } else {
+                or_laplacian(nx, ny, nz, dx, uc, lu);
+                or_laplacian(nx, ny, nz, dx, w + comp * N, lw);
+            }
 #pragma omp parallel for schedule(static)
             for (int k = 0; k < nz; ++k)
                 for (int j = 0; j < ny; ++j)
@@ -327,7 +356,8 @@ int or_run(int nx, int ny, int nz, double dx, double dt, const double *mu, const
                             ucp[c] = 0.0;
                             continue;
                         }
-                        double a = (mu[c] / rho[c]) * lu[c] + (eta[c] / rho[c]) * lw[c];
+                        double a = divform ? (lu[c] + lw[c]) / rho[c]
+                                           : (mu[c] / rho[c]) * lu[c] + (eta[c] / rho[c]) * lw[c];
                         if (fs) a += (gn / rho[c]) * fs[comp * N + c];
                         ucp[c] = 2.0 * uc[c] - ucm[c] + dt * dt * a;
                     }

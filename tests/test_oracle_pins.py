@@ -446,3 +446,54 @@ def test_force_linearity_and_separable_envelope():
     np.testing.assert_allclose(t2, 2 * t1, rtol=1e-12, atol=1e-30)
     np.testing.assert_allclose(t3, 2 * t1, rtol=1e-12, atol=1e-30)
     assert g.sum() == 5  # t_n < 5 dt for n = 0..4
+
+
+# ---------------------------------------------------------------------------
+# Divergence-form operator (heterogeneous variant of Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def test_divergence_form_reduces_to_pointwise_when_homogeneous():
+    n = (14, 12, 13)
+    rng = np.random.default_rng(9)
+    u0 = [rng.standard_normal(n[::-1]) * 1e-6 for _ in range(3)]
+    dt = 0.5 * orc.stable_dt(4e3, 1000.0, 0.6, DX)
+    sens = np.array([[5, 5, 5], [9, 3, 7]], np.int32)
+    a = orc.run(*n, DX, dt, 4e3, 1000.0, 0.6, 50, sens, u_in=u0, uprev_in=u0)
+    b = orc.run(*n, DX, dt, 4e3, 1000.0, 0.6, 50, sens, u_in=u0, uprev_in=u0, divform=True)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-12 * np.abs(a).max())
+
+
+def test_divergence_form_conserves_its_energy():
+    """eta = 0: rho (u^{n+1} - 2u^n + u^{n-1}) / dt^2 = K u^n with K symmetric,
+    so E = sum rho (u^{n+1} - u^n)^2 / dt^2 - <u^{n+1}, K u^n> is conserved
+    (K assembled here from face-averaged moduli with numpy slicing)."""
+    nx, ny, nz = 13, 12, 11
+    rng = np.random.default_rng(12)
+    mu = rng.uniform(1e3, 10e3, (nz, ny, nx))
+    rho = rng.uniform(1000, 1100, (nz, ny, nx))
+    dt = 0.4 * orc.stable_dt(mu, rho, 0.0, DX)
+    u0 = [rng.standard_normal((nz, ny, nx)) * 1e-6 for _ in range(3)]
+    um = [q * 0.98 for q in u0]
+
+    def K(q):
+        out = np.zeros_like(q)
+        c = (slice(1, -1),) * 3
+        for ax in range(3):
+            for sgn in (-1, 1):
+                sl = [slice(1, -1)] * 3
+                sl[ax] = slice(1 + sgn, q.shape[ax] - 1 + sgn)
+                sl = tuple(sl)
+                out[c] += 0.5 * (mu[c] + mu[sl]) * (q[sl] - q[c])
+        return out / DX ** 2
+
+    def E(un, uc):
+        m = interior_mask(nx, ny, nz)
+        return sum(np.sum(rho[m] * (un[c] - uc[c])[m] ** 2) / dt ** 2 - np.sum(un[c] * K(uc[c]))
+                   for c in range(3))
+
+    _, ua, uam = orc.run(nx, ny, nz, DX, dt, mu, rho, 0.0, 7, np.zeros((1, 3), np.int32),
+                         u_in=u0, uprev_in=um, want_state=True, divform=True)
+    _, ub, ubm = orc.run(nx, ny, nz, DX, dt, mu, rho, 0.0, 131, np.zeros((1, 3), np.int32),
+                         u_in=u0, uprev_in=um, want_state=True, divform=True)
+    ea, eb = E(ua, uam), E(ub, ubm)
+    assert ea > 0 and abs(eb - ea) < 1e-10 * abs(ea)
