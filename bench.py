@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 N_TIME_STEPS = 2000
 GRID = 256
 STEP_BYTES_PER_CELL = 56  # (u, d) read + write 48 B, coefficients A', B' 8 B
+DIV_STEP_BYTES_PER_CELL = 60  # divergence form: coefficients m, e, 1/rho 12 B
 FORCE_BYTES_PER_CELL = 12  # projected force on force steps
 
 
@@ -58,6 +59,9 @@ def parse():
                     help="inclusions256: 256^3 inclusions, 2000 steps (the headline); bone512: "
                          "512x512x384 bone shell, 5000 steps; sweep: 26 homogeneous cases on "
                          "uneven grids, 1000 batched steps")
+    ap.add_argument("--operator", default="pointwise", choices=["pointwise", "divergence"],
+                    help="spatial operator of the heterogeneous step: pointwise (G/rho) L u "
+                         "(Sec. 3.1) or the flux form (1/rho) div(G grad u)")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
     ap.add_argument("--step-config", default=None,
@@ -131,7 +135,7 @@ def workload(grid, n_steps, kind="inclusions256"):
     return inputs.heterogeneous_inclusions(n=grid, n_steps=n_steps)
 
 
-def cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=6, n_sample_iters=6):
+def cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=6, n_sample_iters=6, divform=False):
     """Time the FP64 oracle on a bounded sample of the pass: n_sample_iters CG
     iterations and n_sample_steps time steps of the same workload; the whole
     pass is extrapolated with the GPU's CG iteration count."""
@@ -141,14 +145,14 @@ def cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=6, n_sample_iters=6):
     t_cg = (time.perf_counter() - t0) / max(1, st["iters"])
     t0 = time.perf_counter()
     orc.run(w.nx, w.ny, w.nz, w.dx, dt, w.G, w.rho, w.eta, n_sample_steps, w.sensors, fs=fs,
-            g=np.ones(n_sample_steps, np.float32))
+            g=np.ones(n_sample_steps, np.float32), divform=divform)
     t_step = (time.perf_counter() - t0) / n_sample_steps
     total = cg_iters * t_cg + w.n_steps * t_step
     value = w.n_cells * w.n_steps / total / 1e9
     return value, {"cores": orc.get_threads(), "t_cg_iter_s": t_cg, "t_step_s": t_step,
                    "sample": (f"{n_sample_iters} CG iterations + {n_sample_steps} time steps of the "
-                              f"{w.nx}^3 workload, extrapolated to {cg_iters} CG iterations + "
-                              f"{w.n_steps} steps")}
+                              f"{w.nx}x{w.ny}x{w.nz} workload, extrapolated to {cg_iters} CG "
+                              f"iterations + {w.n_steps} steps")}
 
 
 def run_reference(args, rank, world):
@@ -156,22 +160,36 @@ def run_reference(args, rank, world):
         return
     from paper_2607_28414_b300 import inputs
     import oracle as orc
-    w = workload(args.grid, args.time_steps, args.workload)
+    if args.workload == "sweep":
+        # the oracle on the sweep's first case (128 x 128 x 192), whose rate per
+        # cell-update stands for the sweep's
+        n_steps = args.time_steps if args.time_steps != N_TIME_STEPS else 1000
+        w = inputs.sweep_cases(n_steps=n_steps)[0]
+    else:
+        w = workload(args.grid, args.time_steps, args.workload)
     dt = 0.5 * orc.stable_dt(w.G, w.rho, w.eta, w.dx)
     cg_iters = 400
     vals = []
     for it in range(args.warmup + args.steps):
-        v, info = cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=2, n_sample_iters=2)
+        v, info = cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=2, n_sample_iters=2,
+                                    divform=args.operator == "divergence")
         if it >= args.warmup:
             vals.append(v)
     value = float(np.mean(vals))
     ms = w.n_cells * w.n_steps / (value * 1e9) * 1e3
-    line = {"metric": f"KV-FDTD Gcell-updates/s (projection + {w.n_steps} steps)", "value": value,
+    if args.workload == "sweep":
+        metric = f"KV-FDTD Gcell-updates/s (26-case sweep, projections + {w.n_steps} steps)"
+        config = {"workload": "sweep_26_cases", "time_steps": w.n_steps,
+                  "sampled_case": [w.nx, w.ny, w.nz]}
+    else:
+        metric = f"KV-FDTD Gcell-updates/s (projection + {w.n_steps} steps)"
+        config = {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "time_steps": w.n_steps,
+                  "cg_tol": w.tol, "operator": args.operator}
+    line = {"metric": metric, "value": value,
             "unit": "Gcell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "grid": [w.nx, w.ny, w.nz], "time_steps": w.n_steps,
-                       "cg_tol": w.tol},
+            "config": config,
             "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": info["cores"],
                              "kind": "oracle", "sample": info["sample"] + " (CG iteration count "
                              "fixed at 400 for the extrapolation)"},
@@ -306,8 +324,15 @@ def main():
     torch.cuda.set_stream(stream)
     medium_d = [torch.from_numpy(a).to(device) for a in (w.G, w.rho, w.eta)]
     force_d = [torch.from_numpy(a).to(device) for a in w.force]
-    dt = 0.5 * kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *medium_d)
+    div = args.operator == "divergence"
+    lim = kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *medium_d)
+    if div:
+        lim = min(lim, kv.kv_stable_dt_op(w.nx, w.ny, w.nz, w.dx, *medium_d, kv.KV_OP_DIVERGENCE))
+    dt = 0.5 * lim
     h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, *medium_d, stream=stream.cuda_stream)
+    if div:
+        kv.kv_set_operator(h, kv.KV_OP_DIVERGENCE, *medium_d)
+    bytes_per_cell = DIV_STEP_BYTES_PER_CELL if div else STEP_BYTES_PER_CELL
     if args.step_config:
         vals = [int(v) for v in args.step_config.split(",")]
         variant, (tx, ty, zc, ns) = (vals[0], vals[1:]) if len(vals) == 5 else (0, vals)
@@ -370,13 +395,13 @@ def main():
     value = world * N * w.n_steps * args.steps / t_max / 1e9
     step_gcells = N * w.n_steps * args.steps / t_steps / 1e9
     launch_s = t_steps / (w.n_steps * args.steps)
-    alg_bytes = (N * STEP_BYTES_PER_CELL * w.n_steps + N * FORCE_BYTES_PER_CELL * n_force_steps) \
+    alg_bytes = (N * bytes_per_cell * w.n_steps + N * FORCE_BYTES_PER_CELL * n_force_steps) \
         / w.n_steps
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_kind = peaks()
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "kv_step_traffic.json")
-    if os.path.exists(tfile):
+    if os.path.exists(tfile) and not div:
         try:
             tj = json.load(open(tfile))
             if tj.get("grid") == [w.nx, w.ny, w.nz]:
@@ -414,7 +439,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, info = cpu_oracle_sample(w, dt, int(np.median(cg_iters)))
+        v, info = cpu_oracle_sample(w, dt, int(np.median(cg_iters)), divform=div)
         cpu = {"value": v, "unit": "Gcell-updates/s", "cores": info["cores"], "kind": "oracle",
                "sample": info["sample"]}
 
@@ -431,6 +456,7 @@ def main():
                        "medium": ("8 seeded spherical inclusions (seed 102), speckled beam"
                                   if args.workload == "inclusions256" else
                                   "bone shell over smooth soft tissue (seed 105), speckled beam"),
+                       "operator": args.operator,
                        "reductions": "f64", "parallelism": f"replicas{world}",
                        "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2 (inputs larger than L2)"},
             "kv_step_gcells": step_gcells,
@@ -439,7 +465,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_step_tma", "peak_kind": peak_kind,
-                         "bytes_model": f"{STEP_BYTES_PER_CELL} B/cell + {FORCE_BYTES_PER_CELL} "
+                         "bytes_model": f"{bytes_per_cell} B/cell + {FORCE_BYTES_PER_CELL} "
                                         "B/cell on force steps"},
             "gpu_launches": int(launches),
             "clocks": clk,

@@ -62,6 +62,15 @@ typedef enum { KV_FP32 = 0, KV_FP64 = 1 } kv_precision;
 
 typedef enum { KV_SCALAR = 0, KV_HOST = 1, KV_DEVICE = 2 } kv_where;
 
+/* Spatial operator of the shear-wave equation in a heterogeneous medium.
+ * KV_OP_POINTWISE   (G/rho) L u + (eta/rho) L udot with the 7-point Laplacian L
+ *                   (Sec. 3.1, Eq. of the reduced Kelvin-Voigt model).
+ * KV_OP_DIVERGENCE  (1/rho) div(G grad u) + (1/rho) div(eta grad udot): the
+ *                   flux form for spatially varying moduli, each of the six
+ *                   face fluxes using the mean of the two nodes' moduli.
+ * The two coincide in a homogeneous medium. */
+typedef enum { KV_OP_POINTWISE = 0, KV_OP_DIVERGENCE = 1 } kv_operator;
+
 /* A scalar or a dense nx*ny*nz float field on the host or the device. */
 typedef struct {
     const float *data; /* dense field (KV_HOST / KV_DEVICE), else ignored */
@@ -93,6 +102,15 @@ typedef struct kv_handle kv_handle;
 kv_status kv_stable_dt(int nx, int ny, int nz, double dx, kv_field G, kv_field rho,
                        kv_field eta, double *dt_max);
 
+/* Stability limit for an operator (kv_operator). KV_OP_POINTWISE is
+ * kv_stable_dt. KV_OP_DIVERGENCE bounds the spectrum of the flux operator by
+ * Gershgorin's theorem: at every interior node the pointwise formula is
+ * evaluated with G and eta replaced by the mean of the six face values
+ * (6 G_i + sum of the six neighbours' G) / 12, and rho by the node's own rho.
+ * Boundary nodes are only checked for valid values. Synchronising. */
+kv_status kv_stable_dt_op(int nx, int ny, int nz, double dx, kv_field G, kv_field rho,
+                          kv_field eta, int op, double *dt_max);
+
 /*
  * Create a solver for one grid (Sec. 3.1, 3.5). G (shear modulus mu, Pa),
  * rho (kg/m^3), eta (Pa s) are scalars or dense fields; all three scalar gives
@@ -108,6 +126,15 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
  * A = dt^2 G/rho, B = dt eta/rho, S = dt^2/rho). The homogeneous/heterogeneous
  * choice must match kv_create's. Synchronising (it checks dt). */
 kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta);
+
+/* Select the spatial operator (kv_operator) and fold the medium for it. The
+ * handle's dt must not exceed kv_stable_dt_op for that operator (else
+ * KV_ERR_UNSTABLE_DT and nothing changes). The divergence form stores three
+ * coefficient fields (dt^2 G/dx^2, dt eta/dx^2, 1/rho) instead of two; the
+ * two-step kernel (kv_set_step_config variant 2) supports only the pointwise
+ * operator (KV_ERR_UNSUPPORTED). The state and traces are kept. A kv_create
+ * handle starts with KV_OP_POINTWISE. Synchronising. */
+kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_field eta);
 
 /* Temporal envelope g(t_n), n = 0..n-1 (Sec. 3.3, Eq. separable_force); g = 0
  * beyond the table. g: float table on the host or device (where). */
@@ -268,7 +295,9 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
 kv_status kv_sync(kv_handle *h);
 
 /* Kernel selection and launch shape of the FP32 step (autotuning and tests).
- * variant 0: TMA-staged z-march kernel (default); 1: plain per-node kernel.
+ * variant 0: TMA-staged z-march kernel (default); 1: plain per-node kernel;
+ * 2: two steps per z sweep (temporal blocking, pointwise operator only;
+ * tiles 32x4, 32x8, 64x4, 64x8, 128x4 with ns in {4, 6}).
  * tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in [64, 512];
  * zc >= 1 planes per block; ns in {4, 6, 8} shared-memory stages (ns - 3
  * planes in flight per block). Values <= 0 keep the current choice. A shape
@@ -292,8 +321,9 @@ kv_status kv_destroy(kv_handle *h);
 
 /*
  * Batched time stepping (parameter sweeps, Sec. 3.1 applied to many media at
- * once). A batch refers to n existing FP32 handles -- all homogeneous or all
- * heterogeneous, all created on the same stream -- of any grid sizes. Each
+ * once). A batch refers to n existing FP32 handles -- all homogeneous, all
+ * heterogeneous with the pointwise operator or all with the divergence-form
+ * operator, all created on the same stream -- of any grid sizes. Each
  * kv_batch_step(b, n) advances every case by n steps with one kernel launch
  * per step covering the tile grids of all cases (blocks of 32 steps replay
  * from a CUDA graph); each case keeps its own state, coefficients, envelope,

@@ -313,18 +313,40 @@ def kv_weak_loss_alpha(omega, mu, rho, eta):
     return eta * omega ** 2 / (2.0 * rho * c ** 3)
 
 
-def kv_discrete(omega, mu, rho, eta, dx, dt):
+def kv_discrete(omega, mu, rho, eta, dx, dt, lam_t=0.0):
     """Exact dispersion of the 1D recurrence (derived from Sec. 3.1).
 
     With u_i^n = z^n exp(-i k x_i), z = exp(i omega dt), the update gives
     lam = (4/dx^2) sin^2(k dx/2) = -(z-1)^2 / ((a+b) z - b), a = dt^2 mu/rho,
-    b = dt eta/rho. Solve for complex k; returns (alpha, phase speed)."""
+    b = dt eta/rho. Solve for complex k; returns (alpha, phase speed).
+
+    lam_t: eigenvalue of -L over the two transverse directions of a guided
+    mode u = U(x) s(y) s(z) on a 3D grid (the 3D recurrence acts on U as the
+    1D one with lam replaced by lam + lam_t); 0 for a plane wave."""
     a = dt * dt * mu / rho
     b = dt * eta / rho
     z = np.exp(1j * omega * dt)
-    lam = -(z - 1.0) ** 2 / ((a + b) * z - b)
+    lam = -(z - 1.0) ** 2 / ((a + b) * z - b) - lam_t
     s = np.sqrt(lam * dx * dx / 4.0)
     k = 2.0 / dx * np.arcsin(s)
+    return float(abs(k.imag)), float(omega / abs(k.real))
+
+
+def dirichlet_mode_eigenvalue(n, dx):
+    """Eigenvalue of -d^2/dx^2 (3-point) for the first Dirichlet sine mode
+    s_j = sin(pi j / (n - 1)), j = 0..n-1, of a line of n nodes with both end
+    nodes fixed: (4/dx^2) sin^2(pi / (2 (n - 1)))."""
+    return 4.0 / dx ** 2 * np.sin(np.pi / (2.0 * (n - 1))) ** 2
+
+
+def kv_plane_from_guided(alpha, c, omega, dx, lam_t):
+    """Plane-wave (alpha, phase speed) equivalent to a guided mode measured
+    with (alpha, c): the guided wavenumber k_x has (4/dx^2) sin^2(k_x dx/2) =
+    lam - lam_t, so the plane-wave k has (4/dx^2) sin^2(k dx/2) =
+    (4/dx^2) sin^2(k_x dx/2) + lam_t."""
+    kx = omega / c - 1j * alpha
+    lam = 4.0 / dx ** 2 * np.sin(kx * dx / 2.0) ** 2 + lam_t
+    k = 2.0 / dx * np.arcsin(np.sqrt(lam * dx * dx / 4.0))
     return float(abs(k.imag)), float(omega / abs(k.real))
 
 

@@ -69,7 +69,7 @@ double dt_limit_node(double g, double r, double e, double dx) {
 }
 
 kv_status stable_dt_impl(kv_handle *h, int nx, int ny, int nz, double dx, const kv_field &G,
-                         const kv_field &rho, const kv_field &eta, double *out) {
+                         const kv_field &rho, const kv_field &eta, int op, double *out) {
     const kv_field *fs[3] = {&G, &rho, &eta};
     int n_host = 0, n_dev = 0;
     for (auto *f : fs) {
@@ -82,18 +82,34 @@ kv_status stable_dt_impl(kv_handle *h, int nx, int ny, int nz, double dx, const 
     const long long n = (long long)nx * ny * nz;
     double m;
     if (n_dev) {
-        kv_status st = stable_dt_device(h ? h->stream : 0, h ? h->dtmin : nullptr, (int)n, dx,
+        kv_status st = stable_dt_device(h ? h->stream : 0, h ? h->dtmin : nullptr, nx, ny, nz, dx,
                                         G.where == KV_DEVICE ? G.data : nullptr, G.value,
                                         rho.where == KV_DEVICE ? rho.data : nullptr, rho.value,
-                                        eta.where == KV_DEVICE ? eta.data : nullptr, eta.value, &m);
+                                        eta.where == KV_DEVICE ? eta.data : nullptr, eta.value, op, &m);
         if (st != KV_OK) return set_error(h, st, "device stability reduction failed");
     } else if (n_host) {
         m = INFINITY;
+        auto val = [](const kv_field &f, long long c) { return f.where == KV_HOST ? (double)f.data[c] : f.value; };
+        const long long sy = nx, sz = (long long)nx * ny;
         for (long long c = 0; c < n; ++c) {
-            const double g = G.where == KV_HOST ? G.data[c] : G.value;
-            const double r = rho.where == KV_HOST ? rho.data[c] : rho.value;
-            const double e = eta.where == KV_HOST ? eta.data[c] : eta.value;
-            m = fmin(m, dt_limit_node(g, r, e, dx));
+            double g = val(G, c), e = val(eta, c);
+            const double r = val(rho, c);
+            double v = dt_limit_node(g, r, e, dx);
+            if (v >= 0.0 && op == KV_OP_DIVERGENCE) {
+                const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / sz);
+                if (i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2) {
+                    const long long nb[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+                    double gs = 6.0 * g, es = 6.0 * e;
+                    for (long long q : nb) {
+                        gs += val(G, q);
+                        es += val(eta, q);
+                    }
+                    v = dt_limit_node(gs / 12.0, r, es / 12.0, dx);
+                } else {
+                    v = INFINITY;  // boundary node: values checked, never updated
+                }
+            }
+            m = fmin(m, v);
         }
     } else {
         m = dt_limit_node(G.value, rho.value, eta.value, dx);
@@ -124,7 +140,29 @@ kv_status poll_flags(kv_handle *h) {
     return KV_OK;
 }
 
+template <typename P>
+kv_status dalloc(kv_handle *h, P **p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_check(h, e, "cudaMalloc");
+    }
+    return KV_OK;
+}
+
 kv_status fold(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_field &eta) {
+    if (h->het && step_kind(h) == kKindDiv && h->coef_fields < 3) {  // third field: 1/rho
+        kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "coefficient reallocation");
+        if (st != KV_OK) return st;
+        cudaFree(h->coef);
+        h->coef = nullptr;
+        h->coef_fields = 0;
+        if ((st = dalloc(h, &h->coef, 3 * (size_t)h->Np * h->esize)) != KV_OK) {
+            h->sticky = 1;  // no coefficient storage left: the handle cannot step
+            return st;
+        }
+        h->coef_fields = 3;
+    }
     if (!h->het) {
         h->A_s = h->dt * h->dt * G.value / rho.value / (h->dx * h->dx);
         h->B_s = h->dt * eta.value / rho.value / (h->dx * h->dx);
@@ -144,16 +182,6 @@ kv_status fold(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_fi
     kv_status st = launch_fold(h, ptr[0], G.value, ptr[1], rho.value, ptr[2], eta.value);
     if (st != KV_OK) return st;
     return cuda_check(h, cudaStreamSynchronize(h->stream), "medium fold");
-}
-
-template <typename P>
-kv_status dalloc(kv_handle *h, P **p, size_t bytes) {
-    cudaError_t e = cudaMalloc((void **)p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return cuda_check(h, e, "cudaMalloc");
-    }
-    return KV_OK;
 }
 
 }  // namespace
@@ -183,7 +211,15 @@ kv_status kv_stable_dt(int nx, int ny, int nz, double dx, kv_field G, kv_field r
                        double *dt_max) {
     if (nx < 3 || ny < 3 || nz < 3 || !(dx > 0.0) || !dt_max)
         return set_error(nullptr, KV_ERR_ARG, "kv_stable_dt: invalid grid, dx or output pointer");
-    return stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, dt_max);
+    return stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, KV_OP_POINTWISE, dt_max);
+}
+
+kv_status kv_stable_dt_op(int nx, int ny, int nz, double dx, kv_field G, kv_field rho, kv_field eta,
+                          int op, double *dt_max) {
+    if (nx < 3 || ny < 3 || nz < 3 || !(dx > 0.0) || !dt_max ||
+        (op != KV_OP_POINTWISE && op != KV_OP_DIVERGENCE))
+        return set_error(nullptr, KV_ERR_ARG, "kv_stable_dt_op: invalid grid, dx, operator or output pointer");
+    return stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, op, dt_max);
 }
 
 kv_status kv_destroy(kv_handle *h) {
@@ -214,7 +250,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     if (px * ny * (long long)nz > (1ll << 31) - 1)
         return set_error(nullptr, KV_ERR_ARG, "kv_create: grid too large (more than 2^31 padded nodes)");
     double dt_max;
-    kv_status st = stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, &dt_max);
+    kv_status st = stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, KV_OP_POINTWISE, &dt_max);
     if (st != KV_OK) return st;
     if (dt > dt_max * (1.0 + 1e-12))
         return set_error(nullptr, KV_ERR_UNSTABLE_DT,
@@ -233,6 +269,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     h->precision = precision;
     h->esize = precision == KV_FP64 ? 8 : 4;
     h->het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
+    h->op = KV_OP_POINTWISE;
     h->variant = 0;
     h->tx = 64;
     h->ty = 8;
@@ -262,6 +299,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
             goto fail;
         if (h->het && ((st = dalloc(h, &h->coef, 2 * Np * es)) || (st = dalloc(h, &h->S, Np * es))))
             goto fail;
+        h->coef_fields = h->het ? 2 : 0;
         h->p[0] = h->cgv;
         h->r = (char *)h->cgv + Np * es;
         h->p[1] = (char *)h->cgv + 2 * Np * es;
@@ -299,13 +337,38 @@ kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta) {
     double dt_max;
     kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_medium");
     if (st != KV_OK) return st;
-    if ((st = stable_dt_impl(h, h->nx, h->ny, h->nz, h->dx, G, rho, eta, &dt_max)) != KV_OK) return st;
+    if ((st = stable_dt_impl(h, h->nx, h->ny, h->nz, h->dx, G, rho, eta, h->op, &dt_max)) != KV_OK) return st;
     if (h->dt > dt_max * (1.0 + 1e-12))
         return set_error(h, KV_ERR_UNSTABLE_DT, "dt = %.6e s exceeds the stability limit %.6e s", h->dt,
                          dt_max);
     h->dt_max = dt_max;
     free_graphs(h);
     return fold(h, G, rho, eta);
+}
+
+kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_field eta) {
+    if (!h) return KV_ERR_ARG;
+    if (op != KV_OP_POINTWISE && op != KV_OP_DIVERGENCE)
+        return set_error(h, KV_ERR_ARG, "kv_set_operator: unknown operator %d", op);
+    if (h->sticky) return KV_ERR_STATE;
+    const int het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
+    if (het != h->het)
+        return set_error(h, KV_ERR_ARG, "kv_set_operator: homogeneous/heterogeneous kind differs from kv_create");
+    if (op == KV_OP_DIVERGENCE && h->het && h->precision == KV_FP32 && h->variant == 2)
+        return set_error(h, KV_ERR_UNSUPPORTED, "kv_set_operator: the two-step kernel supports only the pointwise operator");
+    double dt_max;
+    kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_operator");
+    if (st != KV_OK) return st;
+    if ((st = stable_dt_impl(h, h->nx, h->ny, h->nz, h->dx, G, rho, eta, op, &dt_max)) != KV_OK) return st;
+    if (h->dt > dt_max * (1.0 + 1e-12))
+        return set_error(h, KV_ERR_UNSTABLE_DT, "dt = %.6e s exceeds the stability limit %.6e s of operator %d",
+                         h->dt, dt_max, op);
+    h->op = op;
+    h->dt_max = dt_max;
+    h->tma_ready = 0;
+    free_graphs(h);
+    if ((st = fold(h, G, rho, eta)) != KV_OK) h->sticky = 1;  // coefficients of neither operator
+    return st;
 }
 
 kv_status kv_set_envelope(kv_handle *h, const float *g, int n, int where) {

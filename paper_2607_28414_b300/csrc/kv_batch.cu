@@ -2,8 +2,9 @@
 // step (parameter sweeps over uneven grids), and force sharing between handles
 // on the same grid.
 //
-// A batch refers to existing FP32 handles (all homogeneous or all
-// heterogeneous, all on one stream, all at the same ping-pong parity). Each
+// A batch refers to existing FP32 handles (all of one step kind: homogeneous,
+// pointwise or divergence-form heterogeneous; all on one stream, all at the
+// same ping-pong parity). Each
 // step is one launch of k_step_batch over the concatenated tile grids of all
 // cases; every case keeps its own state, coefficients, envelope, sensors,
 // traces and step counter. Blocks of steps replay from a CUDA graph. The case
@@ -62,7 +63,10 @@ kv_status refresh(kv_batch *b) {
     void *kernel;
     size_t smem;
     int nt;
-    if (kv::batch_kernel_for(b->tx, b->ty, b->ns, b->h[0]->het != 0, &kernel, &smem, &nt) != KV_OK)
+    for (int c = 1; c < n; ++c)
+        if (kv::step_kind(b->h[c]) != kv::step_kind(b->h[0]))
+            return berr(b, KV_ERR_ARG, "kv_batch: cases must all use the same medium kind and operator");
+    if (kv::batch_kernel_for(b->tx, b->ty, b->ns, kv::step_kind(b->h[0]), &kernel, &smem, &nt) != KV_OK)
         return berr(b, KV_ERR_ARG, "kv_batch: no batched kernel for this tile / stage count");
     const bool changed = b->table_host.size() != t.size() || b->kernel != kernel ||
                          memcmp(b->table_host.data(), t.data(), sizeof(kv::BatchCase) * n) != 0;
@@ -123,9 +127,10 @@ kv_status kv_batch_create(kv_batch **out, int n, kv_handle *const *cases) {
         kv_handle *h = cases[c];
         if (!h || h->precision != KV_FP32)
             return kv::set_error(nullptr, KV_ERR_ARG, "kv_batch_create: cases must be FP32 handles");
-        if (h->het != cases[0]->het)
+        if (kv::step_kind(h) != kv::step_kind(cases[0]))
             return kv::set_error(nullptr, KV_ERR_ARG,
-                                 "kv_batch_create: cases must be all homogeneous or all heterogeneous");
+                                 "kv_batch_create: cases must all be homogeneous, all pointwise or all "
+                                 "divergence-form heterogeneous");
         if (h->stream != cases[0]->stream)
             return kv::set_error(nullptr, KV_ERR_ARG, "kv_batch_create: cases must share one stream");
     }
@@ -153,7 +158,7 @@ kv_status kv_batch_set_config(kv_batch *b, int tx, int ty, int zc, int ns) {
     void *kernel;
     size_t smem;
     int nt;
-    if (zc < 1 || kv::batch_kernel_for(tx, ty, ns, b->h[0]->het != 0, &kernel, &smem, &nt) != KV_OK)
+    if (zc < 1 || kv::batch_kernel_for(tx, ty, ns, kv::step_kind(b->h[0]), &kernel, &smem, &nt) != KV_OK)
         return berr(b, KV_ERR_ARG, "kv_batch_set_config: unsupported tile, stage count or z chunk");
     b->tx = tx;
     b->ty = ty;

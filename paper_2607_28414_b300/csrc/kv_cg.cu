@@ -643,22 +643,43 @@ k_grad(const float *__restrict__ f, const double *__restrict__ phi, const T *__r
 }
 
 // Per-node stability limit dt <= h^2 / (nu + sqrt(nu^2 + c^2 h^2)), h^2 = dx^2/3
-// (the positive root of dt^2 c^2 + 2 dt nu = h^2), block minima.
-__global__ void k_dtmin(int n, double dx, const float *G, double Gs, const float *rho, double rhos,
-                        const float *eta, double etas, double *out) {
+// (the positive root of dt^2 c^2 + 2 dt nu = h^2), block minima. Dense
+// nx*ny*nz fields. op = KV_OP_DIVERGENCE: at interior nodes c^2 and nu use the
+// mean face modulus (6 G_i + sum of the neighbours' G) / 12 (Gershgorin bound
+// of the flux operator); boundary nodes are only validated.
+__global__ void k_dtmin(int nx, int ny, int nz, double dx, const float *G, double Gs,
+                        const float *rho, double rhos, const float *eta, double etas, int op,
+                        double *out) {
     __shared__ double sh[256];
     double m = INFINITY;
     const double h2 = dx * dx / 3.0;
+    const long long n = (long long)nx * ny * nz;
+    const long long sy = nx, sz = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
          c += (long long)gridDim.x * blockDim.x) {
-        const double g = G ? (double)G[c] : Gs;
+        double g = G ? (double)G[c] : Gs;
         const double r = rho ? (double)rho[c] : rhos;
-        const double e = eta ? (double)eta[c] : etas;
+        double e = eta ? (double)eta[c] : etas;
+        const bool bad = !(r > 0.0) || g < 0.0 || e < 0.0 || !isfinite(g) || !isfinite(r) || !isfinite(e);
+        bool use = true;
+        if (op == KV_OP_DIVERGENCE) {
+            const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / sz);
+            use = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+            if (use) {
+                const long long nb[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+                double gs = 6.0 * g, es = 6.0 * e;
+                for (int f = 0; f < 6; ++f) {
+                    gs += G ? (double)G[nb[f]] : Gs;
+                    es += eta ? (double)eta[nb[f]] : etas;
+                }
+                g = gs / 12.0;
+                e = es / 12.0;
+            }
+        }
         const double c2 = g / r, nu = e / r;
         const double den = nu + sqrt(nu * nu + c2 * h2);
-        double v = den > 0.0 ? h2 / den : INFINITY;
-        if (!(r > 0.0) || g < 0.0 || e < 0.0 || !isfinite(g) || !isfinite(r) || !isfinite(e))
-            v = -1.0;  // invalid medium
+        double v = (use && den > 0.0) ? h2 / den : INFINITY;
+        if (bad) v = -1.0;  // invalid medium
         m = fmin(m, v);
     }
     sh[threadIdx.x] = m;
@@ -670,12 +691,12 @@ __global__ void k_dtmin(int n, double dx, const float *G, double Gs, const float
     if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
-kv_status stable_dt_device(cudaStream_t stream, double *scratch, int n, double dx, const float *G,
-                           double Gs, const float *rho, double rhos, const float *eta, double etas,
-                           double *out) {
+kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny, int nz, double dx,
+                           const float *G, double Gs, const float *rho, double rhos, const float *eta,
+                           double etas, int op, double *out) {
     double *d = scratch;
     if (!d && cudaMalloc(&d, kDtBlocks * sizeof(double)) != cudaSuccess) return KV_ERR_OOM;
-    k_dtmin<<<kDtBlocks, 256, 0, stream>>>(n, dx, G, Gs, rho, rhos, eta, etas, d);
+    k_dtmin<<<kDtBlocks, 256, 0, stream>>>(nx, ny, nz, dx, G, Gs, rho, rhos, eta, etas, op, d);
     double hbuf[kDtBlocks];
     cudaError_t e = cudaMemcpyAsync(hbuf, d, sizeof(hbuf), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);

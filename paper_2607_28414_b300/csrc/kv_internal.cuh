@@ -115,8 +115,10 @@ struct kv_handle {
 
     // medium
     int het;
+    int op;                // kv_operator: KV_OP_POINTWISE or KV_OP_DIVERGENCE
     double A_s, B_s, S_s;  // homogeneous scalars (A, B already divided by dx^2)
-    void *coef;            // [2][Np] (A', B') when het
+    void *coef;            // het: [2][Np] (A', B') pointwise, [3][Np] (m, e, 1/rho) divergence form
+    int coef_fields;       // fields allocated in coef
     void *S;               // [Np] dt^2/rho when het
     double dt_max;
 
@@ -191,8 +193,15 @@ kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attribu
 kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
 kv_status step2_launch(kv_handle *h, int from_buffer); // two steps (variant 2), one buffer swap
 
+// Step kernel kinds: homogeneous, pointwise heterogeneous (Sec. 3.1),
+// divergence-form heterogeneous.
+enum { kKindHomo = 0, kKindPoint = 1, kKindDiv = 2 };
+inline int step_kind(const kv_handle *h) {
+    return !h->het ? kKindHomo : (h->op == KV_OP_DIVERGENCE ? kKindDiv : kKindPoint);
+}
+
 // Batched step (kv_step.cu)
-kv_status batch_kernel_for(int tx, int ty, int ns, bool het, void **kernel, size_t *smem, int *nt);
+kv_status batch_kernel_for(int tx, int ty, int ns, int kind, void **kernel, size_t *smem, int *nt);
 kv_status batch_fill_case(kv_handle *h, struct BatchCase *bc, int tx, int ty, int zc, int begin,
                           int *blocks);
 kv_status batch_launch(void *kernel, const struct BatchCase *table, int ncases, int total_blocks,
@@ -208,9 +217,9 @@ kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_ou
 // Device stability limit over dense fields: kDtBlocks block minima in
 // `scratch` (kDtBlocks doubles; NULL = a temporary allocation), synchronising.
 constexpr int kDtBlocks = 592;
-kv_status stable_dt_device(cudaStream_t stream, double *scratch, int n, double dx, const float *G,
-                           double Gs, const float *rho, double rhos, const float *eta, double etas,
-                           double *out);
+kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny, int nz, double dx,
+                           const float *G, double Gs, const float *rho, double rhos, const float *eta,
+                           double etas, int op, double *out);
 
 inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
 
@@ -234,6 +243,20 @@ __device__ __forceinline__ float kv_add<float>(float a, float b) { return __fadd
 template <>
 __device__ __forceinline__ double kv_add<double>(double a, double b) { return __dadd_rn(a, b); }
 
+template <typename T>
+__device__ __forceinline__ T kv_sub(T a, T b);
+template <>
+__device__ __forceinline__ float kv_sub<float>(float a, float b) { return __fsub_rn(a, b); }
+template <>
+__device__ __forceinline__ double kv_sub<double>(double a, double b) { return __dsub_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T kv_mul(T a, T b);
+template <>
+__device__ __forceinline__ float kv_mul<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double kv_mul<double>(double a, double b) { return __dmul_rn(a, b); }
+
 // One node of the increment-form update. su / sd are the sums of the six
 // neighbours of u / d, formed by the caller as ((xm + xp) + (ym + yp)) + (zm + zp).
 //   L^u = su - 6u,  L^d = sd - 6d
@@ -248,6 +271,33 @@ __device__ __forceinline__ void kv_update(T u, T su, T d, T sd, T A, T B, T g, T
     T dn = kv_fma(g, F, d);
     dn = kv_fma(B, ld, dn);
     dn = kv_fma(A, lu, dn);
+    d_out = dn;
+    u_out = kv_add(u, dn);
+}
+
+// One node of the divergence-form update (heterogeneous operator
+// (1/rho) div(G grad u) + (1/rho) div(eta grad udot)). Neighbour order
+// xm, xp, ym, yp, zm, zp; face weights wm[f] = (m_c + m_f)/2 with m = dt^2 G/dx^2,
+// we[f] = (e_c + e_f)/2 with e = dt eta/dx^2; r = 1/rho at the node.
+//   s  = sum_f wm[f] (u_f - u) + sum_f we[f] (d_f - d)
+//   d' = d + r s + gF,  u' = u + d'
+// Explicit rounding steps in a fixed order, as in kv_update.
+template <typename T>
+__device__ __forceinline__ T face_weight(T c, T nb) {
+    return kv_mul(T(0.5), kv_add(c, nb));
+}
+
+template <typename T>
+__device__ __forceinline__ void kv_update_div(T u, const T (&nu)[6], T d, const T (&nd)[6],
+                                              const T (&wm)[6], const T (&we)[6], T r, T g, T F,
+                                              T &u_out, T &d_out) {
+    T s = kv_mul(wm[0], kv_sub(nu[0], u));
+#pragma unroll
+    for (int f = 1; f < 6; ++f) s = kv_fma(wm[f], kv_sub(nu[f], u), s);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) s = kv_fma(we[f], kv_sub(nd[f], d), s);
+    T dn = kv_fma(g, F, d);
+    dn = kv_fma(r, s, dn);
     d_out = dn;
     u_out = kv_add(u, dn);
 }

@@ -58,8 +58,9 @@ __device__ __forceinline__ void step_epilogue(const T *out, const StepParams &p,
 // ---------------------------------------------------------------------------
 // Plain per-node kernel (FP64 check mode; FP32 reference variant).
 // Grid: (ceil(nx/128), ny-2, nz-2), block 128; node (i, 1+blockIdx.y, 1+blockIdx.z).
+// K: kKindHomo / kKindPoint (coef = [A', B']) / kKindDiv (coef = [m, e, 1/rho]).
 // ---------------------------------------------------------------------------
-template <typename T, bool HET>
+template <typename T, int K>
 __global__ void __launch_bounds__(128)
 k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict__ coef,
              const T *__restrict__ F, StepParams p) {
@@ -72,21 +73,49 @@ k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict_
     if (i >= 1 && i <= p.nx - 2) {
         const long long sy = p.px, sz = (long long)p.px * p.ny;
         const long long c = k * sz + j * sy + i;
-        const T A = HET ? coef[c] : T(p.A);
-        const T B = HET ? coef[p.Np + c] : T(p.B);
+        const long long nb[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+        if constexpr (K == kKindDiv) {
+            const T *m = coef, *e = coef + p.Np;
+            T wm[6], we[6];
 #pragma unroll
-        for (int comp = 0; comp < 3; ++comp) {
-            const T *u = in + comp * p.Np;
-            const T *d = in + (3 + comp) * p.Np;
-            const T su = kv_add(kv_add(kv_add(u[c - 1], u[c + 1]), kv_add(u[c - sy], u[c + sy])),
-                                kv_add(u[c - sz], u[c + sz]));
-            const T sd = kv_add(kv_add(kv_add(d[c - 1], d[c + 1]), kv_add(d[c - sy], d[c + sy])),
-                                kv_add(d[c - sz], d[c + sz]));
-            const T Fv = force ? F[comp * p.Np + c] : T(0);
-            T uo, dn;
-            kv_update(u[c], su, d[c], sd, A, B, g, Fv, uo, dn);
-            out[comp * p.Np + c] = uo;
-            out[(3 + comp) * p.Np + c] = dn;
+            for (int f = 0; f < 6; ++f) {
+                wm[f] = face_weight(m[c], m[nb[f]]);
+                we[f] = face_weight(e[c], e[nb[f]]);
+            }
+            const T r = coef[2 * p.Np + c];
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                const T *u = in + comp * p.Np;
+                const T *d = in + (3 + comp) * p.Np;
+                T nu[6], nd[6];
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    nu[f] = u[nb[f]];
+                    nd[f] = d[nb[f]];
+                }
+                const T Fv = force ? F[comp * p.Np + c] : T(0);
+                T uo, dn;
+                kv_update_div(u[c], nu, d[c], nd, wm, we, r, g, Fv, uo, dn);
+                out[comp * p.Np + c] = uo;
+                out[(3 + comp) * p.Np + c] = dn;
+            }
+        } else {
+            const T A = K == kKindPoint ? coef[c] : T(p.A);
+            const T B = K == kKindPoint ? coef[p.Np + c] : T(p.B);
+#pragma unroll
+            for (int comp = 0; comp < 3; ++comp) {
+                const T *u = in + comp * p.Np;
+                const T *d = in + (3 + comp) * p.Np;
+                const T su = kv_add(kv_add(kv_add(u[c - 1], u[c + 1]), kv_add(u[c - sy], u[c + sy])),
+                                    kv_add(u[c - sz], u[c + sz]));
+                const T sd = kv_add(kv_add(kv_add(d[c - 1], d[c + 1]), kv_add(d[c - sy], d[c + sy])),
+                                    kv_add(d[c - sz], d[c + sz]));
+                const T Fv = force ? F[comp * p.Np + c] : T(0);
+                T uo, dn;
+                kv_update(u[c], su, d[c], sd, A, B, g, Fv, uo, dn);
+                out[comp * p.Np + c] = uo;
+                out[(3 + comp) * p.Np + c] = dn;
+            }
         }
     }
     step_epilogue<T>(out, p, step);
@@ -106,8 +135,12 @@ k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict_
 // consecutive x nodes (one float4) of one row; its x neighbours come from warp
 // shuffles (row edges from shared memory). Outputs go straight to global
 // memory as float4 stores.
+//
+// Divergence form (K = kKindDiv): the face weights need the moduli of the six
+// neighbours, so every staged plane also carries the three coefficient fields
+// (m, e, 1/rho) with the same halo, in a second box (TX+8, TY+2, 1, 3).
 // ---------------------------------------------------------------------------
-template <int TX, int TY, bool HET>
+template <int TX, int TY, int K>
 struct TmaTile {
     static constexpr int NT = TX * TY / 4;
     static constexpr int GX = TX / 4;
@@ -115,17 +148,63 @@ struct TmaTile {
     static constexpr int BY = TY + 2;
     static constexpr int FIELD = BX * BY;
     static constexpr int STATE = 6 * FIELD;
-    static constexpr int COEF = HET ? 2 * TX * TY : 0;
+    static constexpr int COEF = K == kKindPoint ? 2 * TX * TY : K == kKindDiv ? 3 * FIELD : 0;
     static constexpr int STAGE = (STATE + COEF + 31) / 32 * 32;  // floats, 128 B multiple
 };
 
+// The seven-point neighbourhood of four consecutive x nodes of one staged
+// field: centre, x-, x+, y-, y+, z-, z+ (each a float4 over the four nodes).
+struct Nb7 {
+    float4 c, xm, xp, ym, yp, zm, zp;
+};
+
+template <int BX, int GX>
+__device__ __forceinline__ Nb7 gather7(const float *sc, const float *sm, const float *sp, int off,
+                                       int gx) {
+    Nb7 n;
+    const float *fc = sc + off;
+    n.c = *reinterpret_cast<const float4 *>(fc);
+    n.ym = *reinterpret_cast<const float4 *>(fc - BX);
+    n.yp = *reinterpret_cast<const float4 *>(fc + BX);
+    n.zm = *reinterpret_cast<const float4 *>(sm + off);
+    n.zp = *reinterpret_cast<const float4 *>(sp + off);
+    float left = __shfl_up_sync(0xffffffffu, n.c.w, 1);
+    float right = __shfl_down_sync(0xffffffffu, n.c.x, 1);
+    if (gx == 0) left = fc[-1];
+    if (gx == GX - 1) right = fc[4];
+    n.xm = make_float4(left, n.c.x, n.c.y, n.c.z);
+    n.xp = make_float4(n.c.y, n.c.z, n.c.w, right);
+    return n;
+}
+
+// Lane q (0..3) of a float4.
+__device__ __forceinline__ float lane4(const float4 &v, int q) {
+    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_lane4(float4 &v, int q, float x) {
+    if (q == 0) v.x = x;
+    else if (q == 1) v.y = x;
+    else if (q == 2) v.z = x;
+    else v.w = x;
+}
+
+// Neighbour values of node q of a gathered neighbourhood, order xm, xp, ym, yp, zm, zp.
+__device__ __forceinline__ void nb_of(const Nb7 &n, int q, float (&v)[6]) {
+    v[0] = lane4(n.xm, q);
+    v[1] = lane4(n.xp, q);
+    v[2] = lane4(n.ym, q);
+    v[3] = lane4(n.yp, q);
+    v[4] = lane4(n.zm, q);
+    v[5] = lane4(n.zp, q);
+}
+
 // One block's work: the TX x TY column (bx, by) over planes of z chunk bz.
 // tm_in / tm_coef: addresses of tensor maps in parameter or global memory.
-template <int TX, int TY, int NS, bool HET>
+template <int TX, int TY, int NS, int K>
 __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtensorMap *tm_coef,
                                           const float *__restrict__ F, float *__restrict__ out,
                                           const StepParams &p, int bx, int by, int bz) {
-    using TT = TmaTile<TX, TY, HET>;
+    using TT = TmaTile<TX, TY, K>;
     extern __shared__ __align__(128) float smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * TT::STAGE);
 
@@ -151,11 +230,12 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
         const int s = (q - kb) % NS;
         float *st = smem + s * TT::STAGE;
         const uint32_t bar = bar0 + 8 * s;
-        const bool wc = HET && (q >= k0 && q < k1);
+        const bool wc = (K == kKindPoint && q >= k0 && q < k1) || K == kKindDiv;
         const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0);
         mbar_expect_tx(bar, bytes);
         tma_load_4d(smem_u32(st), tm_in, x0 - 4, y0 - 1, q, 0, bar);
-        if (wc) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0, y0, q, 0, bar);
+        if (K == kKindPoint && wc) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0, y0, q, 0, bar);
+        if (K == kKindDiv) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0 - 4, y0 - 1, q, 0, bar);
     };
 
     if (tid == 0) {
@@ -182,58 +262,102 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
         const float *sm = smem + ((k - 1 - kb) % NS) * TT::STAGE;
         const float *sp = smem + ((k + 1 - kb) % NS) * TT::STAGE;
 
-        float4 ctr[6], sum[6];
+        if constexpr (K == kKindDiv) {
+            // face weights of the four nodes, shared by the three components
+            const Nb7 mn = gather7<TT::BX, TT::GX>(sc, sm, sp, TT::STATE + o, gx);
+            const Nb7 en = gather7<TT::BX, TT::GX>(sc, sm, sp, TT::STATE + TT::FIELD + o, gx);
+            const float4 r4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + 2 * TT::FIELD + o);
+            float wm[4][6], we[4][6];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const float *fc = sc + f * TT::FIELD + o;
-            const float4 c = *reinterpret_cast<const float4 *>(fc);
-            const float4 ym = *reinterpret_cast<const float4 *>(fc - TT::BX);
-            const float4 yp = *reinterpret_cast<const float4 *>(fc + TT::BX);
-            const float4 zm = *reinterpret_cast<const float4 *>(sm + f * TT::FIELD + o);
-            const float4 zp = *reinterpret_cast<const float4 *>(sp + f * TT::FIELD + o);
-            float left = __shfl_up_sync(FULL, c.w, 1);
-            float right = __shfl_down_sync(FULL, c.x, 1);
-            if (gx == 0) left = fc[-1];
-            if (gx == TT::GX - 1) right = fc[4];
-            float4 s;
-            s.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
-            s.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
-            s.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
-            s.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
-            ctr[f] = c;
-            sum[f] = s;
-        }
-        float4 A4, B4;
-        if (HET) {
-            A4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + gy * TX + 4 * gx);
-            B4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + TX * TY + gy * TX + 4 * gx);
-        } else {
-            A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
-            B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
-        }
-        if (row_ok) {
+            for (int q = 0; q < 4; ++q) {
+                float vm[6], ve[6];
+                nb_of(mn, q, vm);
+                nb_of(en, q, ve);
+                const float mc = lane4(mn.c, q), ec = lane4(en.c, q);
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    wm[q][f] = face_weight(mc, vm[f]);
+                    we[q][f] = face_weight(ec, ve[f]);
+                }
+            }
             const long long gbase = k * sz + y * sy + x;
-            const bool m0 = (x >= 1) && (x <= p.nx - 2);
-            const bool m1 = (x + 1 >= 1) && (x + 1 <= p.nx - 2);
-            const bool m2 = (x + 2 <= p.nx - 2);
-            const bool m3 = (x + 3 <= p.nx - 2);
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
-                float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (force)  // force steps are few: the projected force is read directly
-                    F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
-                const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
-                float4 uo, dn;
-                kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g, F4.x, uo.x, dn.x);
-                kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g, F4.y, uo.y, dn.y);
-                kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g, F4.z, uo.z, dn.z);
-                kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g, F4.w, uo.w, dn.w);
-                if (!m0) uo.x = dn.x = 0.f;
-                if (!m1) uo.y = dn.y = 0.f;
-                if (!m2) uo.z = dn.z = 0.f;
-                if (!m3) uo.w = dn.w = 0.f;
-                *reinterpret_cast<float4 *>(out + comp * p.Np + gbase) = uo;
-                *reinterpret_cast<float4 *>(out + (3 + comp) * p.Np + gbase) = dn;
+                const Nb7 un = gather7<TT::BX, TT::GX>(sc, sm, sp, comp * TT::FIELD + o, gx);
+                const Nb7 dnb = gather7<TT::BX, TT::GX>(sc, sm, sp, (3 + comp) * TT::FIELD + o, gx);
+                if (row_ok) {
+                    float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (force) F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
+                    float4 uo, dn;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float nu[6], nd[6], uq, dq;
+                        nb_of(un, q, nu);
+                        nb_of(dnb, q, nd);
+                        kv_update_div(lane4(un.c, q), nu, lane4(dnb.c, q), nd, wm[q], we[q],
+                                      lane4(r4, q), g, lane4(F4, q), uq, dq);
+                        const bool inside = (x + q >= 1) && (x + q <= p.nx - 2);
+                        set_lane4(uo, q, inside ? uq : 0.f);
+                        set_lane4(dn, q, inside ? dq : 0.f);
+                    }
+                    *reinterpret_cast<float4 *>(out + comp * p.Np + gbase) = uo;
+                    *reinterpret_cast<float4 *>(out + (3 + comp) * p.Np + gbase) = dn;
+                }
+            }
+        } else {
+            float4 ctr[6], sum[6];
+    #pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                const float *fc = sc + f * TT::FIELD + o;
+                const float4 c = *reinterpret_cast<const float4 *>(fc);
+                const float4 ym = *reinterpret_cast<const float4 *>(fc - TT::BX);
+                const float4 yp = *reinterpret_cast<const float4 *>(fc + TT::BX);
+                const float4 zm = *reinterpret_cast<const float4 *>(sm + f * TT::FIELD + o);
+                const float4 zp = *reinterpret_cast<const float4 *>(sp + f * TT::FIELD + o);
+                float left = __shfl_up_sync(FULL, c.w, 1);
+                float right = __shfl_down_sync(FULL, c.x, 1);
+                if (gx == 0) left = fc[-1];
+                if (gx == TT::GX - 1) right = fc[4];
+                float4 s;
+                s.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+                s.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+                s.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+                s.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+                ctr[f] = c;
+                sum[f] = s;
+            }
+            float4 A4, B4;
+            if (K == kKindPoint) {
+                A4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + gy * TX + 4 * gx);
+                B4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + TX * TY + gy * TX + 4 * gx);
+            } else {
+                A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+                B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+            }
+            if (row_ok) {
+                const long long gbase = k * sz + y * sy + x;
+                const bool m0 = (x >= 1) && (x <= p.nx - 2);
+                const bool m1 = (x + 1 >= 1) && (x + 1 <= p.nx - 2);
+                const bool m2 = (x + 2 <= p.nx - 2);
+                const bool m3 = (x + 3 <= p.nx - 2);
+    #pragma unroll
+                for (int comp = 0; comp < 3; ++comp) {
+                    float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (force)  // force steps are few: the projected force is read directly
+                        F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
+                    const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
+                    float4 uo, dn;
+                    kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g, F4.x, uo.x, dn.x);
+                    kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g, F4.y, uo.y, dn.y);
+                    kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g, F4.z, uo.z, dn.z);
+                    kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g, F4.w, uo.w, dn.w);
+                    if (!m0) uo.x = dn.x = 0.f;
+                    if (!m1) uo.y = dn.y = 0.f;
+                    if (!m2) uo.z = dn.z = 0.f;
+                    if (!m3) uo.w = dn.w = 0.f;
+                    *reinterpret_cast<float4 *>(out + comp * p.Np + gbase) = uo;
+                    *reinterpret_cast<float4 *>(out + (3 + comp) * p.Np + gbase) = dn;
+                }
             }
         }
         __syncthreads();  // every thread is done with plane k-1's stage
@@ -259,18 +383,18 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
     step_epilogue<float>(out, p, step);
 }
 
-template <int TX, int TY, int NS, bool HET>
+template <int TX, int TY, int NS, int K>
 __global__ void __launch_bounds__(TX *TY / 4)
 k_step_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
            const float *__restrict__ F, float *__restrict__ out, StepParams p) {
-    step_tile<TX, TY, NS, HET>(&tm_in, &tm_coef, F, out, p, blockIdx.x, blockIdx.y, blockIdx.z);
+    step_tile<TX, TY, NS, K>(&tm_in, &tm_coef, F, out, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Batched step: one launch advances every case of a batch by one step. Block
 // b belongs to the case whose [block_begin, block_begin + blocks) holds b; the
 // case's own tensor maps, coefficients, envelope, sensors and control block
 // come from the case table, and its last block runs that case's epilogue.
-template <int TX, int TY, int NS, bool HET>
+template <int TX, int TY, int NS, int K>
 __global__ void __launch_bounds__(TX *TY / 4)
 k_step_batch(const BatchCase *__restrict__ cases, int ncases, int from) {
     int c = 0;
@@ -278,7 +402,7 @@ k_step_batch(const BatchCase *__restrict__ cases, int ncases, int from) {
     const BatchCase &cs = cases[c];
     const int local = blockIdx.x - cs.block_begin;
     const int bx = local % cs.gx, by = (local / cs.gx) % cs.gy, bz = local / (cs.gx * cs.gy);
-    step_tile<TX, TY, NS, HET>(&cs.tm_state[from], &cs.tm_coef, cs.F, cs.state[1 - from], cs.p, bx,
+    step_tile<TX, TY, NS, K>(&cs.tm_state[from], &cs.tm_coef, cs.F, cs.state[1 - from], cs.p, bx,
                                by, bz);
 }
 
@@ -552,17 +676,20 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
 // Small kernels: medium fold, initial velocity
 // ---------------------------------------------------------------------------
 // Grid: (ceil(px/128), ny, nz), block 128.
+// div = 0: coef = [A', B'] = [dt^2 G/(rho dx^2), dt eta/(rho dx^2)] (pointwise operator);
+// div = 1: coef = [m, e, 1/rho] = [dt^2 G/dx^2, dt eta/dx^2, 1/rho] (divergence form).
 template <typename T>
 __global__ void k_fold(const float *__restrict__ G, const float *__restrict__ rho,
                        const float *__restrict__ eta, double Gs, double rhos, double etas,
                        T *__restrict__ coef, T *__restrict__ S, long long Np, int nx, int px,
-                       int ny, double dt, double dx) {
+                       int ny, double dt, double dx, int div) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= px) return;
     const long long c = ((long long)blockIdx.z * ny + blockIdx.y) * px + i;
     if (i >= nx) {  // row padding
         coef[c] = T(0);
         coef[Np + c] = T(0);
+        if (div) coef[2 * Np + c] = T(0);
         S[c] = T(0);
         return;
     }
@@ -570,8 +697,14 @@ __global__ void k_fold(const float *__restrict__ G, const float *__restrict__ rh
     const double r = rho ? (double)rho[c] : rhos;
     const double e = eta ? (double)eta[c] : etas;
     const double inv = 1.0 / (dx * dx);
-    coef[c] = T(dt * dt * g / r * inv);
-    coef[Np + c] = T(dt * e / r * inv);
+    if (div) {
+        coef[c] = T(dt * dt * g * inv);
+        coef[Np + c] = T(dt * e * inv);
+        coef[2 * Np + c] = T(1.0 / r);
+    } else {
+        coef[c] = T(dt * dt * g / r * inv);
+        coef[Np + c] = T(dt * e / r * inv);
+    }
     S[c] = T(dt * dt / r);
 }
 
@@ -632,47 +765,56 @@ kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields
 
 typedef void (*TmaKernel)(const CUtensorMap, const CUtensorMap, const float *, float *, StepParams);
 
+template <int TX, int TY, int NS, int K>
+static void pick_kind(TmaKernel *k, size_t *smem) {
+    *k = k_step_tma<TX, TY, NS, K>;
+    *smem = NS * TmaTile<TX, TY, K>::STAGE * 4 + NS * 8;
+}
+
 template <int TX, int TY, int NS>
-static bool pick(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+static bool pick(int tx, int ty, int ns, int kind, TmaKernel *k, size_t *smem, int *nt) {
     if (tx != TX || ty != TY || ns != NS) return false;
-    if (het) {
-        *k = k_step_tma<TX, TY, NS, true>;
-        *smem = NS * TmaTile<TX, TY, true>::STAGE * 4 + NS * 8;
-    } else {
-        *k = k_step_tma<TX, TY, NS, false>;
-        *smem = NS * TmaTile<TX, TY, false>::STAGE * 4 + NS * 8;
+    switch (kind) {
+        case kKindHomo: pick_kind<TX, TY, NS, kKindHomo>(k, smem); break;
+        case kKindPoint: pick_kind<TX, TY, NS, kKindPoint>(k, smem); break;
+        case kKindDiv: pick_kind<TX, TY, NS, kKindDiv>(k, smem); break;
+        default: return false;
     }
     *nt = TX * TY / 4;
     return true;
 }
 
 template <int NS>
-static bool pick_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
-    return pick<32, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<32, 16, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<64, 4, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<64, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<64, 16, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<128, 2, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<128, 4, NS>(tx, ty, NS, het, k, smem, nt) ||
-           pick<128, 8, NS>(tx, ty, NS, het, k, smem, nt);
+static bool pick_tile(int tx, int ty, int kind, TmaKernel *k, size_t *smem, int *nt) {
+    return pick<32, 8, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<32, 16, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<64, 4, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<64, 8, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<64, 16, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<128, 2, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<128, 4, NS>(tx, ty, NS, kind, k, smem, nt) ||
+           pick<128, 8, NS>(tx, ty, NS, kind, k, smem, nt);
 }
 
 typedef void (*BatchKernel)(const BatchCase *, int, int);
 
 template <int TX, int TY, int NS>
-static bool bpick(int tx, int ty, int ns, bool het, BatchKernel *k) {
+static bool bpick(int tx, int ty, int ns, int kind, BatchKernel *k) {
     if (tx != TX || ty != TY || ns != NS) return false;
-    *k = het ? k_step_batch<TX, TY, NS, true> : k_step_batch<TX, TY, NS, false>;
-    return true;
+    switch (kind) {
+        case kKindHomo: *k = k_step_batch<TX, TY, NS, kKindHomo>; return true;
+        case kKindPoint: *k = k_step_batch<TX, TY, NS, kKindPoint>; return true;
+        case kKindDiv: *k = k_step_batch<TX, TY, NS, kKindDiv>; return true;
+    }
+    return false;
 }
 
 template <int NS>
-static bool bpick_tile(int tx, int ty, bool het, BatchKernel *k) {
-    return bpick<32, 8, NS>(tx, ty, NS, het, k) || bpick<32, 16, NS>(tx, ty, NS, het, k) ||
-           bpick<64, 4, NS>(tx, ty, NS, het, k) || bpick<64, 8, NS>(tx, ty, NS, het, k) ||
-           bpick<64, 16, NS>(tx, ty, NS, het, k) || bpick<128, 2, NS>(tx, ty, NS, het, k) ||
-           bpick<128, 4, NS>(tx, ty, NS, het, k) || bpick<128, 8, NS>(tx, ty, NS, het, k);
+static bool bpick_tile(int tx, int ty, int kind, BatchKernel *k) {
+    return bpick<32, 8, NS>(tx, ty, NS, kind, k) || bpick<32, 16, NS>(tx, ty, NS, kind, k) ||
+           bpick<64, 4, NS>(tx, ty, NS, kind, k) || bpick<64, 8, NS>(tx, ty, NS, kind, k) ||
+           bpick<64, 16, NS>(tx, ty, NS, kind, k) || bpick<128, 2, NS>(tx, ty, NS, kind, k) ||
+           bpick<128, 4, NS>(tx, ty, NS, kind, k) || bpick<128, 8, NS>(tx, ty, NS, kind, k);
 }
 
 template <int TX, int TY, int NS>
@@ -704,12 +846,23 @@ static bool tma2_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size
     }
 }
 
-static bool tma_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+static bool tma_kernel_for(int tx, int ty, int ns, int kind, TmaKernel *k, size_t *smem, int *nt) {
     switch (ns) {
-        case 4: return pick_tile<4>(tx, ty, het, k, smem, nt);
-        case 6: return pick_tile<6>(tx, ty, het, k, smem, nt);
-        case 8: return pick_tile<8>(tx, ty, het, k, smem, nt);
+        case 4: return pick_tile<4>(tx, ty, kind, k, smem, nt);
+        case 6: return pick_tile<6>(tx, ty, kind, k, smem, nt);
+        case 8: return pick_tile<8>(tx, ty, kind, k, smem, nt);
         default: return false;
+    }
+}
+
+// Tensor map of the coefficient fields for a tile (tx, ty): the centre tile
+// of (A', B') for the pointwise operator, the haloed tile of (m, e, 1/rho)
+// for the divergence form; unused placeholder for a homogeneous medium.
+static kv_status encode_coef_map(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
+    switch (step_kind(h)) {
+        case kKindPoint: return encode_tensor_4d(h, tm, h->coef, 2, tx, ty, 2);
+        case kKindDiv: return encode_tensor_4d(h, tm, h->coef, 3, tx + 8, ty + 2, 3);
+        default: *tm = h->tm_state[0]; return KV_OK;
     }
 }
 
@@ -720,6 +873,8 @@ kv_status step_prepare(kv_handle *h) {
     size_t smem;
     int nt;
     if (h->variant == 2) {
+        if (step_kind(h) == kKindDiv)
+            return set_error(h, KV_ERR_UNSUPPORTED, "the two-step kernel supports only the pointwise operator");
         if (!tma2_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
             return set_error(h, KV_ERR_ARG, "no two-step kernel for tile %dx%d with %d stages", h->tx, h->ty,
                              h->ns_stages);
@@ -738,7 +893,7 @@ kv_status step_prepare(kv_handle *h) {
         h->tma_ready = 1;
         return KV_OK;
     }
-    if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
+    if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, step_kind(h), &k, &smem, &nt))
         return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d with %d stages", h->tx,
                          h->ty, h->ns_stages);
     if (smem > 227 * 1024)
@@ -748,9 +903,7 @@ kv_status step_prepare(kv_handle *h) {
     for (int b = 0; b < 2; ++b)
         if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 2, 6)) != KV_OK)
             return st;
-    if (h->het && (st = encode_tensor_4d(h, &h->tm_coef, h->coef, 2, h->tx, h->ty, 2)) != KV_OK)
-        return st;
-    if (!h->het) h->tm_coef = h->tm_state[0];  // unused placeholder
+    if ((st = encode_coef_map(h, &h->tm_coef, h->tx, h->ty)) != KV_OK) return st;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(step)");
     h->tma_ready = 1;
@@ -811,7 +964,7 @@ kv_status step_launch(kv_handle *h, int from) {
         TmaKernel k;
         size_t smem;
         int nt;
-        tma_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt);
+        tma_kernel_for(h->tx, h->ty, h->ns_stages, step_kind(h), &k, &smem, &nt);
         dim3 grid((h->px + h->tx - 1) / h->tx, (h->ny - 2 + h->ty - 1) / h->ty,
                   (h->nz - 2 + h->zc - 1) / h->zc);
         StepParams p = make_params(h, grid.x * grid.y * grid.z);
@@ -820,22 +973,19 @@ kv_status step_launch(kv_handle *h, int from) {
     } else {
         dim3 grid((h->nx + 127) / 128, h->ny - 2, h->nz - 2);
         StepParams p = make_params(h, grid.x * grid.y * grid.z);
+        const int kind = step_kind(h);
         if (h->precision == KV_FP64) {
-            if (h->het)
-                k_step_plain<double, true><<<grid, 128, 0, h->stream>>>(
-                    (const double *)in, (double *)out, (const double *)h->coef,
-                    (const double *)h->F, p);
-            else
-                k_step_plain<double, false><<<grid, 128, 0, h->stream>>>(
-                    (const double *)in, (double *)out, nullptr, (const double *)h->F, p);
+            const double *ci = (const double *)in, *co = (const double *)h->coef, *cf = (const double *)h->F;
+            double *o = (double *)out;
+            if (kind == kKindDiv) k_step_plain<double, kKindDiv><<<grid, 128, 0, h->stream>>>(ci, o, co, cf, p);
+            else if (kind == kKindPoint) k_step_plain<double, kKindPoint><<<grid, 128, 0, h->stream>>>(ci, o, co, cf, p);
+            else k_step_plain<double, kKindHomo><<<grid, 128, 0, h->stream>>>(ci, o, nullptr, cf, p);
         } else {
-            if (h->het)
-                k_step_plain<float, true><<<grid, 128, 0, h->stream>>>(
-                    (const float *)in, (float *)out, (const float *)h->coef, (const float *)h->F,
-                    p);
-            else
-                k_step_plain<float, false><<<grid, 128, 0, h->stream>>>(
-                    (const float *)in, (float *)out, nullptr, (const float *)h->F, p);
+            const float *ci = (const float *)in, *co = (const float *)h->coef, *cf = (const float *)h->F;
+            float *o = (float *)out;
+            if (kind == kKindDiv) k_step_plain<float, kKindDiv><<<grid, 128, 0, h->stream>>>(ci, o, co, cf, p);
+            else if (kind == kKindPoint) k_step_plain<float, kKindPoint><<<grid, 128, 0, h->stream>>>(ci, o, co, cf, p);
+            else k_step_plain<float, kKindHomo><<<grid, 128, 0, h->stream>>>(ci, o, nullptr, cf, p);
         }
     }
     h->launches++;
@@ -849,11 +999,11 @@ kv_status launch_fold(kv_handle *h, const float *G, double Gs, const float *rho,
     if (h->precision == KV_FP64)
         k_fold<double><<<grid, 128, 0, h->stream>>>(G, rho, eta, Gs, rhos, etas, (double *)h->coef,
                                                     (double *)h->S, h->Np, h->nx, h->px, h->ny,
-                                                    h->dt, h->dx);
+                                                    h->dt, h->dx, step_kind(h) == kKindDiv);
     else
         k_fold<float><<<grid, 128, 0, h->stream>>>(G, rho, eta, Gs, rhos, etas, (float *)h->coef,
                                                    (float *)h->S, h->Np, h->nx, h->px, h->ny, h->dt,
-                                                   h->dx);
+                                                   h->dx, step_kind(h) == kKindDiv);
     h->launches++;
     return cuda_check(h, cudaGetLastError(), "fold launch");
 }
@@ -874,15 +1024,15 @@ kv_status launch_init_velocity(kv_handle *h, const float *v_pitched) {
 // ---------------------------------------------------------------------------
 // Batched step support (kv_batch.cu)
 // ---------------------------------------------------------------------------
-kv_status batch_kernel_for(int tx, int ty, int ns, bool het, void **kernel, size_t *smem, int *nt) {
+kv_status batch_kernel_for(int tx, int ty, int ns, int kind, void **kernel, size_t *smem, int *nt) {
     TmaKernel single;
-    if (!tma_kernel_for(tx, ty, ns, het, &single, smem, nt)) return KV_ERR_ARG;
+    if (!tma_kernel_for(tx, ty, ns, kind, &single, smem, nt)) return KV_ERR_ARG;
     BatchKernel k = nullptr;
     bool ok = false;
     switch (ns) {
-        case 4: ok = bpick_tile<4>(tx, ty, het, &k); break;
-        case 6: ok = bpick_tile<6>(tx, ty, het, &k); break;
-        case 8: ok = bpick_tile<8>(tx, ty, het, &k); break;
+        case 4: ok = bpick_tile<4>(tx, ty, kind, &k); break;
+        case 6: ok = bpick_tile<6>(tx, ty, kind, &k); break;
+        case 8: ok = bpick_tile<8>(tx, ty, kind, &k); break;
     }
     if (!ok || *smem > 227 * 1024) return KV_ERR_ARG;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
@@ -899,7 +1049,7 @@ kv_status batch_fill_case(kv_handle *h, BatchCase *bc, int tx, int ty, int zc, i
         if ((st = encode_tensor_4d(h, &bc->tm_state[b], h->state[b], 6, tx + 8, ty + 2, 6)) != KV_OK)
             return st;
     if (h->het) {
-        if ((st = encode_tensor_4d(h, &bc->tm_coef, h->coef, 2, tx, ty, 2)) != KV_OK) return st;
+        if ((st = encode_coef_map(h, &bc->tm_coef, tx, ty)) != KV_OK) return st;
     } else {
         bc->tm_coef = bc->tm_state[0];
     }

@@ -145,6 +145,14 @@ def pulsed_envelope(n_steps, dt, t_on, t_off, n_pulses):
     return (on & (idx < n_pulses)).astype(np.float32)
 
 
+def harmonic_envelope(n_steps, dt, omega, t_ramp):
+    """Harmonic drive g_n = r(t_n) sin(omega t_n), t_n = n dt, with a
+    raised-cosine ramp r = (1 - cos(pi t / t_ramp)) / 2 for t < t_ramp."""
+    t = np.arange(n_steps, dtype=np.float64) * dt
+    r = np.where(t < t_ramp, 0.5 * (1.0 - np.cos(np.pi * t / max(t_ramp, 1e-300))), 1.0)
+    return (r * np.sin(omega * t)).astype(np.float32)
+
+
 def line_sensors(start_ijk, axis, stop, stride=1):
     """Sensors along one axis from start_ijk (inclusive) to stop (exclusive)."""
     pts = []
@@ -392,3 +400,35 @@ def qiba_phantom(G, nx=240, ny=200, nz=200, dx=0.25 * MM, x_f=30 * MM, sigma=(4.
                  (bx, zero, zero.copy()), t_push, n_steps, sensors, 1e-8,
                  extra={"offsets_m": (np.arange(j0, j1 + 1) - cj) * dx, "t_window_s": (offsets[1] + 6 * MM) / c + t_push})
     return w
+
+
+def guided_mode_case(nx, ny, nz, dx, G, rho, eta, src_i, sensor_i, amp=1e3, src_w=1.5,
+                     name=None):
+    """Harmonic-benchmark geometry on a 3D grid with Dirichlet walls: a force
+    whose z component has the separable shape h(x) s(y) s(z), s the first
+    Dirichlet sine mode of the cross-section (s_j = sin(pi j / (n - 1))).
+
+    The force is the forward-difference curl of Psi = y_hat psi,
+    psi = H(x) s(y) s(z), H(i) = amp exp(-((i - src_i) / src_w)^2):
+    f_x = -(psi_{k+1} - psi_k) / dx, f_y = 0, f_z = (psi_{i+1} - psi_i) / dx
+    (psi = 0 beyond the grid). Its backward-difference divergence vanishes on
+    every interior node, so the projection leaves it unchanged up to rounding.
+    Sensors on the x line through the centre of the cross-section at nodes
+    sensor_i (ny, nz odd so that the centre is a node)."""
+    assert ny % 2 == 1 and nz % 2 == 1
+    i = np.arange(nx, dtype=np.float64)
+    H = amp * np.exp(-((i - src_i) / src_w) ** 2)
+    sy = np.sin(np.pi * np.arange(ny) / (ny - 1))
+    sz = np.sin(np.pi * np.arange(nz) / (nz - 1))
+    psi = sz[:, None, None] * sy[None, :, None] * H[None, None, :]
+    pad_x = np.concatenate([psi, np.zeros((nz, ny, 1))], axis=2)
+    pad_z = np.concatenate([psi, np.zeros((1, ny, nx))], axis=0)
+    fz = (pad_x[:, :, 1:] - pad_x[:, :, :-1]) / dx
+    fx = -(pad_z[1:] - pad_z[:-1]) / dx
+    fy = np.zeros_like(fz)
+    sensors = np.stack([np.asarray(sensor_i, np.int32),
+                        np.full(len(sensor_i), ny // 2, np.int32),
+                        np.full(len(sensor_i), nz // 2, np.int32)], axis=1)
+    return Workload(name or f"guided_mode_{nx}x{ny}x{nz}_eta{eta:g}", nx, ny, nz, dx, G, rho, eta,
+                    (fx.astype(np.float32), fy.astype(np.float32), fz.astype(np.float32)), 0.0, 0,
+                    sensors, 1e-8)

@@ -35,6 +35,8 @@ KV_FP64 = 1
 KV_SCALAR = 0
 KV_HOST = 1
 KV_DEVICE = 2
+KV_OP_POINTWISE = 0
+KV_OP_DIVERGENCE = 1
 
 FIELD_U, FIELD_D, FIELD_PHI, FIELD_F = 0, 1, 2, 3
 
@@ -78,6 +80,8 @@ def lib():
         L.kv_stable_dt.argtypes = [i, i, i, d, F, F, F, ctypes.POINTER(d)]
         L.kv_create.argtypes = [ctypes.POINTER(H), i, i, i, d, d, F, F, F, i, vp]
         L.kv_set_medium.argtypes = [H, F, F, F]
+        L.kv_stable_dt_op.argtypes = [i, i, i, d, F, F, F, i, ctypes.POINTER(d)]
+        L.kv_set_operator.argtypes = [H, i, F, F, F]
         L.kv_set_envelope.argtypes = [H, vp, i, i]
         L.kv_set_sensors.argtypes = [H, vp, i, i]
         L.kv_reset.argtypes = [H]
@@ -192,6 +196,14 @@ def kv_stable_dt(nx, ny, nz, dx, G, rho, eta):
     return out.value
 
 
+def kv_stable_dt_op(nx, ny, nz, dx, G, rho, eta, op):
+    keep = []
+    out = ctypes.c_double()
+    _check(lib().kv_stable_dt_op(nx, ny, nz, dx, field(G, keep), field(rho, keep), field(eta, keep),
+                                 int(op), ctypes.byref(out)))
+    return out.value
+
+
 def kv_create(nx, ny, nz, dx, dt, G, rho, eta, precision=KV_FP32, stream=None):
     keep = []
     h = ctypes.c_void_p()
@@ -204,6 +216,11 @@ def kv_create(nx, ny, nz, dx, dt, G, rho, eta, precision=KV_FP32, stream=None):
 def kv_set_medium(h, G, rho, eta):
     keep = []
     _check(lib().kv_set_medium(h, field(G, keep), field(rho, keep), field(eta, keep)), h)
+
+
+def kv_set_operator(h, op, G, rho, eta):
+    keep = []
+    _check(lib().kv_set_operator(h, int(op), field(G, keep), field(rho, keep), field(eta, keep)), h)
 
 
 def kv_set_envelope(h, g):

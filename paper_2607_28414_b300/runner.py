@@ -21,7 +21,8 @@ class Solver:
     """Owns one libkv handle for a workload."""
 
     def __init__(self, w: inputs.Workload, precision=kv.KV_FP32, dt=None, n_steps=None,
-                 device="cuda:0", stream=None, step_config=None):
+                 device="cuda:0", stream=None, step_config=None, operator=kv.KV_OP_POINTWISE,
+                 envelope=None):
         import torch
         self.w = w
         self.device = torch.device(device)
@@ -30,13 +31,19 @@ class Solver:
         self.medium = [to_device(x, self.device) for x in (w.G, w.rho, w.eta)]
         self.force = [to_device(f, self.device) for f in w.force]
         if dt is None:
-            dt = w.cfl_fraction * kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *self.medium)
+            lim = kv.kv_stable_dt(w.nx, w.ny, w.nz, w.dx, *self.medium)
+            if operator != kv.KV_OP_POINTWISE:
+                lim = min(lim, kv.kv_stable_dt_op(w.nx, w.ny, w.nz, w.dx, *self.medium, operator))
+            dt = w.cfl_fraction * lim
         self.dt = dt
         self.h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, *self.medium, precision=precision,
                               stream=stream)
+        if operator != kv.KV_OP_POINTWISE:
+            kv.kv_set_operator(self.h, operator, *self.medium)
         if step_config:
             kv.kv_set_step_config(self.h, **step_config)
-        self.envelope = inputs.push_envelope(self.n_steps, dt, w.t_push)
+        self.envelope = (inputs.push_envelope(self.n_steps, dt, w.t_push) if envelope is None
+                         else envelope(self.n_steps, dt))
         kv.kv_set_envelope(self.h, self.envelope)
         kv.kv_set_sensors(self.h, w.sensors, self.n_steps)
         self.trace_dtype = torch.float64 if precision == kv.KV_FP64 else torch.float32

@@ -115,3 +115,75 @@ def test_xcorr_group_speed_recovers_a_known_speed():
     tr = np.stack([np.exp(-((t - 2e-3 - o / c) / 6e-4) ** 2) * np.sin(2 * np.pi * 400 * (t - o / c))
                    for o in offs], axis=1)
     assert orc.xcorr_group_speed(tr, offs, dt) == pytest.approx(c, rel=2e-3)
+
+
+# ---------------------------------------------------------------------------
+# Guided-mode form of the harmonic benchmark (3D grids with Dirichlet walls)
+# ---------------------------------------------------------------------------
+
+def test_dirichlet_mode_eigenvalue_is_the_sine_mode_eigenvalue():
+    n, dx = 23, 1.3e-4
+    j = np.arange(n)
+    s = np.sin(np.pi * j / (n - 1))
+    lap = np.zeros(n)
+    lap[1:-1] = -(s[2:] - 2 * s[1:-1] + s[:-2]) / dx ** 2
+    lam = orc.dirichlet_mode_eigenvalue(n, dx)
+    np.testing.assert_allclose(lap[1:-1], lam * s[1:-1], rtol=1e-10)
+    # continuum limit (pi / L)^2
+    assert orc.dirichlet_mode_eigenvalue(2001, 1e-6) == pytest.approx((np.pi / 2e-3) ** 2, rel=1e-6)
+
+
+def test_guided_dispersion_reduces_to_the_waveguide_relation():
+    """eta = 0, fine grid and step: k_x^2 = omega^2 / c^2 - lam_t (continuum
+    waveguide); lam_t = 0 gives the plane-wave relation unchanged."""
+    w = 2 * np.pi * 800.0
+    c0 = np.sqrt(MU / RHO)
+    lam_t = (0.4 * w / c0) ** 2
+    dx, dt = 1e-7, 1e-11
+    _, c = orc.kv_discrete(w, MU, RHO, 0.0, dx, dt, lam_t=lam_t)
+    kx = np.sqrt((w / c0) ** 2 - lam_t)
+    assert c == pytest.approx(w / kx, rel=1e-6)
+    a0 = orc.kv_discrete(w, MU, RHO, 0.7, 1e-4, 2e-6)
+    assert orc.kv_discrete(w, MU, RHO, 0.7, 1e-4, 2e-6, lam_t=0.0) == a0
+    # a guide slows nothing down in phase below c0 and adds attenuation
+    ag, cg = orc.kv_discrete(w, MU, RHO, 0.7, 1e-4, 2e-6, lam_t=(0.5 * w / c0) ** 2)
+    assert cg > a0[1] and ag > a0[0]
+
+
+def test_plane_from_guided_inverts_the_guide():
+    w = 2 * np.pi * 761.0
+    for eta in (0.0, 0.3, 1.5):
+        dx, dt = 1e-4, 5e-7
+        lam_t = 2 * orc.dirichlet_mode_eigenvalue(49, dx)
+        ag, cg = orc.kv_discrete(w, MU, RHO, eta, dx, dt, lam_t=lam_t)
+        ap, cp = orc.kv_plane_from_guided(ag, cg, w, dx, lam_t)
+        a0, c0 = orc.kv_discrete(w, MU, RHO, eta, dx, dt)
+        assert cp == pytest.approx(c0, rel=1e-9)
+        assert ap == pytest.approx(a0, rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.slow
+def test_guided_mode_of_the_3d_recurrence_follows_the_guided_dispersion():
+    """The oracle's 3D stepper driven by a separable curl force
+    (u_z = U(x) s(y) s(z)) propagates U with kv_discrete(..., lam_t)."""
+    from paper_2607_28414_b300 import inputs
+    eta, f0 = 0.3, 800.0
+    w = 2 * np.pi * f0
+    dx = 1.25e-4
+    nt = 31
+    a_c, c_c = orc.kv_continuum(w, MU, RHO, eta)
+    le = 1.0 / a_c
+    src = 4
+    sens = src + 6 + np.round(np.linspace(0.5 * le, 3.0 * le, 12) / dx).astype(np.int32)
+    nx = int(sens[-1] + 8 * le / dx) + 2
+    dt = 0.5 * orc.stable_dt(MU, RHO, eta, dx)
+    period = 1 / f0
+    n_steps = int((3 * le / c_c + 18 * period) / dt)
+    wl = inputs.guided_mode_case(nx, nt, nt, dx, MU, RHO, eta, src, sens)
+    g = inputs.harmonic_envelope(n_steps, dt, w, 4 * period)
+    tr = orc.run(nx, nt, nt, dx, dt, MU, RHO, eta, n_steps, wl.sensors, fs=wl.force, g=g)
+    lam_t = 2 * orc.dirichlet_mode_eigenvalue(nt, dx)
+    a_m, c_m = orc.lockin_fit(tr[:, :, 2], sens * dx, dt, w, 6)
+    a_d, c_d = orc.kv_discrete(w, MU, RHO, eta, dx, dt, lam_t=lam_t)
+    assert a_m == pytest.approx(a_d, rel=5e-4)
+    assert c_m == pytest.approx(c_d, rel=2e-4)
