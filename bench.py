@@ -46,6 +46,23 @@ DIV_STEP_BYTES_PER_CELL = 60  # divergence form: coefficients m, e, 1/rho 12 B
 FORCE_BYTES_PER_CELL = 12  # projected force on force steps
 
 
+def slowest(t, world, device):
+    """The job time of independent replicas: the maximum of the per-rank time
+    over all ranks (an all-reduce on the process group; identity at world 1)."""
+    if world == 1:
+        return float(t)
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def job_rate(world, cell_updates_per_rank, t_max):
+    """Whole-job Gcell-updates/s: every rank's cell-updates over the slowest rank's time."""
+    return world * cell_updates_per_rank / t_max / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -67,6 +84,8 @@ def parse():
     ap.add_argument("--step-config", default=None,
                     help="[variant,]tx,ty,zc,ns of the step kernel instead of autotuning "
                          "(profiling runs; variant 0 one step per sweep, 2 two steps per sweep)")
+    ap.add_argument("--cg-config", type=int, default=None,
+                    help="z chunk of the CG passes (default: the CG autotuner's choice)")
     ap.add_argument("--cg-tol", type=float, default=1e-8,
                     help="projection tolerance (1e-8 is the workload's; larger values only for "
                          "short profiling runs)")
@@ -206,9 +225,12 @@ def run_sweep(args, rank, world):
     batched steps, traces read."""
     import torch
     from paper_2607_28414_b300 import inputs, kv
+    import torch.distributed as dist
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
     n_steps = args.time_steps if args.time_steps != N_TIME_STEPS else 1000
@@ -248,6 +270,9 @@ def run_sweep(args, rank, world):
         one_pass()
     torch.cuda.synchronize(device)
     clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(device)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = kv.kv_batch_launch_count(b) + sum(kv.kv_launch_count(h) for h in hs)
@@ -256,8 +281,10 @@ def run_sweep(args, rank, world):
         n_proj = one_pass()
     e1.record(stream)
     torch.cuda.synchronize(device)
+    if world > 1:
+        dist.barrier()
     clk = clocks.stop()
-    t = e0.elapsed_time(e1) / 1e3
+    t = slowest(e0.elapsed_time(e1) / 1e3, world, device)
     # step-only timing of the batched kernel
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for h in hs:
@@ -271,7 +298,7 @@ def run_sweep(args, rank, world):
     kv.kv_batch_destroy(b)
     for h in hs:
         kv.kv_destroy(h)
-    value = N * n_steps * args.steps / t / 1e9
+    value = job_rate(world, N * n_steps * args.steps, t)
     bytes_per_step = 48.0 * N  # homogeneous: (u, d) read + write
     achieved = bytes_per_step / (t_steps / n_steps) / 1e9
     peak, peak_kind = peaks()
@@ -282,6 +309,7 @@ def run_sweep(args, rank, world):
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep_26_cases", "cells": N, "time_steps": n_steps,
+                       "parallelism": f"replicas{world}",
                        "projections_per_pass": n_proj, "batch_config": cfg,
                        "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2"},
             "kv_step_gcells": N * n_steps / t_steps / 1e9, "autotune_ms_per_step": tune_ms,
@@ -290,6 +318,8 @@ def run_sweep(args, rank, world):
                          "peak_kind": peak_kind, "bytes_model": "48 B/cell (homogeneous)"},
             "gpu_launches": int(launches), "clocks": clk, "e2e": None, "cpu_baseline": None}),
             flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -341,6 +371,12 @@ def main():
     else:
         tune_ms = kv.kv_autotune_step(h, 8)  # picks tile / stages / z chunk; resets the state
     step_cfg = kv.kv_get_step_config(h)
+    if args.cg_config is not None:
+        kv.kv_set_cg_config(h, args.cg_config)
+        cg_tune_ms = None
+    else:
+        cg_tune_ms = kv.kv_autotune_cg(h, *force_d, 40)  # trial projections; the pass projects again
+    cg_zc = kv.kv_get_cg_config(h)
     g = inputs.push_envelope(w.n_steps, dt, w.t_push)
     n_force_steps = int(g.sum())
     kv.kv_set_envelope(h, g)
@@ -387,12 +423,8 @@ def main():
     launches = kv.kv_launch_count(h) - launches0
     t_total = e0.elapsed_time(e1) / 1e3
     t_steps = sum(a.elapsed_time(b) for a, b in step_evs) / 1e3
-    t_max = t_total
-    if world > 1:
-        t = torch.tensor([t_total], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * N * w.n_steps * args.steps / t_max / 1e9
+    t_max = slowest(t_total, world, device)
+    value = job_rate(world, N * w.n_steps * args.steps, t_max)
     step_gcells = N * w.n_steps * args.steps / t_steps / 1e9
     launch_s = t_steps / (w.n_steps * args.steps)
     alg_bytes = (N * bytes_per_cell * w.n_steps + N * FORCE_BYTES_PER_CELL * n_force_steps) \
@@ -427,12 +459,8 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize(device)
         barrier()
-        t_e2e = max(f0.elapsed_time(f1) / 1e3, 1e-12)
-        if world > 1:
-            t = torch.tensor([t_e2e], device=device, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * N * w.n_steps * args.steps / t_e2e / 1e9,
+        t_e2e = slowest(max(f0.elapsed_time(f1) / 1e3, 1e-12), world, device)
+        e2e = {"value": job_rate(world, N * w.n_steps * args.steps, t_e2e),
                "unit": "Gcell-updates/s", "h2d_bytes_per_step": 6 * N * 4,
                "d2h_bytes_per_step": int(traces_h.numel() * 4),
                "wall_s": time.perf_counter() - t0}
@@ -462,6 +490,7 @@ def main():
             "kv_step_gcells": step_gcells,
             "projection_ms": float(np.mean(cg_ms)), "cg_iters": int(np.median(cg_iters)),
             "step_config": step_cfg, "autotune_ms_per_step": tune_ms,
+            "cg_zc": cg_zc, "cg_autotune_ms_40_iters": cg_tune_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_step_tma", "peak_kind": peak_kind,

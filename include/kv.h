@@ -314,6 +314,23 @@ kv_status kv_get_step_config(kv_handle *h, int *cfg);
  * milliseconds per step of the choice (NULL allowed). Synchronising. */
 kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms);
 
+/* Launch shape of the FP32 CG passes (Sec. 3.2.3 iteration): zc planes per
+ * block of the TMA z-march (0: default 16). A value giving more blocks than
+ * the handle's reduction buffer holds is refused (KV_ERR_ARG). The arithmetic
+ * and its order do not depend on zc except through the order of the block
+ * partial sums. kv_get_cg_config: the current zc. */
+kv_status kv_set_cg_config(kv_handle *h, int zc);
+kv_status kv_get_cg_config(kv_handle *h, int *zc);
+
+/* Autotuner of the FP32 CG passes: runs the projection of (fx, fy, fz) for
+ * iters iterations (twice) with each z chunk in {8, 16, 24, 32, 48, 64, 96,
+ * 128} that fits the grid, keeps the fastest and reports its wall time in
+ * *best_ms (NULL allowed). The trial projections stop early, so the force
+ * must be projected again (kv_project_force) before stepping. No-op for
+ * FP64 handles. Synchronising. */
+kv_status kv_autotune_cg(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, int iters,
+                         double *best_ms);
+
 /* Number of kernel launches libkv has issued on this handle. */
 long long kv_launch_count(kv_handle *h);
 

@@ -487,6 +487,58 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
     return project(h, tol, max_iter, mode, fs_out, stats);
 }
 
+kv_status kv_set_cg_config(kv_handle *h, int zc) {
+    if (!h || zc < 0) return set_error(h, KV_ERR_ARG, "kv_set_cg_config: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    const long long gx = (h->px + 63) / 64, gy = (h->ny - 2 + 7) / 8;
+    const int z = zc > 0 ? zc : 16;
+    if (gx * gy * ((h->nz - 2 + z - 1) / z) > h->partials_len)
+        return set_error(h, KV_ERR_ARG, "kv_set_cg_config: z chunk %d gives too many blocks", zc);
+    h->cg_zc = zc;
+    return KV_OK;
+}
+
+kv_status kv_get_cg_config(kv_handle *h, int *zc) {
+    if (!h || !zc) return KV_ERR_ARG;
+    *zc = h->cg_zc > 0 ? h->cg_zc : 16;
+    return KV_OK;
+}
+
+kv_status kv_autotune_cg(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, int iters, double *best_ms) {
+    if (!h || iters < 1) return set_error(h, KV_ERR_ARG, "kv_autotune_cg: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    if (h->precision != KV_FP32) {  // the FP64 passes have one fixed shape
+        if (best_ms) *best_ms = 0.0;
+        return KV_OK;
+    }
+    const int cand[] = {8, 16, 24, 32, 48, 64, 96, 128};
+    const int saved = h->cg_zc;
+    int best = -1;
+    double best_t = INFINITY;
+    for (int zc : cand) {
+        if (zc > std::max(h->nz - 2, 8) || kv_set_cg_config(h, zc) != KV_OK) continue;
+        double t = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run also warms the caches
+            kv_cg_stats stc;
+            kv_status st = kv_project_force(h, fx, fy, fz, 1e-30, iters, 0, nullptr, &stc);
+            if (st != KV_OK && st != KV_CG_MAXITER) {
+                h->cg_zc = saved;
+                return st;
+            }
+            t = std::min(t, stc.ms);
+        }
+        if (t < best_t) {
+            best_t = t;
+            best = zc;
+        }
+    }
+    h->cg_zc = best > 0 ? best : saved;
+    h->have_force = 0;  // the trial projections stopped early: project again before stepping
+    h->phi_valid = 0;
+    if (best_ms) *best_ms = best_t;
+    return KV_OK;
+}
+
 kv_status kv_step_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol, int max_iter,
                         int mode, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;

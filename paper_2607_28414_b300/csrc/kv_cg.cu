@@ -827,9 +827,10 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     cudaError_t e;
     // FP32: the two CG passes run as TMA-staged z-march kernels
     const bool use_tma = (h->precision == KV_FP32);
+    const int tzc = h->cg_zc > 0 ? h->cg_zc : kCgTZc;
     const dim3 tgrid((h->px + kCgTX - 1) / kCgTX, (h->ny - 2 + kCgTY - 1) / kCgTY,
-                     (h->nz - 2 + kCgTZc - 1) / kCgTZc);
-    CgParams pt = cg_params(h, tgrid, kCgTZc);
+                     (h->nz - 2 + tzc - 1) / tzc);
+    CgParams pt = cg_params(h, tgrid, tzc);
     if (use_tma) {
         kv_status ts = cg_tma_prepare(h);
         if (ts != KV_OK) return ts;

@@ -145,6 +145,7 @@ struct kv_handle {
     void *e;               // [Np] correction accumulated since the last replacement
     CUtensorMap tm_cg_h2, tm_cg_h1, tm_cg_c1;  // TMA views of cgv (FP32)
     int cg_tma_ready;
+    int cg_zc;             // planes per block of the TMA CG passes (0: default)
     double *phi;           // [Np]
     double *b;             // [Np] right-hand side
     double *scal;          // kv::kCgScalars

@@ -96,6 +96,9 @@ def lib():
         L.kv_read_field.argtypes = [H, i, i, vp, i]
         L.kv_sync.argtypes = [H]
         L.kv_set_step_config.argtypes = [H, i, i, i, i, i]
+        L.kv_set_cg_config.argtypes = [H, i]
+        L.kv_get_cg_config.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
+        L.kv_autotune_cg.argtypes = [H, F, F, F, i, ctypes.POINTER(d)]
         L.kv_get_step_config.argtypes = [H, ctypes.POINTER(ctypes.c_int)]
         L.kv_autotune_step.argtypes = [H, i, ctypes.POINTER(d)]
         L.kv_launch_count.argtypes = [H]
@@ -335,6 +338,24 @@ def kv_get_step_config(h):
     cfg = (ctypes.c_int * 5)()
     _check(lib().kv_get_step_config(h, cfg), h)
     return dict(zip(("variant", "tx", "ty", "zc", "ns"), list(cfg)))
+
+
+def kv_set_cg_config(h, zc):
+    _check(lib().kv_set_cg_config(h, int(zc)), h)
+
+
+def kv_get_cg_config(h):
+    zc = ctypes.c_int()
+    _check(lib().kv_get_cg_config(h, ctypes.byref(zc)), h)
+    return zc.value
+
+
+def kv_autotune_cg(h, fx, fy, fz, iters=40):
+    keep = []
+    out = ctypes.c_double()
+    _check(lib().kv_autotune_cg(h, field(fx, keep), field(fy, keep), field(fz, keep), int(iters),
+                                ctypes.byref(out)), h)
+    return out.value
 
 
 def kv_autotune_step(h, trial_steps=8):
