@@ -4,8 +4,9 @@ One bench step is one whole pass of the pre-computed-projection pipeline over
 the 256^3 heterogeneous workload (8 seeded spherical inclusions, speckled axial
 beam, dx = 0.2 mm, dt = 0.5 x the stability limit): fold the medium into the
 step coefficients, zero the state, project the force (CG to a true relative
-residual of 1e-8), run 2000 fused time steps with sensor recording and read
-the traces.
+residual of 1e-8; by default preconditioned by a multigrid V-cycle, with
+--projection cg the paper's plain CG), run 2000 fused time steps with sensor
+recording and read the traces.
 
 value  = cell-updates of the pass (nx*ny*nz*2000) / pass time, in Gcell/s,
          inputs resident on the device.
@@ -63,6 +64,26 @@ def job_rate(world, cell_updates_per_rank, t_max):
     return world * cell_updates_per_rank / t_max / 1e9
 
 
+def step_traffic(w, step_cfg, operator, n_force_steps):
+    """DRAM bytes per step launch from the committed ncu capture
+    (profiles/kv_step_traffic.json: dram__bytes_read.sum + dram__bytes_write.sum
+    of force and plain steps), averaged over this pass's launches like
+    `achieved`; None unless the capture is of this grid, operator and kernel
+    configuration."""
+    tfile = os.path.join(ROOT, "profiles", "kv_step_traffic.json")
+    if not os.path.exists(tfile):
+        return None
+    try:
+        for c in json.load(open(tfile))["captures"]:
+            if (c["grid"] == [w.nx, w.ny, w.nz] and c["operator"] == operator
+                    and c["step_config"] == step_cfg):
+                nf = n_force_steps
+                return (nf * c["bytes_force_step"] + (w.n_steps - nf) * c["bytes_plain_step"]) / w.n_steps
+    except (KeyError, ValueError, TypeError):
+        return None
+    return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -84,6 +105,9 @@ def parse():
     ap.add_argument("--step-config", default=None,
                     help="[variant,]tx,ty,zc,ns of the step kernel instead of autotuning "
                          "(profiling runs; variant 0 one step per sweep, 2 two steps per sweep)")
+    ap.add_argument("--projection", default="mg", choices=["mg", "cg"],
+                    help="mg: CG preconditioned by a multigrid V-cycle (mode 4, same system and "
+                         "stopping rule); cg: the paper's plain CG from zero (mode 0)")
     ap.add_argument("--cg-config", type=int, default=None,
                     help="z chunk of the CG passes (default: the CG autotuner's choice)")
     ap.add_argument("--cg-tol", type=float, default=1e-8,
@@ -386,10 +410,12 @@ def main():
     ev = lambda: torch.cuda.Event(enable_timing=True)
     stats_last = {}
 
+    proj_mode = 4 if args.projection == "mg" else 0
+
     def one_pass(step_events=None, medium=medium_d, force=force_d, traces=traces_d):
         kv.kv_set_medium(h, *medium)
         kv.kv_reset(h)
-        st = kv.kv_project_force(h, *force, w.tol)
+        st = kv.kv_project_force(h, *force, w.tol, 0, proj_mode)
         stats_last.update(st)
         if step_events is not None:
             step_events[0].record(stream)
@@ -401,6 +427,12 @@ def main():
     for _ in range(args.warmup):
         one_pass()
     torch.cuda.synchronize(device)
+    # both projections once, outside the timed region, for the record (the
+    # paper's plain CG from zero and the multigrid-preconditioned CG)
+    by_mode = {}
+    for name, mode in (("cg", 0), ("mg", 4)):
+        st = kv.kv_project_force(h, *force_d, w.tol, 0, mode)
+        by_mode[name] = {"ms": st["ms"], "iters": st["iters"], "rel_res_true": st["rel_res_true"]}
 
     # ---- timed region: inputs resident on the device ----
     clocks = ClockSampler(local)
@@ -431,15 +463,7 @@ def main():
         / w.n_steps
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "kv_step_traffic.json")
-    if os.path.exists(tfile) and not div:
-        try:
-            tj = json.load(open(tfile))
-            if tj.get("grid") == [w.nx, w.ny, w.nz]:
-                traffic = tj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = step_traffic(w, step_cfg, args.operator, n_force_steps)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -467,7 +491,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, info = cpu_oracle_sample(w, dt, int(np.median(cg_iters)), divform=div)
+        # the oracle runs the paper's plain CG: extrapolate with its iteration count
+        v, info = cpu_oracle_sample(w, dt, by_mode["cg"]["iters"], divform=div)
         cpu = {"value": v, "unit": "Gcell-updates/s", "cores": info["cores"], "kind": "oracle",
                "sample": info["sample"]}
 
@@ -485,10 +510,13 @@ def main():
                                   if args.workload == "inclusions256" else
                                   "bone shell over smooth soft tissue (seed 105), speckled beam"),
                        "operator": args.operator,
+                       "projection": ("CG preconditioned by a multigrid V(1,1)-cycle (mode 4)"
+                                      if proj_mode == 4 else "plain CG from zero (mode 0)"),
                        "reductions": "f64", "parallelism": f"replicas{world}",
                        "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2 (inputs larger than L2)"},
             "kv_step_gcells": step_gcells,
             "projection_ms": float(np.mean(cg_ms)), "cg_iters": int(np.median(cg_iters)),
+            "projection_by_mode": by_mode,
             "step_config": step_cfg, "autotune_ms_per_step": tune_ms,
             "cg_zc": cg_zc, "cg_autotune_ms_40_iters": cg_tune_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

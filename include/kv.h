@@ -165,7 +165,12 @@ kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_fie
  * by the minimal-residual factor alpha = (A phi0).b / |A phi0|^2 (its residual
  * is never larger than the zero start's; the stopping rule is the same);
  * 3 = start from the potential of the previous projection on this handle
- * (zero if there is none); other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
+ * (zero if there is none); 4 = zero start, CG preconditioned by one symmetric
+ * multigrid V(1,1)-cycle (damped Jacobi smoothing, trilinear prolongation,
+ * its transpose as restriction; not in the paper: the same system and the
+ * same stopping rule, far fewer iterations; FP32 handles only, and the first
+ * mode-4 call allocates the level arrays, about 2.3 floats per node);
+ * other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
  * pointer to 3*nx*ny*nz floats (component-major) that receives f_S0.
  * stats: NULL or filled. Returns KV_OK, KV_CG_MAXITER, KV_CG_BREAKDOWN or
  * KV_ERR_NONFINITE (the stats say which). A zero right-hand side gives

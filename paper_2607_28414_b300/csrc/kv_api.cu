@@ -228,7 +228,7 @@ kv_status kv_destroy(kv_handle *h) {
     free_graphs(h);
     void *dev[] = {h->state[0], h->state[1], h->F, h->coef, h->S, h->g_dev, h->sens_dev,
                    h->traces, h->ctrl, h->cgv, h->phi, h->b, h->scal,
-                   h->partials, h->fstage, h->dtmin};
+                   h->partials, h->fstage, h->dtmin, h->mg_pool};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
@@ -466,8 +466,10 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
                            int max_iter, int mode, float *fs_out, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;
     if (h->sticky) return KV_ERR_STATE;
-    if (mode != 0 && mode != 1 && mode != 3)
+    if (mode != 0 && mode != 1 && mode != 3 && mode != 4)
         return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
+    if (mode == 4 && h->precision != KV_FP32)
+        return set_error(h, KV_ERR_UNSUPPORTED, "projection mode 4 (multigrid-preconditioned CG) needs an FP32 handle");
     if (mode == 1 && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
         return set_error(h, KV_ERR_STATE, "mode 1 needs a network attached with kv_attach_net that fits the grid");
     if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");

@@ -35,6 +35,7 @@
 #include <chrono>
 
 #include "kv_internal.cuh"
+#include "kv_reduce.cuh"
 
 namespace kv {
 
@@ -43,67 +44,6 @@ constexpr double kReplace = 1e-2;     // residual replacement after each 100x dr
 
 __device__ __forceinline__ bool is_interior(int i, int j, int k, int nx, int ny, int nz) {
     return i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
-}
-
-// ---------------------------------------------------------------------------
-// Accumulators: float-float for float vectors, double for double vectors.
-// ---------------------------------------------------------------------------
-struct AccFF {
-    float hi = 0.f, lo = 0.f;
-    // acc += x * y with the product and the sum formed exactly (TwoProd by FMA,
-    // TwoSum), then renormalised.
-    __device__ __forceinline__ void add_prod(float x, float y) {
-        const float p = __fmul_rn(x, y);
-        const float pe = __fmaf_rn(x, y, -p);
-        const float s = __fadd_rn(hi, p);
-        const float bb = __fsub_rn(s, hi);
-        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-        const float t = __fadd_rn(__fadd_rn(e, pe), lo);
-        hi = __fadd_rn(s, t);
-        lo = __fsub_rn(t, __fsub_rn(hi, s));
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-struct AccD {
-    double v = 0.0;
-    __device__ __forceinline__ void add_prod(double x, double y) { v = __fma_rn(x, y, v); }
-    __device__ __forceinline__ double value() const { return v; }
-};
-template <typename T> struct AccOf;
-template <> struct AccOf<float> { using type = AccFF; };
-template <> struct AccOf<double> { using type = AccD; };
-
-// Last-block finisher: returns true in the block that finished last; sums[q]
-// then holds the deterministic grand total of partial slot q.
-template <int NQ>
-__device__ __forceinline__ bool last_block_sums(const CgParams &p, const double (&v)[NQ],
-                                                double (&sums)[NQ]) {
-    __shared__ double sh[33];
-    __shared__ int s_last;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const int tid = threadIdx.x;
-    for (int q = 0; q < NQ; ++q) {
-        double t = block_sum_d(v[q], sh);
-        if (tid == 0) p.partials[(size_t)q * p.nblocks + bid] = t;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long t =
-            atomicAdd(reinterpret_cast<unsigned long long *>(&p.ctrl[kCgTicket]), 1ull);
-        s_last = (t == (unsigned long long)(p.nblocks - 1));
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    for (int q = 0; q < NQ; ++q) {
-        double acc = 0.0;
-        for (int b = tid; b < p.nblocks; b += blockDim.x)
-            acc += __ldcg(&p.partials[(size_t)q * p.nblocks + b]);
-        sums[q] = block_sum_d(acc, sh);
-    }
-    if (tid == 0) p.ctrl[kCgTicket] = 0;
-    return true;
 }
 
 // The CG kernels use 1D blocks of kCgBX*kCgBY threads mapped to (x, y) columns.
@@ -191,9 +131,11 @@ k_true_res(const double *__restrict__ b, const double *__restrict__ phi, T *__re
         } else if (p.ctrl[kCgIters] >= p.ctrl[kCgMaxIter]) {
             p.ctrl[kCgStatus] = kCgMaxIterHit;
         } else {
-            const double rr_prev = p.scal[kRR];
-            p.scal[kBeta] = (p.ctrl[kCgIters] == 0 || rr_prev <= 0.0) ? 0.0 : s[1] / rr_prev;
-            p.scal[kRR] = s[1];
+            if (!p.pcg) {  // preconditioned CG: beta and r.z come from the preconditioner pass
+                const double rr_prev = p.scal[kRR];
+                p.scal[kBeta] = (p.ctrl[kCgIters] == 0 || rr_prev <= 0.0) ? 0.0 : s[1] / rr_prev;
+                p.scal[kRR] = s[1];
+            }
             p.scal[kRR0] = s[1];
             p.scal[kRRLast] = s[1];
             p.ctrl[kCgStatus] = kCgRunning;
@@ -323,40 +265,6 @@ static_assert((kCgStageDir * 4) % 128 == 0 && (kCgStageUpd * 4) % 128 == 0, "sta
 constexpr size_t kCgSmemDir = kCgNS * kCgStageDir * 4 + kCgNS * 8;
 constexpr size_t kCgSmemUpd = kCgNS * kCgStageUpd * 4 + kCgNS * 8;
 
-__device__ __forceinline__ void ff_add(float &hi, float &lo, float bh, float bl) {
-    const float s = __fadd_rn(hi, bh);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-    const float t = __fadd_rn(__fadd_rn(e, lo), bl);
-    hi = __fadd_rn(s, t);
-    lo = __fsub_rn(t, __fsub_rn(hi, s));
-}
-
-// Block total of a float-float accumulator, as a double in thread 0.
-__device__ __forceinline__ double block_total_ff(AccFF a) {
-    __shared__ float sh_hi[32], sh_lo[32];
-    float hi = a.hi, lo = a.lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        ff_add(hi, lo, h2, l2);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) {
-        sh_hi[warp] = hi;
-        sh_lo[warp] = lo;
-    }
-    __syncthreads();
-    double tot = 0.0;
-    if (threadIdx.x == 0) {
-        float th = 0.f, tl = 0.f;
-        for (int w = 0; w < nw; ++w) ff_add(th, tl, sh_hi[w], sh_lo[w]);
-        tot = (double)th + (double)tl;
-    }
-    return tot;
-}
-
 // Per-block partial (thread 0's value) -> last block sums all partials.
 __device__ __forceinline__ bool finish_blocks(const CgParams &p, double tot, double &sum) {
     __shared__ double sh[33];
@@ -399,7 +307,7 @@ __device__ __forceinline__ void upd_finish(const CgParams &p, double rr) {
     } else if (rr <= 0.25 * tol * tol * bb || rr <= repl * repl * p.scal[kRR0] ||
                it >= p.ctrl[kCgMaxIter]) {
         p.ctrl[kCgStatus] = kCgNeedTrue;
-    } else {
+    } else if (!p.pcg) {  // preconditioned CG: the preconditioner pass sets beta and r.z
         p.scal[kBeta] = rr / p.scal[kRR];
         p.scal[kRR] = rr;
     }
@@ -522,13 +430,13 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
 
 __global__ void __launch_bounds__(kCgNT)
 k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ CUtensorMap tm_c1,
-             float *__restrict__ cgv, CgParams p) {
+             const __grid_constant__ CUtensorMap tm_r, float *__restrict__ cgv, CgParams p) {
     if (__ldcg(&p.ctrl[kCgStatus]) != kCgRunning) return;
     const int par = (int)(__ldcg(&p.ctrl[kCgIters]) & 1);
     const int pf = par ? 0 : 2;                      // field of p' (written by k_cg_dir_tma)
     const float alpha = (float)__ldcg(&p.scal[kAlpha]);
     const float inv = (float)p.inv_dx2;
-    float *__restrict__ rg = cgv + p.Np;
+    float *__restrict__ rg = p.rbuf;
     float *__restrict__ eg = cgv + 3 * p.Np;
     extern __shared__ __align__(128) float smem[];
     const uint32_t bar0 = smem_u32(smem + kCgNS * kCgStageUpd);
@@ -545,7 +453,7 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
         mbar_expect_tx(bar, (kCgHalo + (centre ? 2 * kCgCtr : 0)) * 4);
         tma_load_4d(smem_u32(st), &tm_h1, t.x0 - 4, t.y0 - 1, q, pf, bar);
         if (centre) {
-            tma_load_4d(smem_u32(st + kCgHaloPad), &tm_c1, t.x0, t.y0, q, 1, bar);
+            tma_load_4d(smem_u32(st + kCgHaloPad), &tm_r, t.x0, t.y0, q, p.rfield, bar);
             tma_load_4d(smem_u32(st + kCgHaloPad + kCgCtr), &tm_c1, t.x0, t.y0, q, 3, bar);
         }
     };
@@ -713,6 +621,9 @@ kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny,
 // ---------------------------------------------------------------------------
 static CgParams cg_params(kv_handle *h, dim3 grid, int zc) {
     CgParams p;
+    p.pcg = 0;
+    p.rbuf = (float *)h->cgv + h->Np;  // r in field 1 of the CG vectors
+    p.rfield = 1;
     p.nx = h->nx;
     p.ny = h->ny;
     p.nz = h->nz;
@@ -831,6 +742,18 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     const dim3 tgrid((h->px + kCgTX - 1) / kCgTX, (h->ny - 2 + kCgTY - 1) / kCgTY,
                      (h->nz - 2 + tzc - 1) / tzc);
     CgParams pt = cg_params(h, tgrid, tzc);
+    // mode 4: CG preconditioned by the multigrid V-cycle (kv_mg.cu); r lives
+    // in the preconditioner's fine array, z takes r's slot of the CG vectors
+    const bool pcg = (mode == 4);
+    if (pcg) {
+        if (!use_tma) return set_error(h, KV_ERR_UNSUPPORTED, "projection mode 4 needs an FP32 handle");
+        kv_status ms = mg_prepare(h);
+        if (ms != KV_OK) return ms;
+        p.pcg = pt.pcg = 1;
+        pt.rbuf = h->mg[0].r;
+        pt.rfield = 0;
+    }
+    T *rvec = pcg ? (T *)h->mg[0].r : (T *)h->r;
     if (use_tma) {
         kv_status ts = cg_tma_prepare(h);
         if (ts != KV_OK) return ts;
@@ -857,7 +780,9 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     ci[kCgMaxIter] = max_iter;
     for (int q = 0; q < kCgScalars; ++q) si[q] = 0.0;
     si[kTol] = tol;
-    si[kInner] = (h->precision == KV_FP64) ? 0.0 : kReplace;
+    // preconditioned CG drops the residual by 100x in two or three iterations:
+    // replace it after every 1000x drop instead
+    si[kInner] = (h->precision == KV_FP64) ? 0.0 : (mode == 4 ? kReplace * 0.1 : kReplace);
     e = cudaMemcpyAsync(h->ctrl, ci, kCtrlWords * sizeof(long long), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->scal, si, kCgScalars * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -896,19 +821,21 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     if (!isfinite(bb)) {
         status = KV_ERR_NONFINITE;
     } else if (bb > 0.0) {
-        const int chunk = 32;
+        const int chunk = pcg ? 4 : 32;  // iterations queued between polls of the control word
         while (true) {
             const long long c = h->ctrl_host[kCgStatus];
             if (c == kCgNeedTrue) {
                 k_fold_e<T><<<fold_blocks, 256, 0, s>>>(h->phi, (T *)h->e, h->Np, p);
-                k_true_res<T><<<grid, nt, 0, s>>>(h->b, h->phi, (T *)h->r, p);
+                k_true_res<T><<<grid, nt, 0, s>>>(h->b, h->phi, rvec, p);
                 h->launches += 2;
             } else if (c == kCgRunning) {
                 T *p0 = (T *)h->p[0], *p1 = (T *)h->p[1];
                 for (int it = 0; it < chunk; ++it) {
                     if (use_tma) {
+                        if (pcg) mg_apply(h, pt);
                         k_cg_dir_tma<<<tgrid, kCgNT, kCgSmemDir, s>>>(h->tm_cg_h2, (float *)h->cgv, pt);
                         k_cg_upd_tma<<<tgrid, kCgNT, kCgSmemUpd, s>>>(h->tm_cg_h1, h->tm_cg_c1,
+                                                                      pcg ? h->tm_mg_r : h->tm_cg_c1,
                                                                       (float *)h->cgv, pt);
                     } else {
                         k_cg_dir<T><<<grid, nt, 0, s>>>((const T *)h->r, p0, p1, p);

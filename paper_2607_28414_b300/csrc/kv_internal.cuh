@@ -99,6 +99,20 @@ struct CgParams {
     double *partials;    // one double per block (or two)
     int zc;
     int nblocks;
+    int pcg;             // 1: preconditioned CG (z in the CG vector slot of r, r in rbuf)
+    float *rbuf;         // residual of the TMA update pass (FP32)
+    int rfield;          // field of rbuf's tensor map holding r
+};
+
+// One level of the multigrid preconditioner: nx, ny, nz interior cells, arrays
+// of (nx + 2) x (ny + 2) x (nz + 2) with a zero ghost layer and row pitch px
+// (level 0 is the handle's pitched grid).
+constexpr int kMgMaxLevels = 12;
+struct MgLevel {
+    int nx, ny, nz, px;
+    long long n;         // elements of one array (px * (ny + 2) * (nz + 2))
+    double h2;           // grid spacing squared
+    float *r, *e, *t;    // right-hand side, solution, residual after pre-smoothing
 };
 
 }  // namespace kv
@@ -146,6 +160,12 @@ struct kv_handle {
     CUtensorMap tm_cg_h2, tm_cg_h1, tm_cg_c1;  // TMA views of cgv (FP32)
     int cg_tma_ready;
     int cg_zc;             // planes per block of the TMA CG passes (0: default)
+
+    // multigrid preconditioner (projection mode 4), allocated on first use
+    int mg_levels;
+    kv::MgLevel mg[kv::kMgMaxLevels];
+    float *mg_pool;        // all level arrays in one allocation
+    CUtensorMap tm_mg_r;   // TMA view of the fine residual (mg[0].r)
     double *phi;           // [Np]
     double *b;             // [Np] right-hand side
     double *scal;          // kv::kCgScalars
@@ -214,6 +234,11 @@ kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields
 
 // Projection kernels (kv_cg.cu)
 kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_out, kv_cg_stats *st);
+
+// Multigrid preconditioner (kv_mg.cu): level setup and one application
+// z = M r from mg[0].r into cgv field 1, with r.z reduced into scal[kRR].
+kv_status mg_prepare(kv_handle *h);
+void mg_apply(kv_handle *h, const CgParams &p);
 
 // Device stability limit over dense fields: kDtBlocks block minima in
 // `scratch` (kDtBlocks doubles; NULL = a temporary allocation), synchronising.

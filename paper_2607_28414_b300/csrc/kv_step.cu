@@ -128,10 +128,11 @@ k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict_
 // plane of all six state fields, with a 4-node x halo (keeps the TMA x start
 // 16-byte aligned) and a 1-node y halo, arrives in one 4D TMA box
 // (TX+8, TY+2, 1, 6) into a ring of NS shared-memory stages; the coefficient
-// (A', B') tile of the centre plane rides in the same stage. Planes k-1, k, k+1
-// are resident while plane k is computed and NS-3 further planes are in flight.
+// (A', B') tile of the centre plane rides in the same stage. Planes k and k+1
+// are resident while plane k is computed (the z-1 neighbours are plane k-1's
+// centre values, kept in registers) and NS-2 further planes are in flight.
 // The projected force (needed only on the few force steps) is read directly
-// from global memory as float4. Each thread computes four
+// from global memory as float4, one plane ahead. Each thread computes four
 // consecutive x nodes (one float4) of one row; its x neighbours come from warp
 // shuffles (row edges from shared memory). Outputs go straight to global
 // memory as float4 stores.
@@ -159,14 +160,14 @@ struct Nb7 {
 };
 
 template <int BX, int GX>
-__device__ __forceinline__ Nb7 gather7(const float *sc, const float *sm, const float *sp, int off,
+__device__ __forceinline__ Nb7 gather7(const float *sc, const float4 &zm, const float *sp, int off,
                                        int gx) {
     Nb7 n;
     const float *fc = sc + off;
     n.c = *reinterpret_cast<const float4 *>(fc);
     n.ym = *reinterpret_cast<const float4 *>(fc - BX);
     n.yp = *reinterpret_cast<const float4 *>(fc + BX);
-    n.zm = *reinterpret_cast<const float4 *>(sm + off);
+    n.zm = zm;
     n.zp = *reinterpret_cast<const float4 *>(sp + off);
     float left = __shfl_up_sync(0xffffffffu, n.c.w, 1);
     float right = __shfl_down_sync(0xffffffffu, n.c.x, 1);
@@ -251,21 +252,52 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
     const long long sy = p.px, sz = (long long)p.px * p.ny;
     const unsigned FULL = 0xffffffffu;
 
+    // Register-blocked z march: the z-1 neighbours are the previous plane's
+    // centre values, kept in registers, so a stage is free as soon as its
+    // plane has been computed and NS-2 planes are in flight.
+    float4 prev[6], prevc[2];
+    ok &= mbar_wait_bounded(bar0, 0);  // plane kb, slot 0, first phase
+#pragma unroll
+    for (int f = 0; f < 6; ++f) prev[f] = *reinterpret_cast<const float4 *>(smem + f * TT::FIELD + o);
+    if (K == kKindDiv) {
+        prevc[0] = *reinterpret_cast<const float4 *>(smem + TT::STATE + o);
+        prevc[1] = *reinterpret_cast<const float4 *>(smem + TT::STATE + TT::FIELD + o);
+    }
+    __syncthreads();  // every thread has read plane kb: its slot is free
+    if (tid == 0 && kb + NS <= k1) {
+        fence_proxy_async();
+        issue(kb + NS);
+    }
+    ok &= mbar_wait_bounded(bar0 + 8 * ((k0 - kb) % NS), ((k0 - kb) / NS) & 1);
+
+    // Force steps: the projected force of the next plane is loaded one plane
+    // ahead, so its latency overlaps the current plane's work.
+    float4 Fn[3];
+    auto load_force = [&](int kk) {
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp)
+            Fn[comp] = (force && row_ok)
+                           ? __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + kk * sz + y * sy + x))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    if (force) load_force(k0);
+
     for (int k = k0; k < k1; ++k) {
-        if (k == k0) {
-            ok &= mbar_wait_bounded(bar0 + 8 * ((kb - kb) % NS), ((kb - kb) / NS) & 1);
-            ok &= mbar_wait_bounded(bar0 + 8 * ((k0 - kb) % NS), ((k0 - kb) / NS) & 1);
-        }
+        float4 Fc[3];
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) Fc[comp] = force ? Fn[comp] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (force && k + 1 < k1) load_force(k + 1);
         ok &= mbar_wait_bounded(bar0 + 8 * ((k + 1 - kb) % NS), ((k + 1 - kb) / NS) & 1);
 
         const float *sc = smem + ((k - kb) % NS) * TT::STAGE;
-        const float *sm = smem + ((k - 1 - kb) % NS) * TT::STAGE;
         const float *sp = smem + ((k + 1 - kb) % NS) * TT::STAGE;
 
         if constexpr (K == kKindDiv) {
             // face weights of the four nodes, shared by the three components
-            const Nb7 mn = gather7<TT::BX, TT::GX>(sc, sm, sp, TT::STATE + o, gx);
-            const Nb7 en = gather7<TT::BX, TT::GX>(sc, sm, sp, TT::STATE + TT::FIELD + o, gx);
+            const Nb7 mn = gather7<TT::BX, TT::GX>(sc, prevc[0], sp, TT::STATE + o, gx);
+            const Nb7 en = gather7<TT::BX, TT::GX>(sc, prevc[1], sp, TT::STATE + TT::FIELD + o, gx);
+            prevc[0] = mn.c;
+            prevc[1] = en.c;
             const float4 r4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + 2 * TT::FIELD + o);
             float wm[4][6], we[4][6];
 #pragma unroll
@@ -283,11 +315,12 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
             const long long gbase = k * sz + y * sy + x;
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
-                const Nb7 un = gather7<TT::BX, TT::GX>(sc, sm, sp, comp * TT::FIELD + o, gx);
-                const Nb7 dnb = gather7<TT::BX, TT::GX>(sc, sm, sp, (3 + comp) * TT::FIELD + o, gx);
+                const Nb7 un = gather7<TT::BX, TT::GX>(sc, prev[comp], sp, comp * TT::FIELD + o, gx);
+                const Nb7 dnb = gather7<TT::BX, TT::GX>(sc, prev[3 + comp], sp, (3 + comp) * TT::FIELD + o, gx);
+                prev[comp] = un.c;
+                prev[3 + comp] = dnb.c;
                 if (row_ok) {
-                    float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (force) F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
+                    const float4 F4 = Fc[comp];
                     float4 uo, dn;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -312,7 +345,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
                 const float4 c = *reinterpret_cast<const float4 *>(fc);
                 const float4 ym = *reinterpret_cast<const float4 *>(fc - TT::BX);
                 const float4 yp = *reinterpret_cast<const float4 *>(fc + TT::BX);
-                const float4 zm = *reinterpret_cast<const float4 *>(sm + f * TT::FIELD + o);
+                const float4 zm = prev[f];
                 const float4 zp = *reinterpret_cast<const float4 *>(sp + f * TT::FIELD + o);
                 float left = __shfl_up_sync(FULL, c.w, 1);
                 float right = __shfl_down_sync(FULL, c.x, 1);
@@ -325,6 +358,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
                 s.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
                 ctr[f] = c;
                 sum[f] = s;
+                prev[f] = c;
             }
             float4 A4, B4;
             if (K == kKindPoint) {
@@ -342,9 +376,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
                 const bool m3 = (x + 3 <= p.nx - 2);
     #pragma unroll
                 for (int comp = 0; comp < 3; ++comp) {
-                    float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (force)  // force steps are few: the projected force is read directly
-                        F4 = __ldg(reinterpret_cast<const float4 *>(F + comp * p.Np + gbase));
+                    const float4 F4 = Fc[comp];
                     const float4 u = ctr[comp], su = sum[comp], d = ctr[3 + comp], sd = sum[3 + comp];
                     float4 uo, dn;
                     kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g, F4.x, uo.x, dn.x);
@@ -360,9 +392,9 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
                 }
             }
         }
-        __syncthreads();  // every thread is done with plane k-1's stage
+        __syncthreads();  // every thread is done with plane k's stage
         if (tid == 0) {
-            const int q = k - 1 + NS;
+            const int q = k + NS;
             if (q <= k1) {
                 fence_proxy_async();
                 issue(q);
