@@ -170,7 +170,8 @@ kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_fie
  * its transpose as restriction; not in the paper: the same system and the
  * same stopping rule, far fewer iterations; FP32 handles only, and the first
  * mode-4 call allocates the level arrays, about 2.3 floats per node);
- * other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
+ * 5 = the learned initial guess of mode 1, then the preconditioned CG of
+ * mode 4; other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
  * pointer to 3*nx*ny*nz floats (component-major) that receives f_S0.
  * stats: NULL or filled. Returns KV_OK, KV_CG_MAXITER, KV_CG_BREAKDOWN or
  * KV_ERR_NONFINITE (the stats say which). A zero right-hand side gives
@@ -272,9 +273,11 @@ kv_status kv_step(kv_handle *h, int n);
  * General per-step projection (Sec. 3.2: a different body force at each time
  * step, each projected on its own): project this step's force f^n (fields as
  * in kv_project_force; mode 0: the CG starts from zero, as the paper's general
- * solver; mode 3: from the previous step's potential; both stop on tol), then
- * advance one step with f_S^n (envelope 1 for this step). The projected force stays stored afterwards. stats: NULL or the
- * projection's statistics. Synchronising.
+ * solver; mode 3: from the previous step's potential; mode 4: from zero,
+ * preconditioned by the multigrid V-cycle (FP32 only); all stop on tol), then
+ * advance one step with f_S^n (envelope 1 for this step). The projected force
+ * stays stored afterwards. stats: NULL or the projection's statistics.
+ * Synchronising.
  */
 kv_status kv_step_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, double tol, int max_iter,
                         int mode, kv_cg_stats *stats);

@@ -82,7 +82,7 @@ kv_status stable_dt_impl(kv_handle *h, int nx, int ny, int nz, double dx, const 
     const long long n = (long long)nx * ny * nz;
     double m;
     if (n_dev) {
-        kv_status st = stable_dt_device(h ? h->stream : 0, h ? h->dtmin : nullptr, nx, ny, nz, dx,
+        kv_status st = stable_dt_device(h ? h->stream : 0, h ? h->dtmin : nullptr, nx, ny, nz, nx, dx,
                                         G.where == KV_DEVICE ? G.data : nullptr, G.value,
                                         rho.where == KV_DEVICE ? rho.data : nullptr, rho.value,
                                         eta.where == KV_DEVICE ? eta.data : nullptr, eta.value, op, &m);
@@ -169,9 +169,24 @@ kv_status fold(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_fi
         h->S_s = h->dt * h->dt / rho.value;
         return KV_OK;
     }
+    // the fields were staged (pitched) into fstage by stage_medium
+    const kv_field *fs[3] = {&G, &rho, &eta};
+    const float *ptr[3];
+    for (int q = 0; q < 3; ++q) ptr[q] = fs[q]->where != KV_SCALAR ? h->fstage + q * h->Np : nullptr;
+    kv_status st = launch_fold(h, ptr[0], G.value, ptr[1], rho.value, ptr[2], eta.value);
+    if (st != KV_OK) return st;
+    return cuda_check(h, cudaStreamSynchronize(h->stream), "medium fold");
+}
+
+// Copy the medium's dense fields (host or device) into the handle's pitched
+// staging planes and evaluate the stability limit of operator op there, on
+// the device (a handle never loops over a host field on the CPU).
+kv_status stage_medium(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_field &eta, int op,
+                       double *dt_max) {
     const kv_field *fs[3] = {&G, &rho, &eta};
     const float *ptr[3];
     for (int q = 0; q < 3; ++q) {
+        if (!field_ok(*fs[q])) return set_error(h, KV_ERR_ARG, "invalid medium field");
         ptr[q] = nullptr;
         if (fs[q]->where != KV_SCALAR) {
             kv_status st = stage(h, *fs[q], h->fstage + q * h->Np);
@@ -179,9 +194,17 @@ kv_status fold(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_fi
             ptr[q] = h->fstage + q * h->Np;
         }
     }
-    kv_status st = launch_fold(h, ptr[0], G.value, ptr[1], rho.value, ptr[2], eta.value);
-    if (st != KV_OK) return st;
-    return cuda_check(h, cudaStreamSynchronize(h->stream), "medium fold");
+    double m;
+    if (!ptr[0] && !ptr[1] && !ptr[2]) {
+        m = dt_limit_node(G.value, rho.value, eta.value, h->dx);
+    } else {
+        kv_status st = stable_dt_device(h->stream, h->dtmin, h->nx, h->ny, h->nz, h->px, h->dx, ptr[0], G.value,
+                                        ptr[1], rho.value, ptr[2], eta.value, op, &m);
+        if (st != KV_OK) return set_error(h, st, "device stability reduction failed");
+    }
+    if (m < 0.0) return set_error(h, KV_ERR_ARG, "medium has rho <= 0, G < 0, eta < 0 or non-finite values");
+    *dt_max = m;
+    return KV_OK;
 }
 
 }  // namespace
@@ -249,12 +272,26 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     const long long px = round_up(nx, kPitchAlign);
     if (px * ny * (long long)nz > (1ll << 31) - 1)
         return set_error(nullptr, KV_ERR_ARG, "kv_create: grid too large (more than 2^31 padded nodes)");
-    double dt_max;
-    kv_status st = stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, KV_OP_POINTWISE, &dt_max);
-    if (st != KV_OK) return st;
-    if (dt > dt_max * (1.0 + 1e-12))
-        return set_error(nullptr, KV_ERR_UNSTABLE_DT,
-                         "dt = %.6e s exceeds the stability limit %.6e s", dt, dt_max);
+    double dt_max = INFINITY;
+    kv_status st;
+    {
+        const kv_field *fs[3] = {&G, &rho, &eta};
+        int n_host = 0, n_dev = 0;
+        for (auto *f : fs) {
+            if (!field_ok(*f)) return set_error(nullptr, KV_ERR_ARG, "invalid medium field");
+            n_host += f->where == KV_HOST;
+            n_dev += f->where == KV_DEVICE;
+        }
+        if (n_host && n_dev)
+            return set_error(nullptr, KV_ERR_ARG, "medium arrays must all be on the host or all on the device");
+        if (!n_host && !n_dev) {  // scalars: check before allocating anything
+            if ((st = stable_dt_impl(nullptr, nx, ny, nz, dx, G, rho, eta, KV_OP_POINTWISE, &dt_max)) != KV_OK)
+                return st;
+            if (dt > dt_max * (1.0 + 1e-12))
+                return set_error(nullptr, KV_ERR_UNSTABLE_DT,
+                                 "dt = %.6e s exceeds the stability limit %.6e s", dt, dt_max);
+        }
+    }
 
     kv_handle *h = (kv_handle *)calloc(1, sizeof(kv_handle));
     if (!h) return set_error(nullptr, KV_ERR_OOM, "kv_create: host allocation failed");
@@ -318,6 +355,11 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
         if (e == cudaSuccess && h->het) e = cudaMemsetAsync(h->S, 0, Np * es, h->stream);
         if ((st = cuda_check(h, e, "initial memset")) != KV_OK) goto fail;
     }
+    if ((st = stage_medium(h, G, rho, eta, KV_OP_POINTWISE, &h->dt_max)) != KV_OK) goto fail;
+    if (dt > h->dt_max * (1.0 + 1e-12)) {
+        st = set_error(h, KV_ERR_UNSTABLE_DT, "dt = %.6e s exceeds the stability limit %.6e s", dt, h->dt_max);
+        goto fail;
+    }
     if ((st = fold(h, G, rho, eta)) != KV_OK) goto fail;
     if ((st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_create")) != KV_OK) goto fail;
     *out = h;
@@ -337,7 +379,7 @@ kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta) {
     double dt_max;
     kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_medium");
     if (st != KV_OK) return st;
-    if ((st = stable_dt_impl(h, h->nx, h->ny, h->nz, h->dx, G, rho, eta, h->op, &dt_max)) != KV_OK) return st;
+    if ((st = stage_medium(h, G, rho, eta, h->op, &dt_max)) != KV_OK) return st;
     if (h->dt > dt_max * (1.0 + 1e-12))
         return set_error(h, KV_ERR_UNSTABLE_DT, "dt = %.6e s exceeds the stability limit %.6e s", h->dt,
                          dt_max);
@@ -359,7 +401,7 @@ kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_fie
     double dt_max;
     kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_operator");
     if (st != KV_OK) return st;
-    if ((st = stable_dt_impl(h, h->nx, h->ny, h->nz, h->dx, G, rho, eta, op, &dt_max)) != KV_OK) return st;
+    if ((st = stage_medium(h, G, rho, eta, op, &dt_max)) != KV_OK) return st;
     if (h->dt > dt_max * (1.0 + 1e-12))
         return set_error(h, KV_ERR_UNSTABLE_DT, "dt = %.6e s exceeds the stability limit %.6e s of operator %d",
                          h->dt, dt_max, op);
@@ -466,12 +508,12 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
                            int max_iter, int mode, float *fs_out, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;
     if (h->sticky) return KV_ERR_STATE;
-    if (mode != 0 && mode != 1 && mode != 3 && mode != 4)
+    if (mode != 0 && mode != 1 && mode != 3 && mode != 4 && mode != 5)
         return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
-    if (mode == 4 && h->precision != KV_FP32)
-        return set_error(h, KV_ERR_UNSUPPORTED, "projection mode 4 (multigrid-preconditioned CG) needs an FP32 handle");
-    if (mode == 1 && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
-        return set_error(h, KV_ERR_STATE, "mode 1 needs a network attached with kv_attach_net that fits the grid");
+    if ((mode == 4 || mode == 5) && h->precision != KV_FP32)
+        return set_error(h, KV_ERR_UNSUPPORTED, "projection modes 4 and 5 (multigrid-preconditioned CG) need an FP32 handle");
+    if ((mode == 1 || mode == 5) && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
+        return set_error(h, KV_ERR_STATE, "modes 1 and 5 need a network attached with kv_attach_net that fits the grid");
     if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");
     const kv_field *f[3] = {&fx, &fy, &fz};
     for (auto *q : f)
@@ -545,7 +587,10 @@ kv_status kv_step_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, dou
                         int mode, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;
     if (h->sticky) return KV_ERR_STATE;
-    if (mode != 0 && mode != 3) return set_error(h, KV_ERR_ARG, "kv_step_force: mode must be 0 or 3");
+    if (mode != 0 && mode != 3 && mode != 4)
+        return set_error(h, KV_ERR_ARG, "kv_step_force: mode must be 0, 3 or 4");
+    if (mode == 4 && h->precision != KV_FP32)
+        return set_error(h, KV_ERR_UNSUPPORTED, "kv_step_force: mode 4 needs an FP32 handle");
     if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");
     const kv_field *f[3] = {&fx, &fy, &fz};
     for (auto *q : f)

@@ -551,44 +551,68 @@ k_grad(const float *__restrict__ f, const double *__restrict__ phi, const T *__r
 }
 
 // Per-node stability limit dt <= h^2 / (nu + sqrt(nu^2 + c^2 h^2)), h^2 = dx^2/3
-// (the positive root of dt^2 c^2 + 2 dt nu = h^2), block minima. Dense
-// nx*ny*nz fields. op = KV_OP_DIVERGENCE: at interior nodes c^2 and nu use the
+// (the positive root of dt^2 c^2 + 2 dt nu = h^2), block minima. Fields of
+// nx*ny*nz nodes in rows of pitch px (px = nx: dense). op = KV_OP_DIVERGENCE: at interior nodes c^2 and nu use the
 // mean face modulus (6 G_i + sum of the neighbours' G) / 12 (Gershgorin bound
 // of the flux operator); boundary nodes are only validated.
-__global__ void k_dtmin(int nx, int ny, int nz, double dx, const float *G, double Gs,
+template <typename T>
+__device__ __forceinline__ T dt_node_limit(long long q, int nx, int ny, int nz, int px, T h2, const float *G,
+                                           double Gs, const float *rho, double rhos, const float *eta, double etas,
+                                           int op) {
+    // node q of the dense enumeration, at element c of rows of pitch px
+    const long long c = (q / nx) * px + q % nx;
+    const long long sy = px, sz = (long long)px * ny;
+    T g = G ? T(G[c]) : T(Gs);
+    const T r = rho ? T(rho[c]) : T(rhos);
+    T e = eta ? T(eta[c]) : T(etas);
+    if (!(r > T(0)) || g < T(0) || e < T(0) || !isfinite(g) || !isfinite(r) || !isfinite(e))
+        return T(-1);  // invalid medium
+    if (op == KV_OP_DIVERGENCE) {
+        const int i = (int)(q % nx), j = (int)((q / nx) % ny), k = (int)(q / ((long long)nx * ny));
+        if (!(i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2)) return T(INFINITY);
+        const long long nb[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
+        T gs = T(6) * g, es = T(6) * e;
+        for (int f = 0; f < 6; ++f) {
+            gs += G ? T(G[nb[f]]) : T(Gs);
+            es += eta ? T(eta[nb[f]]) : T(etas);
+        }
+        g = gs / T(12);
+        e = es / T(12);
+    }
+    const T c2 = g / r, nu = e / r;
+    const T den = nu + sqrt(nu * nu + c2 * h2);
+    return den > T(0) ? h2 / den : T(INFINITY);
+}
+
+// Block minima of the limit. The FP64 formula is evaluated only where a
+// single-precision estimate (relative error ~1e-6) comes within 1e-3 of the
+// block's smallest estimate, so the result is the exact FP64 minimum while
+// almost every node costs FP32 arithmetic only (B300's FP64 rate is a small
+// fraction of its FP32 rate).
+__global__ void k_dtmin(int nx, int ny, int nz, int px, double dx, const float *G, double Gs,
                         const float *rho, double rhos, const float *eta, double etas, int op,
                         double *out) {
     __shared__ double sh[256];
-    double m = INFINITY;
-    const double h2 = dx * dx / 3.0;
+    __shared__ float shf[256];
     const long long n = (long long)nx * ny * nz;
-    const long long sy = nx, sz = (long long)nx * ny;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-         c += (long long)gridDim.x * blockDim.x) {
-        double g = G ? (double)G[c] : Gs;
-        const double r = rho ? (double)rho[c] : rhos;
-        double e = eta ? (double)eta[c] : etas;
-        const bool bad = !(r > 0.0) || g < 0.0 || e < 0.0 || !isfinite(g) || !isfinite(r) || !isfinite(e);
-        bool use = true;
-        if (op == KV_OP_DIVERGENCE) {
-            const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / sz);
-            use = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
-            if (use) {
-                const long long nb[6] = {c - 1, c + 1, c - sy, c + sy, c - sz, c + sz};
-                double gs = 6.0 * g, es = 6.0 * e;
-                for (int f = 0; f < 6; ++f) {
-                    gs += G ? (double)G[nb[f]] : Gs;
-                    es += eta ? (double)eta[nb[f]] : etas;
-                }
-                g = gs / 12.0;
-                e = es / 12.0;
-            }
-        }
-        const double c2 = g / r, nu = e / r;
-        const double den = nu + sqrt(nu * nu + c2 * h2);
-        double v = (use && den > 0.0) ? h2 / den : INFINITY;
-        if (bad) v = -1.0;  // invalid medium
-        m = fmin(m, v);
+    const long long q0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, dq = (long long)gridDim.x * blockDim.x;
+    float mf = INFINITY;
+    for (long long q = q0; q < n; q += dq)
+        mf = fminf(mf, dt_node_limit<float>(q, nx, ny, nz, px, (float)(dx * dx / 3.0), G, Gs, rho, rhos, eta,
+                                            etas, op));
+    shf[threadIdx.x] = mf;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) shf[threadIdx.x] = fminf(shf[threadIdx.x], shf[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const float cut = shf[0] < 0.f ? 0.f : shf[0] * 1.001f;
+    double m = INFINITY;
+    for (long long q = q0; q < n; q += dq) {
+        const float v32 = dt_node_limit<float>(q, nx, ny, nz, px, (float)(dx * dx / 3.0), G, Gs, rho, rhos,
+                                               eta, etas, op);
+        if (v32 <= cut)
+            m = fmin(m, dt_node_limit<double>(q, nx, ny, nz, px, dx * dx / 3.0, G, Gs, rho, rhos, eta, etas, op));
     }
     sh[threadIdx.x] = m;
     __syncthreads();
@@ -599,12 +623,12 @@ __global__ void k_dtmin(int nx, int ny, int nz, double dx, const float *G, doubl
     if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
-kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny, int nz, double dx,
+kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny, int nz, int px, double dx,
                            const float *G, double Gs, const float *rho, double rhos, const float *eta,
                            double etas, int op, double *out) {
     double *d = scratch;
     if (!d && cudaMalloc(&d, kDtBlocks * sizeof(double)) != cudaSuccess) return KV_ERR_OOM;
-    k_dtmin<<<kDtBlocks, 256, 0, stream>>>(nx, ny, nz, dx, G, Gs, rho, rhos, eta, etas, op, d);
+    k_dtmin<<<kDtBlocks, 256, 0, stream>>>(nx, ny, nz, px, dx, G, Gs, rho, rhos, eta, etas, op, d);
     double hbuf[kDtBlocks];
     cudaError_t e = cudaMemcpyAsync(hbuf, d, sizeof(hbuf), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -744,7 +768,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     CgParams pt = cg_params(h, tgrid, tzc);
     // mode 4: CG preconditioned by the multigrid V-cycle (kv_mg.cu); r lives
     // in the preconditioner's fine array, z takes r's slot of the CG vectors
-    const bool pcg = (mode == 4);
+    const bool pcg = (mode == 4 || mode == 5);
     if (pcg) {
         if (!use_tma) return set_error(h, KV_ERR_UNSUPPORTED, "projection mode 4 needs an FP32 handle");
         kv_status ms = mg_prepare(h);
@@ -782,7 +806,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     si[kTol] = tol;
     // preconditioned CG drops the residual by 100x in two or three iterations:
     // replace it after every 1000x drop instead
-    si[kInner] = (h->precision == KV_FP64) ? 0.0 : (mode == 4 ? kReplace * 0.1 : kReplace);
+    si[kInner] = (h->precision == KV_FP64) ? 0.0 : (pcg ? kReplace * 0.1 : kReplace);
     e = cudaMemcpyAsync(h->ctrl, ci, kCtrlWords * sizeof(long long), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->scal, si, kCgScalars * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -795,7 +819,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     const double bb = h->scal_host[kBB];
     int status = KV_OK;
     const int fold_blocks = 148 * 8;
-    if (mode == 1 && isfinite(bb) && bb > 0.0) {
+    if ((mode == 1 || mode == 5) && isfinite(bb) && bb > 0.0) {  // learned initial guess
         // learned warm start: phi_0 = Net(b) on interior nodes; the CG below
         // starts from it and stops on the same true residual as from zero
         k_pitched_to_dense<<<fold_blocks, 256, 0, s>>>(h->b, kv_net_stage_b(h->net), h->nx, h->ny, h->nz, h->px);

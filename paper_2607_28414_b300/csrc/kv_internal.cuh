@@ -243,7 +243,7 @@ void mg_apply(kv_handle *h, const CgParams &p);
 // Device stability limit over dense fields: kDtBlocks block minima in
 // `scratch` (kDtBlocks doubles; NULL = a temporary allocation), synchronising.
 constexpr int kDtBlocks = 592;
-kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny, int nz, double dx,
+kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny, int nz, int px, double dx,
                            const float *G, double Gs, const float *rho, double rhos, const float *eta,
                            double etas, int op, double *out);
 

@@ -729,15 +729,16 @@ __global__ void k_fold(const float *__restrict__ G, const float *__restrict__ rh
     const double r = rho ? (double)rho[c] : rhos;
     const double e = eta ? (double)eta[c] : etas;
     const double inv = 1.0 / (dx * dx);
+    const double rr = 1.0 / r;  // one FP64 division per node
     if (div) {
         coef[c] = T(dt * dt * g * inv);
         coef[Np + c] = T(dt * e * inv);
-        coef[2 * Np + c] = T(1.0 / r);
+        coef[2 * Np + c] = T(rr);
     } else {
-        coef[c] = T(dt * dt * g / r * inv);
-        coef[Np + c] = T(dt * e / r * inv);
+        coef[c] = T(dt * dt * inv * g * rr);
+        coef[Np + c] = T(dt * inv * e * rr);
     }
-    S[c] = T(dt * dt / r);
+    S[c] = T(dt * dt * rr);
 }
 
 template <typename T>

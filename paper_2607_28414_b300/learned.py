@@ -3,8 +3,9 @@
 Training pairs (b, phi) come from the library's own projection (CG to a true
 residual of 1e-10) on random Gaussian force fields; the net (kv_net_*) is
 trained by the library's tensor-core forward/backward kernels; evaluation
-compares kv_project_force with mode 0 (zero start) and mode 1 (learned start)
-at the same tolerance. This module only orchestrates calls through the binding.
+compares kv_project_force with mode 0 (zero start), mode 1 (learned start),
+mode 4 (multigrid-preconditioned CG) and mode 5 (learned start with the
+preconditioned CG) at the same tolerance. This module only orchestrates calls through the binding.
 
     python -m paper_2607_28414_b300.learned --train 2000 --train-n 128 --eval 200 --eval-n 256
 """
@@ -68,26 +69,39 @@ def train(net, B, P, shape, epochs=3, lr=1e-3, dx=DX, seed=0, log=None):
     return losses
 
 
-def evaluate(net, shape, forces, tol=1e-8, dx=DX, device="cuda:0"):
-    """Projection of each field with mode 0 and mode 1 at the same tolerance."""
+MODES = {0: "plain", 1: "learned", 4: "mg", 5: "learned_mg"}
+
+
+def evaluate(net, shape, forces, tol=1e-8, dx=DX, device="cuda:0", modes=(0, 1, 4, 5)):
+    """Projection of each field at the same tolerance with each mode: 0 the
+    paper's CG from zero, 1 the learned start, 4 multigrid-preconditioned CG
+    from zero, 5 the learned start with the multigrid-preconditioned CG.
+    Returns mean iterations and milliseconds per mode (keys <name>_iters,
+    <name>_ms, max_rel_res_<name>) and the wall-time ratios to mode 0."""
     h = projection_handle(shape, dx)
     kv.kv_attach_net(h, net)
-    rows = []
+    rows = {m: [] for m in modes}
     try:
         for f in forces:
-            r = {}
-            for mode in (0, 1):
+            for mode in modes:
                 st = kv.kv_project_force(h, *f, tol, 0, mode)
-                r[mode] = (st["iters"], st["ms"], st["rel_res_true"])
-            rows.append(r)
+                rows[mode].append((st["iters"], st["ms"], st["rel_res_true"]))
     finally:
         kv.kv_destroy(h)
-    plain = np.array([[r[0][0], r[0][1], r[0][2]] for r in rows])
-    learned = np.array([[r[1][0], r[1][1], r[1][2]] for r in rows])
-    return {"plain_iters": float(plain[:, 0].mean()), "plain_ms": float(plain[:, 1].mean()),
-            "learned_iters": float(learned[:, 0].mean()), "learned_ms": float(learned[:, 1].mean()),
-            "max_rel_res_plain": float(plain[:, 2].max()), "max_rel_res_learned": float(learned[:, 2].max()),
-            "speedup_ms": float(plain[:, 1].mean() / learned[:, 1].mean()), "fields": len(rows)}
+    out = {"fields": len(forces)}
+    for mode in modes:
+        a = np.array(rows[mode])
+        name = MODES[mode]
+        out[f"{name}_iters"] = float(a[:, 0].mean())
+        out[f"{name}_ms"] = float(a[:, 1].mean())
+        out[f"max_rel_res_{name}"] = float(a[:, 2].max())
+    if 0 in modes:
+        for mode in modes:
+            if mode != 0:
+                out[f"speedup_ms_{MODES[mode]}"] = out["plain_ms"] / out[f"{MODES[mode]}_ms"]
+        if 1 in modes:
+            out["speedup_ms"] = out["speedup_ms_learned"]
+    return out
 
 
 def main():

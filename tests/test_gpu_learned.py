@@ -95,6 +95,7 @@ def test_warm_start_reaches_the_same_residual_and_saves_iterations(device):
     res = learned.evaluate(net, shape, held, tol=1e-8)
     print("warm start on 40^3:", res)
     assert res["max_rel_res_learned"] < 1e-8 and res["max_rel_res_plain"] < 1e-8
+    assert res["max_rel_res_mg"] < 1e-8 and res["max_rel_res_learned_mg"] < 1e-8
     assert res["learned_iters"] < res["plain_iters"]
     # independent check of the learned-start potential by the oracle
     h = learned.projection_handle(shape)

@@ -114,7 +114,7 @@ def test_precomputed_projection_saves_over_per_step(device):
     torch.cuda.synchronize()
     t_pre = e0.elapsed_time(e1)
     t_gen = {}
-    for mode in (0, 3):
+    for mode in (0, 3, 4):
         s.reset()
         e2, e3 = ev(), ev()
         e2.record()
@@ -126,5 +126,7 @@ def test_precomputed_projection_saves_over_per_step(device):
     s.close()
     print(f"106^3, 85 steps: pre-computed {t_pre:.1f} ms; per-step projection from zero "
           f"{t_gen[0]:.1f} ms (ratio {t_gen[0] / t_pre:.1f}); from the previous potential "
-          f"{t_gen[3]:.1f} ms (ratio {t_gen[3] / t_pre:.1f})")
+          f"{t_gen[3]:.1f} ms (ratio {t_gen[3] / t_pre:.1f}); multigrid-preconditioned from zero "
+          f"{t_gen[4]:.1f} ms (ratio {t_gen[4] / t_pre:.1f})")
     assert t_gen[0] > 10 * t_pre
+    assert t_gen[4] < t_gen[0]
