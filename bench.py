@@ -269,6 +269,7 @@ def run_sweep(args, rank, world):
         forces.append([torch.from_numpy(a).to(device) for a in w.force])
     b = kv.kv_batch_create(hs)
     N = sum(w.n_cells for w in cases)
+    proj_mode = 4 if args.projection == "mg" else 0
 
     def one_pass():
         grids = {}
@@ -278,7 +279,7 @@ def run_sweep(args, rank, world):
             if key in grids:
                 kv.kv_share_force(h, hs[grids[key]])
             else:
-                kv.kv_project_force(h, *forces[i], w.tol)
+                kv.kv_project_force(h, *forces[i], w.tol, 0, proj_mode)
                 grids[key] = i
         kv.kv_batch_step(b, n_steps)
         out = torch.empty((n_steps, 256, 3), dtype=torch.float32, device=device)
@@ -333,6 +334,8 @@ def run_sweep(args, rank, world):
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep_26_cases", "cells": N, "time_steps": n_steps,
+                       "projection": ("CG preconditioned by a multigrid V(1,1)-cycle (mode 4)"
+                                      if proj_mode == 4 else "plain CG from zero (mode 0)"),
                        "parallelism": f"replicas{world}",
                        "projections_per_pass": n_proj, "batch_config": cfg,
                        "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2"},

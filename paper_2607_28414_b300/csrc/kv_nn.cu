@@ -1,8 +1,9 @@
 // kv_nn.cu -- tensor-core building blocks of the learned warm start: 3x3x3
-// convolution forward, input gradient and weight gradient as implicit GEMMs on
-// BF16 operands with FP32 accumulation (WMMA 16x16x16 tiles), plus the
-// channel-last elementwise pieces of a U-Net (pooling, upsampling, skips,
-// ReLU gradient) and the Adam update.
+// convolution forward and input gradient as implicit GEMMs on the
+// 5th-generation tensor cores (tcgen05.mma, BF16 operands from shared memory,
+// FP32 accumulators in tensor memory), the weight gradient as an implicit GEMM
+// with WMMA 16x16x16 tiles (its M = CIN is below the 64/128 rows of a tcgen05
+// tile), and the bias gradient and weight flip.
 //
 // Tensors are channel-last [z][y][x][C] BF16 with C in {16, 32, 64}. Weights
 // W[t][ci][co], tap t = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padding of one voxel:
@@ -21,84 +22,215 @@ namespace wm = nvcuda::wmma;
 namespace kv {
 
 // ---------------------------------------------------------------------------
-// Forward (and input-gradient) convolution
+// Forward (and input-gradient) convolution on the 5th-generation tensor cores
+//
+// Implicit GEMM: a block computes 2 x (128 voxels x COUT) outputs, the voxels
+// of an 8 (x) x 16 (y) tile on two consecutive z planes. Its input brick
+// (10 x 18 x 4 voxels with the one-voxel halo) is staged once in shared memory
+// in the canonical no-swizzle K-major layout of the tensor cores: channels in
+// chunks of 8 (16 bytes), brick[cc][z][y][x][8]. For tap (dx, dy, dz) the A
+// operand (128 voxels x 16 channels) is the brick seen from voxel offset
+// (dx, dy, dz + zt): 8-row core matrices are 8 consecutive x voxels (16-byte
+// rows), the 16 row groups step by one brick row (SBO = 160 bytes), and the two
+// 8-channel halves of K step by one channel chunk (LBO = 720 x 16 bytes). So
+// the 27 taps need no gather: each is a descriptor with a different start
+// address. The weights of the 9 taps of one dz are staged per group in the
+// same layout (B: COUT rows x 16 channels, SBO = 128 bytes, LBO = COUT x 16).
+// One thread issues tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators
+// in tensor memory: 2 x COUT columns), commits to an mbarrier, and the four
+// warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes
+// 32w .. 32w + 31 = tile rows) for the bias / ReLU / store epilogue.
 // ---------------------------------------------------------------------------
-constexpr int kCvTX = 16, kCvTY = 4, kCvTZ = 2;                  // 128 voxels per block
-constexpr int kCvBX = kCvTX + 2, kCvBY = kCvTY + 2, kCvBZ = kCvTZ + 2;
-constexpr int kCvBrick = kCvBX * kCvBY * kCvBZ;                   // 432 voxels with halo
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 2;                      // 2 x 128 voxels per block
+constexpr int kTcBX = kTcX + 2, kTcBY = kTcY + 2, kTcBZ = kTcZ + 2;
+constexpr int kTcBrick = kTcBX * kTcBY * kTcBZ;                   // 720 voxels with halo
 
 template <int CIN, int COUT>
-constexpr size_t conv_fwd_smem() {
-    return (size_t)kCvBrick * CIN * 2 + (size_t)CIN * COUT * 2;
+struct ConvTc {
+    static constexpr size_t kBrickBytes = (size_t)(CIN / 8) * kTcBrick * 16;
+    static constexpr size_t kTapBytes = (size_t)(CIN / 8) * COUT * 16;
+    static constexpr size_t kWBytes = 9 * kTapBytes;
+    static constexpr size_t kSmem = kBrickBytes + kWBytes + 16;  // + mbarrier, TMEM address
+    static constexpr uint32_t kCols = 2 * COUT < 32 ? 32 : 2 * COUT;  // power of two >= 32
+};
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8
+// rows x 16 bytes; lbo = byte stride between core matrices along K, sbo =
+// byte stride between 8-row groups along M (or N).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
+    return d;                // base offset 0, layout type 0 (no swizzle)
 }
 
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M as given.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ int g_conv_timeout;  // set when a bounded wait of a convolution gave up
+
 template <typename OutT>
-__device__ __forceinline__ OutT to_out(float v);
+__device__ __forceinline__ void store16(OutT *dst, const float (&v)[16]);
 template <>
-__device__ __forceinline__ float to_out<float>(float v) { return v; }
+__device__ __forceinline__ void store16<float>(float *dst, const float (&v)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4)
+        *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
 template <>
-__device__ __forceinline__ bf16 to_out<bf16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store16<bf16>(bf16 *dst, const float (&v)[16]) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(dst + 8) = make_uint4(w[4], w[5], w[6], w[7]);
+}
 
 template <int CIN, int COUT, typename OutT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const float *__restrict__ bias,
            OutT *__restrict__ out, int nx, int ny, int nz, int relu) {
-    extern __shared__ __align__(128) unsigned char sm[];
+    using C = ConvTc<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char sm[];
     bf16 *brick = reinterpret_cast<bf16 *>(sm);
-    bf16 *wt = brick + kCvBrick * CIN;
+    bf16 *wts = reinterpret_cast<bf16 *>(sm + C::kBrickBytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kBrickBytes + C::kWBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kCvTX, y0 = blockIdx.y * kCvTY, z0 = blockIdx.z * kCvTZ;
+    const int x0 = blockIdx.x * kTcX, y0 = blockIdx.y * kTcY, z0 = blockIdx.z * kTcZ;
+    const uint32_t bar_a = smem_u32(bar);
 
-    constexpr int VPV = CIN / 8;  // 16-byte vectors per voxel
-    for (int i = tid; i < kCvBrick * VPV; i += 256) {
-        const int vox = i / VPV, part = i % VPV;
-        const int bx = vox % kCvBX, by = (vox / kCvBX) % kCvBY, bz = vox / (kCvBX * kCvBY);
+    if (warp == 0) {  // tensor memory for the two accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(C::kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar_a, 1);
+        mbar_init_fence();
+    }
+    // input brick, channel-chunked
+    for (int i = tid; i < kTcBrick * (CIN / 8); i += 128) {
+        const int cc = i / kTcBrick, vox = i % kTcBrick;
+        const int bx = vox % kTcBX, by = (vox / kTcBX) % kTcBY, bz = vox / (kTcBX * kTcBY);
         const int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-            v = *reinterpret_cast<const uint4 *>(in + (((size_t)gz * ny + gy) * nx + gx) * CIN + part * 8);
-        *reinterpret_cast<uint4 *>(brick + (size_t)vox * CIN + part * 8) = v;
+            v = *reinterpret_cast<const uint4 *>(in + (((size_t)gz * ny + gy) * nx + gx) * CIN + cc * 8);
+        *reinterpret_cast<uint4 *>(brick + ((size_t)cc * kTcBrick + vox) * 8) = v;
     }
-    const int wy = warp % kCvTY, wz = warp / kCvTY;  // this warp's row of 16 voxels
-    wm::fragment<wm::accumulator, 16, 16, 16, float> acc[COUT / 16];
-#pragma unroll
-    for (int j = 0; j < COUT / 16; ++j) wm::fill_fragment(acc[j], 0.f);
-    for (int t = 0; t < 27; ++t) {
-        __syncthreads();  // previous tap's weights consumed (and the brick complete)
-        for (int i = tid; i < CIN * COUT / 8; i += 256)
-            *reinterpret_cast<uint4 *>(wt + i * 8) =
-                *reinterpret_cast<const uint4 *>(W + (size_t)t * CIN * COUT + i * 8);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t brick_a = smem_u32(brick), wts_a = smem_u32(wts);
+    constexpr uint32_t idesc = umma_idesc_bf16(128, COUT);
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int g = 0; g < 3; ++g) {  // the nine taps with dz = g
+        if (g > 0) {               // the previous group's MMAs have read the weight buffer
+            ok &= mbar_wait_bounded(bar_a, phase);
+            phase ^= 1;
+        }
+        for (int i = tid; i < 9 * CIN * COUT; i += 128) {
+            const int tt = i / (CIN * COUT), r = i % (CIN * COUT), ci = r / COUT, co = r % COUT;
+            wts[(((size_t)tt * (CIN / 8) + ci / 8) * COUT + co) * 8 + (ci % 8)] =
+                W[((size_t)(g * 9 + tt) * CIN + ci) * COUT + co];
+        }
+        fence_proxy_async();  // generic-proxy writes of the operands -> tensor-core reads
         __syncthreads();
-        const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
-        const bf16 *arow = brick + ((size_t)((wz + dz) * kCvBY + (wy + dy)) * kCvBX + dx) * CIN;
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll 1
+            for (int tt = 0; tt < 9; ++tt) {
+                const int dy = tt / 3, dx = tt % 3;
 #pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-            wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> a;
-            wm::load_matrix_sync(a, arow + kc * 16, CIN);
+                for (int kk = 0; kk < CIN / 16; ++kk) {
+                    const uint64_t bd = umma_desc(wts_a + (uint32_t)(tt * C::kTapBytes + 2 * kk * COUT * 16),
+                                                  COUT * 16, 128);
 #pragma unroll
-            for (int j = 0; j < COUT / 16; ++j) {
-                wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> b;
-                wm::load_matrix_sync(b, wt + kc * 16 * COUT + j * 16, COUT);
-                wm::mma_sync(acc[j], a, b, acc[j]);
+                    for (int zt = 0; zt < kTcZ; ++zt) {
+                        const uint32_t vox = ((zt + g) * kTcBY + dy) * kTcBX + dx;
+                        const uint64_t ad =
+                            umma_desc(brick_a + (uint32_t)((2 * kk * kTcBrick + vox) * 16), kTcBrick * 16, kTcBX * 16);
+                        umma_bf16(tmem + zt * COUT, ad, bd, idesc, (g | tt | kk) != 0);
+                    }
+                }
             }
+            umma_commit(bar_a);
         }
     }
-    __syncthreads();  // the brick is no longer read: reuse it for the output tiles
-    float *os = reinterpret_cast<float *>(sm) + (size_t)warp * 16 * COUT;
+    ok &= mbar_wait_bounded(bar_a, phase);
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_conv_timeout, 1);
+        mbar_wait_bounded(bar_a, phase);  // give in-flight MMAs a second chance before freeing TMEM
+    }
+    tc_fence_after();
+    // epilogue: TMEM lane 32w + lane = tile row m = y * 8 + x
+    const int m = 32 * warp + lane;
+    const int gx = x0 + (m % kTcX), gy = y0 + (m / kTcX);
 #pragma unroll
-    for (int j = 0; j < COUT / 16; ++j) wm::store_matrix_sync(os + j * 16, acc[j], COUT, wm::mem_row_major);
-    __syncwarp();
-    const int gy = y0 + wy, gz = z0 + wz;
-    if (gy < ny && gz < nz) {
-        for (int e = lane; e < 16 * COUT; e += 32) {
-            const int vx = e / COUT, co = e % COUT;
-            const int gx = x0 + vx;
-            if (gx >= nx) continue;
-            float v = os[e] + (bias ? bias[co] : 0.f);
-            if (relu) v = fmaxf(v, 0.f);
-            out[(((size_t)gz * ny + gy) * nx + gx) * COUT + co] = to_out<OutT>(v);
+    for (int zt = 0; zt < kTcZ; ++zt) {
+        const int gz = z0 + zt;
+        const bool inside = gx < nx && gy < ny && gz < nz;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(zt * COUT + c0), v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                float q = v[i] + (bias ? bias[c0 + i] : 0.f);
+                if (relu) q = fmaxf(q, 0.f);
+                v[i] = ok ? q : __int_as_float(0x7fc00000);  // a timed-out block writes NaN
+            }
+            if (inside) store16<OutT>(out + (((size_t)gz * ny + gy) * nx + gx) * COUT + c0, v);
         }
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kCols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -223,7 +355,7 @@ __global__ void k_flip_weights(const bf16 *__restrict__ W, bf16 *__restrict__ Wt
 template <int CIN, int COUT, typename OutT>
 static kv_status launch_fwd_t(int nx, int ny, int nz, const bf16 *in, const bf16 *W, const float *bias,
                               OutT *out, int relu, cudaStream_t s) {
-    const size_t smem = std::max(conv_fwd_smem<CIN, COUT>(), (size_t)8 * 16 * COUT * 4);
+    const size_t smem = ConvTc<CIN, COUT>::kSmem;
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -231,8 +363,8 @@ static kv_status launch_fwd_t(int nx, int ny, int nz, const bf16 *in, const bf16
             return KV_ERR_CUDA;
         attr = true;
     }
-    dim3 grid((nx + kCvTX - 1) / kCvTX, (ny + kCvTY - 1) / kCvTY, (nz + kCvTZ - 1) / kCvTZ);
-    k_conv_fwd<CIN, COUT, OutT><<<grid, 256, smem, s>>>(in, W, bias, out, nx, ny, nz, relu);
+    dim3 grid((nx + kTcX - 1) / kTcX, (ny + kTcY - 1) / kTcY, (nz + kTcZ - 1) / kTcZ);
+    k_conv_fwd<CIN, COUT, OutT><<<grid, 128, smem, s>>>(in, W, bias, out, nx, ny, nz, relu);
     return cudaGetLastError() == cudaSuccess ? KV_OK : KV_ERR_CUDA;
 }
 

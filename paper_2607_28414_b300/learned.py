@@ -81,14 +81,16 @@ def evaluate(net, shape, forces, tol=1e-8, dx=DX, device="cuda:0", modes=(0, 1, 
     h = projection_handle(shape, dx)
     kv.kv_attach_net(h, net)
     rows = {m: [] for m in modes}
+    n = 0
     try:
         for f in forces:
+            n += 1
             for mode in modes:
                 st = kv.kv_project_force(h, *f, tol, 0, mode)
                 rows[mode].append((st["iters"], st["ms"], st["rel_res_true"]))
     finally:
         kv.kv_destroy(h)
-    out = {"fields": len(forces)}
+    out = {"fields": n}
     for mode in modes:
         a = np.array(rows[mode])
         name = MODES[mode]
