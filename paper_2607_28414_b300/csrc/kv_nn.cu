@@ -173,10 +173,20 @@ k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const float 
             ok &= mbar_wait_bounded(bar_a, phase);
             phase ^= 1;
         }
-        for (int i = tid; i < 9 * CIN * COUT; i += 128) {
-            const int tt = i / (CIN * COUT), r = i % (CIN * COUT), ci = r / COUT, co = r % COUT;
-            wts[(((size_t)tt * (CIN / 8) + ci / 8) * COUT + co) * 8 + (ci % 8)] =
-                W[((size_t)(g * 9 + tt) * CIN + ci) * COUT + co];
+        // one 16-byte row (8 input channels of one output channel) per item;
+        // consecutive threads read consecutive output channels
+        for (int i = tid; i < 9 * (CIN / 8) * COUT; i += 128) {
+            const int co = i % COUT, r = i / COUT, cc = r % (CIN / 8), tt = r / (CIN / 8);
+            const bf16 *src = W + ((size_t)(g * 9 + tt) * CIN + cc * 8) * COUT + co;
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t lo = __bfloat16_as_ushort(src[(2 * j) * COUT]);
+                const uint32_t hi = __bfloat16_as_ushort(src[(2 * j + 1) * COUT]);
+                w[j] = lo | (hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(wts + ((size_t)(tt * (CIN / 8) + cc) * COUT + co) * 8) =
+                make_uint4(w[0], w[1], w[2], w[3]);
         }
         fence_proxy_async();  // generic-proxy writes of the operands -> tensor-core reads
         __syncthreads();
