@@ -148,6 +148,28 @@ kv_status kv_set_sensors(kv_handle *h, const int *ijk, int n, int capacity);
 /* Zero the displacement state, the step counter and the trace record. */
 kv_status kv_reset(kv_handle *h);
 
+/* Failure-path check (no counterpart in the paper): launches one block that
+ * waits, with the bounded wait every step and CG kernel uses (about a second of
+ * SM clocks), on an mbarrier that nothing completes. The wait gives up, sets
+ * the device error flag, and the call returns KV_ERR_TIMEOUT with the handle in
+ * the error state, exactly as a timed-out step or CG kernel would leave it.
+ * Nothing faults and the CUDA context stays usable. Synchronising. */
+kv_status kv_selftest_wait(kv_handle *h);
+
+/* Checkpoint and resume (no counterpart in the paper). The state of a step is
+ * the two fields u^n and d^n = u^n - u^{n-1} in the handle's own layout: six
+ * component planes [6][nz][ny][px] of float (KV_FP32) or double (KV_FP64),
+ * rows padded to px = nx rounded up to 32, kv_state_bytes(h) bytes in all.
+ * kv_save_state copies it to buf (host or device memory, per where) and
+ * returns the step index; kv_load_state copies a buffer saved from a handle of
+ * the same grid and precision back and sets the step index, after which
+ * kv_step continues bit for bit as the saved run did (same medium, force,
+ * envelope and sensors). The outer node layer must hold zeros; the row padding
+ * is never read into a result. Synchronising. */
+long long kv_state_bytes(kv_handle *h);
+kv_status kv_save_state(kv_handle *h, void *buf, int where, long long *step);
+kv_status kv_load_state(kv_handle *h, const void *buf, int where, long long step);
+
 /* Initial velocity v0 (Sec. 3.5 curl-based start): u^0 = 0, u^{-1} = -dt v0,
  * applied on interior nodes. Resets the step counter and traces. */
 kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_field vz);

@@ -488,6 +488,43 @@ kv_status kv_reset(kv_handle *h) {
     return cuda_check(h, e, "kv_reset");
 }
 
+kv_status kv_selftest_wait(kv_handle *h) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    kv_status st = launch_wait_selftest(h);
+    if (st != KV_OK) return st;
+    return poll_flags(h);  // KV_ERR_TIMEOUT, handle in the error state
+}
+
+long long kv_state_bytes(kv_handle *h) { return h ? 6 * (long long)h->Np * (long long)h->esize : 0; }
+
+kv_status kv_save_state(kv_handle *h, void *buf, int where, long long *step) {
+    if (!h || !buf || (where != KV_HOST && where != KV_DEVICE))
+        return set_error(h, KV_ERR_ARG, "kv_save_state: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    kv_status st = poll_flags(h);
+    if (st != KV_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(buf, h->state[h->cur], (size_t)kv_state_bytes(h), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if ((st = cuda_check(h, e, "kv_save_state")) != KV_OK) return st;
+    if (step) *step = h->steps_host;
+    return KV_OK;
+}
+
+kv_status kv_load_state(kv_handle *h, const void *buf, int where, long long step) {
+    if (!h || !buf || step < 0 || (where != KV_HOST && where != KV_DEVICE))
+        return set_error(h, KV_ERR_ARG, "kv_load_state: invalid arguments");
+    if (h->sticky) return KV_ERR_STATE;
+    kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_load_state");
+    if (st != KV_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h->state[h->cur], buf, (size_t)kv_state_bytes(h), cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctrl + kStep, &step, sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if ((st = cuda_check(h, e, "kv_load_state")) != KV_OK) return st;
+    h->steps_host = step;
+    return KV_OK;
+}
+
 kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_field vz) {
     if (!h) return KV_ERR_ARG;
     const kv_field *v[3] = {&vx, &vy, &vz};

@@ -247,7 +247,8 @@ k_cg_upd(const T *__restrict__ p0, const T *__restrict__ p1, T *__restrict__ r, 
 // seen by TMA as a 4D tensor (x, y, z, field). A block owns a kCgTX x kCgTY
 // column and marches z; every plane it needs arrives by TMA into a ring of
 // kCgNS shared-memory stages, so several planes are in flight per block while
-// one is computed. Each thread computes four consecutive x nodes (a float4);
+// one is computed. The z-1 neighbour is the previous plane's centre value,
+// kept in registers, so a stage is refilled as soon as its plane is done. Each thread computes four consecutive x nodes (a float4);
 // x neighbours come from warp shuffles, y and z neighbours from the staged
 // tiles. Per-node arithmetic is the same sequence as the plain kernels above.
 // Reductions: float-float per thread and across the block, double per block.
@@ -375,22 +376,28 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
                m3 = x + 3 <= p.nx - 2;
     const int o = (t.gy + 1) * kCgBXh + 4 + 4 * t.gx;
     const long long sz = (long long)p.px * p.ny;
+    auto pn4 = [&](const float *st, int off) {
+        const float4 pv = ld4(st + ps * kCgHalo + off), rv = ld4(st + rs * kCgHalo + off);
+        return make_float4(kv_fma(beta, pv.x, rv.x), kv_fma(beta, pv.y, rv.y),
+                           kv_fma(beta, pv.z, rv.z), kv_fma(beta, pv.w, rv.w));
+    };
+    // register-blocked z march: p' of plane k-1 (the z-1 neighbour) stays in
+    // registers, so a stage is released once its plane is computed
+    ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.kb), t.parity(t.kb));
+    float4 prev = pn4(smem + t.slot(t.kb) * kCgStageDir, o);
+    __syncthreads();
+    if (threadIdx.x == 0 && t.kb + kCgNS <= t.k1) {
+        fence_proxy_async();
+        issue(t.kb + kCgNS);
+    }
+    ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.k0), t.parity(t.k0));
     for (int k = t.k0; k < t.k1; ++k) {
-        if (k == t.k0) {
-            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k - 1), t.parity(k - 1));
-            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k), t.parity(k));
-        }
         ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k + 1), t.parity(k + 1));
         const float *sc = smem + t.slot(k) * kCgStageDir;
-        const float *sm = smem + t.slot(k - 1) * kCgStageDir;
         const float *sp = smem + t.slot(k + 1) * kCgStageDir;
-        auto pn4 = [&](const float *st, int off) {
-            const float4 pv = ld4(st + ps * kCgHalo + off), rv = ld4(st + rs * kCgHalo + off);
-            return make_float4(kv_fma(beta, pv.x, rv.x), kv_fma(beta, pv.y, rv.y),
-                               kv_fma(beta, pv.z, rv.z), kv_fma(beta, pv.w, rv.w));
-        };
         const float4 c = pn4(sc, o), ym = pn4(sc, o - kCgBXh), yp = pn4(sc, o + kCgBXh);
-        const float4 zm = pn4(sm, o), zp = pn4(sp, o);
+        const float4 zm = prev, zp = pn4(sp, o);
+        prev = c;
         float left = __shfl_up_sync(0xffffffffu, c.w, 1);
         float right = __shfl_down_sync(0xffffffffu, c.x, 1);
         if (t.gx == 0) left = kv_fma(beta, sc[ps * kCgHalo + o - 1], sc[rs * kCgHalo + o - 1]);
@@ -415,7 +422,7 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int q = k - 1 + kCgNS;
+            const int q = k + kCgNS;
             if (q <= t.k1) {
                 fence_proxy_async();
                 issue(q);
@@ -469,17 +476,22 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
     const int o = (t.gy + 1) * kCgBXh + 4 + 4 * t.gx;
     const int oc = t.gy * kCgTX + 4 * t.gx;
     const long long sz = (long long)p.px * p.ny;
+    // register-blocked z march, as in pass 1
+    ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.kb), t.parity(t.kb));
+    float4 prev = ld4(smem + t.slot(t.kb) * kCgStageUpd + o);
+    __syncthreads();
+    if (threadIdx.x == 0 && t.kb + kCgNS <= t.k1) {
+        fence_proxy_async();
+        issue(t.kb + kCgNS);
+    }
+    ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.k0), t.parity(t.k0));
     for (int k = t.k0; k < t.k1; ++k) {
-        if (k == t.k0) {
-            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k - 1), t.parity(k - 1));
-            ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k), t.parity(k));
-        }
         ok &= mbar_wait_bounded(bar0 + 8 * t.slot(k + 1), t.parity(k + 1));
         const float *sc = smem + t.slot(k) * kCgStageUpd;
-        const float *sm = smem + t.slot(k - 1) * kCgStageUpd;
         const float *sp = smem + t.slot(k + 1) * kCgStageUpd;
         const float4 c = ld4(sc + o), ym = ld4(sc + o - kCgBXh), yp = ld4(sc + o + kCgBXh);
-        const float4 zm = ld4(sm + o), zp = ld4(sp + o);
+        const float4 zm = prev, zp = ld4(sp + o);
+        prev = c;
         float left = __shfl_up_sync(0xffffffffu, c.w, 1);
         float right = __shfl_down_sync(0xffffffffu, c.x, 1);
         if (t.gx == 0) left = sc[o - 1];
@@ -509,7 +521,7 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int q = k - 1 + kCgNS;
+            const int q = k + kCgNS;
             if (q <= t.k1) {
                 fence_proxy_async();
                 issue(q);

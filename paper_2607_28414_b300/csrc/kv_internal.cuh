@@ -213,6 +213,7 @@ kv_status cuda_check(kv_handle *h, cudaError_t e, const char *what);
 kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attributes
 kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
 kv_status step2_launch(kv_handle *h, int from_buffer); // two steps (variant 2), one buffer swap
+kv_status launch_wait_selftest(kv_handle *h);          // bounded wait on an mbarrier nothing completes
 
 // Step kernel kinds: homogeneous, pointwise heterogeneous (Sec. 3.1),
 // divergence-form heterogeneous.

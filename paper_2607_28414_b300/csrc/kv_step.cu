@@ -757,6 +757,27 @@ __global__ void k_init_velocity(const float *__restrict__ v, T *__restrict__ st,
     }
 }
 
+// Failure-path check of the bounded waits: an mbarrier that nothing arrives
+// on, waited for with the same bounded wait as the step and CG kernels; the
+// give-up sets the same device error flag (bit 0 of kErrFlags).
+__global__ void k_wait_selftest(long long *ctrl) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(b, 0);
+    if (!ok && threadIdx.x == 0) atomicOr(reinterpret_cast<unsigned long long *>(&ctrl[kErrFlags]), 1ull);
+}
+
+kv_status launch_wait_selftest(kv_handle *h) {
+    k_wait_selftest<<<1, 32, 0, h->stream>>>(h->ctrl);
+    h->launches++;
+    return cuda_check(h, cudaGetLastError(), "wait self-test launch");
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------

@@ -80,6 +80,11 @@ def lib():
         L.kv_stable_dt.argtypes = [i, i, i, d, F, F, F, ctypes.POINTER(d)]
         L.kv_create.argtypes = [ctypes.POINTER(H), i, i, i, d, d, F, F, F, i, vp]
         L.kv_set_medium.argtypes = [H, F, F, F]
+        L.kv_selftest_wait.argtypes = [H]
+        L.kv_state_bytes.argtypes = [H]
+        L.kv_state_bytes.restype = ctypes.c_longlong
+        L.kv_save_state.argtypes = [H, vp, i, ctypes.POINTER(ctypes.c_longlong)]
+        L.kv_load_state.argtypes = [H, vp, i, ctypes.c_longlong]
         L.kv_stable_dt_op.argtypes = [i, i, i, d, F, F, F, i, ctypes.POINTER(d)]
         L.kv_set_operator.argtypes = [H, i, F, F, F]
         L.kv_set_envelope.argtypes = [H, vp, i, i]
@@ -224,6 +229,31 @@ def kv_set_medium(h, G, rho, eta):
 def kv_set_operator(h, op, G, rho, eta):
     keep = []
     _check(lib().kv_set_operator(h, int(op), field(G, keep), field(rho, keep), field(eta, keep)), h)
+
+
+def kv_selftest_wait(h):
+    """Runs the bounded-wait failure path; returns the kv_status (KV_ERR_TIMEOUT)."""
+    return int(lib().kv_selftest_wait(h))
+
+
+def kv_state_bytes(h):
+    return int(lib().kv_state_bytes(h))
+
+
+def kv_save_state(h, buf):
+    """Copy the state (u^n, d^n in the handle's padded layout) into buf, a
+    NumPy array or CUDA tensor of kv_state_bytes(h) bytes; returns the step."""
+    keep = []
+    p, where = _ptr(buf, keep)
+    step = ctypes.c_longlong()
+    _check(lib().kv_save_state(h, p, where, ctypes.byref(step)), h)
+    return step.value
+
+
+def kv_load_state(h, buf, step):
+    keep = []
+    p, where = _ptr(buf, keep)
+    _check(lib().kv_load_state(h, p, where, int(step)), h)
 
 
 def kv_set_envelope(h, g):
