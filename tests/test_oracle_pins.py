@@ -497,3 +497,62 @@ def test_divergence_form_conserves_its_energy():
                          u_in=u0, uprev_in=um, want_state=True, divform=True)
     ea, eb = E(ua, uam), E(ub, ubm)
     assert ea > 0 and abs(eb - ea) < 1e-10 * abs(ea)
+
+
+def test_centred_push_mirror_symmetry():
+    """A centred Gaussian push along z on a grid whose centre is a node drives
+    u_z symmetric in x and y about the centre: the medium, the walls and f_z
+    are mirror symmetric, and f_S,z = f_z - D+_z phi keeps the x and y mirror
+    symmetry of phi."""
+    from paper_2607_28414_b300 import inputs
+    n = 21
+    f = inputs.gaussian_push(n, n, n, DX, 1e3, 1e-3, 2e-3)
+    _, fs, _, _ = orc.project(*f, DX, tol=1e-13)
+    dt = 0.5 * orc.stable_dt(4e3, 1000.0, 0.4, DX)
+    g = inputs.push_envelope(60, dt, 10 * dt)
+    c = n // 2
+    sensors = np.array([[c + 3, c, c], [c - 3, c, c], [c, c + 5, c], [c, c - 5, c]], np.int32)
+    tr = orc.run(n, n, n, DX, dt, 4e3, 1000.0, 0.4, 60, sensors, fs=fs, g=g)
+    scale = np.abs(tr[:, :, 2]).max()
+    assert scale > 0
+    np.testing.assert_allclose(tr[:, 0, 2], tr[:, 1, 2], rtol=0, atol=1e-10 * scale)
+    np.testing.assert_allclose(tr[:, 2, 2], tr[:, 3, 2], rtol=0, atol=1e-10 * scale)
+    # (u_x and u_y are driven by the forward-difference gradient of phi,
+    # which lives half a node off the centre: they carry no such symmetry
+    # once the walls at 0 and n - 1 reflect them.)
+
+
+def test_divergence_form_energy_decays_with_viscosity():
+    """eta > 0 in the flux form: the eta = 0 energy of the same K is not
+    conserved but decreases."""
+    nx, ny, nz = 12, 11, 10
+    rng = np.random.default_rng(5)
+    mu = rng.uniform(1e3, 10e3, (nz, ny, nx))
+    rho = rng.uniform(1000, 1100, (nz, ny, nx))
+    eta = rng.uniform(0.1, 1.0, (nz, ny, nx))
+    dt = 0.4 * orc.stable_dt(mu, rho, eta, DX)
+    u0 = [rng.standard_normal((nz, ny, nx)) * 1e-6 for _ in range(3)]
+    um = [q * 0.98 for q in u0]
+
+    def K(q):
+        out = np.zeros_like(q)
+        c = (slice(1, -1),) * 3
+        for ax in range(3):
+            for sgn in (-1, 1):
+                sl = [slice(1, -1)] * 3
+                sl[ax] = slice(1 + sgn, q.shape[ax] - 1 + sgn)
+                sl = tuple(sl)
+                out[c] += 0.5 * (mu[c] + mu[sl]) * (q[sl] - q[c])
+        return out / DX ** 2
+
+    def E(un, uc):
+        m = interior_mask(nx, ny, nz)
+        return sum(np.sum(rho[m] * (un[c] - uc[c])[m] ** 2) / dt ** 2 - np.sum(un[c] * K(uc[c]))
+                   for c in range(3))
+
+    es = []
+    for n in (3, 30, 90):
+        _, ua, uam = orc.run(nx, ny, nz, DX, dt, mu, rho, eta, n, np.zeros((1, 3), np.int32),
+                             u_in=u0, uprev_in=um, want_state=True, divform=True)
+        es.append(E(ua, uam))
+    assert es[0] > es[1] > es[2] > 0
