@@ -443,9 +443,12 @@ k_step_batch(const BatchCase *__restrict__ cases, int ncases, int from) {
 //
 // Each z-march iteration k first computes the intermediate state (u, d)^{n+1}
 // of plane k+1 over the block's tile plus a one-node ring (rows y0-1..y0+TY,
-// columns x0-4..x0+TX+3 in float4 groups) into a 3-plane shared-memory ring,
+// columns x0-4..x0+TX+3 in float4 groups) into a 2-plane shared-memory ring,
 // then the final state (u, d)^{n+2} of plane k over the tile, written to global
-// memory. The state at step n arrives by TMA with a 2-row y halo and the
+// memory. The z-1 neighbours of both levels (input plane j-1 of an
+// intermediate node, intermediate plane k-1 of an output node) stay in
+// registers, and the output nodes' coefficients are read one plane ahead, so
+// an input stage is refilled as soon as its plane has been used as a centre. The state at step n arrives by TMA with a 2-row y halo and the
 // aligned 4-column x halo. Every node of both levels goes through kv_update
 // with the same neighbour order as the single-step kernels, so two steps here
 // are bit-identical to two single steps. Intermediate nodes outside the grid or
@@ -507,10 +510,12 @@ __global__ void __launch_bounds__(128)
 k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
             const float *__restrict__ F, float *__restrict__ out, StepParams p) {
     using T2 = Tile2<TX, TY, HET>;
+    constexpr int RM = (T2::MID_GROUPS + T2::NT - 1) / T2::NT;  // intermediate groups per thread
+    constexpr int RO = (T2::OUT_GROUPS + T2::NT - 1) / T2::NT;  // output groups per thread
     extern __shared__ __align__(128) float smem[];
     float *inr = smem;                                 // NS input stages
-    float *mid = smem + NS * T2::IN_STAGE;             // 3 intermediate planes
-    uint64_t *bars = reinterpret_cast<uint64_t *>(mid + 3 * T2::MID_STAGE);
+    float *mid = smem + NS * T2::IN_STAGE;             // 2 intermediate planes
+    uint64_t *bars = reinterpret_cast<uint64_t *>(mid + 2 * T2::MID_STAGE);
     const uint32_t bar0 = smem_u32(bars);
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = 1 + blockIdx.y * TY;
@@ -529,6 +534,7 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
     __syncthreads();
     auto slot = [&](int q) { return (q - qb) % NS; };
     auto par = [&](int q) { return (uint32_t)(((q - qb) / NS) & 1); };
+    auto midp = [&](int j) { return mid + ((j - (k0 - 1)) & 1) * T2::MID_STAGE; };
     auto issue = [&](int q) {
         const uint32_t bar = bar0 + 8 * slot(q);
         float *st = inr + slot(q) * T2::IN_STAGE;
@@ -537,18 +543,73 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
         if (HET) tma_load_4d(smem_u32(st + T2::IN_STATE), &tm_coef, x0 - 4, y0 - 1, q, 0, bar);
     };
     int next_issue = qb;
+    auto refill = [&](int upto) {  // thread 0, after a barrier: stage planes up to `upto`
+        if (tid == 0) {
+            fence_proxy_async();
+            for (; next_issue <= min(k1 + 1, upto); ++next_issue) issue(next_issue);
+        }
+    };
     if (tid == 0)
         for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue(next_issue);
     bool ok = true;
 
-    // intermediate plane j (needs input planes j-1, j, j+1 staged)
+    // Register blocking in z: the z-1 neighbours of an intermediate node
+    // (input plane j-1) and of an output node (intermediate plane k-1) are the
+    // centre values this thread read one plane earlier.
+    float4 prev_in[RM][6], prev_mid[RO][6], coef_cur[RO][2], coef_next[RO][2] = {};
+
+    auto load_prev_in = [&](int j) {  // input plane j at this thread's intermediate groups
+        const float *sc = inr + slot(j) * T2::IN_STAGE;
+#pragma unroll
+        for (int rr = 0; rr < RM; ++rr) {
+            const int gi = tid + rr * T2::NT;
+            if (gi >= T2::MID_GROUPS) continue;
+            const int r = gi / T2::GXI, cg = gi % T2::GXI;
+            const int oi = (r + 1) * T2::BX + 4 * cg;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) prev_in[rr][f] = *reinterpret_cast<const float4 *>(sc + f * T2::IN_F + oi);
+        }
+    };
+    auto load_out_coef = [&](int k, float4 (&dst)[RO][2]) {  // plane k's coefficients at the output groups
+        const float *cs = inr + slot(k) * T2::IN_STAGE + T2::IN_STATE;
+#pragma unroll
+        for (int ro = 0; ro < RO; ++ro) {
+            const int go = tid + ro * T2::NT;
+            if (go >= T2::OUT_GROUPS) continue;
+            const int r = go / T2::GX, gx = go % T2::GX;
+            const int om = (r + 1) * T2::BX + 4 + 4 * gx;
+            if (HET) {
+                dst[ro][0] = *reinterpret_cast<const float4 *>(cs + om);
+                dst[ro][1] = *reinterpret_cast<const float4 *>(cs + T2::MID_F + om);
+            } else {
+                dst[ro][0] = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+                dst[ro][1] = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+            }
+        }
+    };
+    auto load_prev_mid = [&](int j) {  // intermediate plane j at this thread's output groups
+        const float *mj = midp(j);
+#pragma unroll
+        for (int ro = 0; ro < RO; ++ro) {
+            const int go = tid + ro * T2::NT;
+            if (go >= T2::OUT_GROUPS) continue;
+            const int r = go / T2::GX, gx = go % T2::GX;
+            const int om = (r + 1) * T2::BX + 4 + 4 * gx;
+#pragma unroll
+            for (int f = 0; f < 6; ++f) prev_mid[ro][f] = *reinterpret_cast<const float4 *>(mj + f * T2::MID_F + om);
+        }
+    };
+
+    // intermediate plane j (input plane j centre and j+1 staged, j-1 in prev_in)
     auto compute_mid = [&](int j) {
-        float *mj = mid + ((j - (k0 - 1)) % 3) * T2::MID_STAGE;
+        float *mj = midp(j);
         const bool plane_in = (j >= 1 && j <= p.nz - 2);
         const float *sc = inr + slot(j) * T2::IN_STAGE;
-        const float *sm = plane_in ? inr + slot(j - 1) * T2::IN_STAGE : sc;
-        const float *sp = plane_in ? inr + slot(j + 1) * T2::IN_STAGE : sc;
-        for (int gi = tid; gi < T2::MID_GROUPS; gi += T2::NT) {
+        const float *sp = inr + slot(j + 1) * T2::IN_STAGE;
+#pragma unroll
+        for (int rr = 0; rr < RM; ++rr) {
+            const int gi = tid + rr * T2::NT;
+            if (gi >= T2::MID_GROUPS) continue;
             const int r = gi / T2::GXI, cg = gi % T2::GXI;
             const int y = y0 - 1 + r, x = x0 - 4 + 4 * cg;
             const int oi = (r + 1) * T2::BX + 4 * cg;  // input tile offset of this group
@@ -572,7 +633,7 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
                 const float4 c = *reinterpret_cast<const float4 *>(fc);
                 const float4 ym = *reinterpret_cast<const float4 *>(fc - T2::BX);
                 const float4 yp = *reinterpret_cast<const float4 *>(fc + T2::BX);
-                const float4 zm = *reinterpret_cast<const float4 *>(sm + f * T2::IN_F + oi);
+                const float4 zm = prev_in[rr][f];
                 const float4 zp = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
                 const float left = (cg == 0) ? 0.f : fc[-1];
                 const float right = (cg == T2::GXI - 1) ? 0.f : fc[4];
@@ -583,6 +644,7 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
                 s4.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
                 ctr[f] = c;
                 sum[f] = s4;
+                prev_in[rr][f] = c;
             }
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
@@ -608,23 +670,35 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
         }
     };
 
+    // Prologue. Planes k0-2 .. k0+NS-3 are in flight. Each input stage is
+    // released as soon as its centre values (and, for plane k, the output
+    // groups' coefficients) are in registers.
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(qb), par(qb));
+    load_prev_in(qb);
+    __syncthreads();
+    refill(qb + NS);
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 - 1), par(k0 - 1));
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0), par(k0));
+    compute_mid(k0 - 1);
+    __syncthreads();
+    refill(k0 - 1 + NS);
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 + 1), par(k0 + 1));
+    compute_mid(k0);
+    load_out_coef(k0, coef_cur);
+    __syncthreads();  // intermediate planes k0-1 and k0 complete
+    load_prev_mid(k0 - 1);
+    refill(k0 + NS);
+    __syncthreads();  // plane k0-1's slot is read: the loop's first intermediate plane overwrites it
+
     for (int k = k0; k < k1; ++k) {
-        if (k == k0) {
-            for (int q = qb; q <= k0 + 1; ++q) ok &= mbar_wait_bounded(bar0 + 8 * slot(q), par(q));
-            compute_mid(k0 - 1);
-            compute_mid(k0);
-            __syncthreads();  // planes k0-2 and k0-1 are free: the oldest needed is k0
-            if (tid == 0) {
-                fence_proxy_async();
-                for (; next_issue <= min(k1 + 1, k0 + NS - 1); ++next_issue) issue(next_issue);
-            }
-        }
         ok &= mbar_wait_bounded(bar0 + 8 * slot(k + 2), par(k + 2));
-        compute_mid(k + 1);
-        __syncthreads();
+        compute_mid(k + 1);  // into the slot of intermediate plane k-1 (now in prev_mid)
+        if (k + 1 < k1) load_out_coef(k + 1, coef_next);
+        __syncthreads();     // intermediate plane k+1 complete; input plane k+1 consumed
+        refill(k + 1 + NS);
         // sensors of the intermediate step owned by this block (plane k)
         if (p.ns > 0 && step < p.cap) {
-            const float *mk = mid + ((k - (k0 - 1)) % 3) * T2::MID_STAGE;
+            const float *mk = midp(k);
             float *tr = reinterpret_cast<float *>(p.traces) + (size_t)step * p.ns * 3;
             for (int q = p.sens_off[k] + tid; q < p.sens_off[k + 1]; q += T2::NT) {
                 const int s = p.sens_ord[q];
@@ -634,24 +708,18 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
                         tr[3 * s + comp] = mk[comp * T2::MID_F + (jj - y0 + 1) * T2::BX + (i - x0 + 4)];
             }
         }
-        // final step of plane k from intermediate planes k-1, k, k+1
-        const float *mc = mid + ((k - (k0 - 1)) % 3) * T2::MID_STAGE;
-        const float *mm = mid + ((k - 1 - (k0 - 1)) % 3) * T2::MID_STAGE;
-        const float *mp = mid + ((k + 1 - (k0 - 1)) % 3) * T2::MID_STAGE;
-        const float *cs = inr + slot(k) * T2::IN_STAGE + T2::IN_STATE;  // coefficients of plane k
-        for (int go = tid; go < T2::OUT_GROUPS; go += T2::NT) {
+        // final step of plane k from intermediate planes k-1 (registers), k, k+1
+        const float *mc = midp(k);
+        const float *mp = midp(k + 1);
+#pragma unroll
+        for (int ro = 0; ro < RO; ++ro) {
+            const int go = tid + ro * T2::NT;
+            if (go >= T2::OUT_GROUPS) continue;
             const int r = go / T2::GX, gx = go % T2::GX;
             const int y = y0 + r, x = x0 + 4 * gx;
-            if (y > p.ny - 2 || x >= p.px) continue;
             const int om = (r + 1) * T2::BX + 4 + 4 * gx;
-            float4 A4, B4;
-            if (HET) {
-                A4 = *reinterpret_cast<const float4 *>(cs + om);
-                B4 = *reinterpret_cast<const float4 *>(cs + T2::MID_F + om);
-            } else {
-                A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
-                B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
-            }
+            const float4 A4 = coef_cur[ro][0], B4 = coef_cur[ro][1];
+            const bool row_ok = (y <= p.ny - 2) && (x < p.px);
             const bool m0 = (x >= 1) && (x <= p.nx - 2), m1 = (x + 1 <= p.nx - 2);
             const bool m2 = (x + 2 <= p.nx - 2), m3 = (x + 3 <= p.nx - 2);
             float4 ctr[6], sum[6];
@@ -661,7 +729,7 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
                 const float4 c = *reinterpret_cast<const float4 *>(fc);
                 const float4 ym = *reinterpret_cast<const float4 *>(fc - T2::BX);
                 const float4 yp = *reinterpret_cast<const float4 *>(fc + T2::BX);
-                const float4 zm = *reinterpret_cast<const float4 *>(mm + f * T2::MID_F + om);
+                const float4 zm = prev_mid[ro][f];
                 const float4 zp = *reinterpret_cast<const float4 *>(mp + f * T2::MID_F + om);
                 const float left = fc[-1], right = fc[4];
                 float4 s4;
@@ -671,7 +739,9 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
                 s4.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
                 ctr[f] = c;
                 sum[f] = s4;
+                prev_mid[ro][f] = c;
             }
+            if (!row_ok) continue;
             const long long gbase = k * sz + (long long)y * sy + x;
 #pragma unroll
             for (int comp = 0; comp < 3; ++comp) {
@@ -691,11 +761,12 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
                 *reinterpret_cast<float4 *>(out + (3 + comp) * p.Np + gbase) = dn;
             }
         }
-        __syncthreads();  // input plane k and intermediate plane k-1 are free
-        if (tid == 0) {
-            fence_proxy_async();
-            for (; next_issue <= min(k1 + 1, k + NS); ++next_issue) issue(next_issue);
+#pragma unroll
+        for (int ro = 0; ro < RO; ++ro) {
+            coef_cur[ro][0] = coef_next[ro][0];
+            coef_cur[ro][1] = coef_next[ro][1];
         }
+        __syncthreads();  // intermediate plane k is no longer read: its slot takes plane k+2
     }
     if (__syncthreads_or(!ok) && tid == 0) {
         atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
@@ -876,10 +947,10 @@ static bool pick2(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, 
     if (tx != TX || ty != TY || ns != NS) return false;
     if (het) {
         *k = k_step2_tma<TX, TY, NS, true>;
-        *smem = (NS * Tile2<TX, TY, true>::IN_STAGE + 3 * Tile2<TX, TY, true>::MID_STAGE) * 4 + NS * 8;
+        *smem = (NS * Tile2<TX, TY, true>::IN_STAGE + 2 * Tile2<TX, TY, true>::MID_STAGE) * 4 + NS * 8;
     } else {
         *k = k_step2_tma<TX, TY, NS, false>;
-        *smem = (NS * Tile2<TX, TY, false>::IN_STAGE + 3 * Tile2<TX, TY, false>::MID_STAGE) * 4 + NS * 8;
+        *smem = (NS * Tile2<TX, TY, false>::IN_STAGE + 2 * Tile2<TX, TY, false>::MID_STAGE) * 4 + NS * 8;
     }
     *nt = 128;
     return true;
