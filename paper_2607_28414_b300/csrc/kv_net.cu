@@ -30,6 +30,7 @@ kv_status nn_conv_fwd(int nx, int ny, int nz, int cin, int cout, const void *x, 
 kv_status nn_conv_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x, const void *g,
                         float *gW, float *gb, cudaStream_t s);
 kv_status nn_flip(int cin, int cout, const void *W, void *Wt, cudaStream_t s);
+kv_status nn_take_timeout();
 }  // namespace kv
 
 namespace {
@@ -500,6 +501,7 @@ kv_status kv_net_train_step(kv_net *n, int nx, int ny, int nz, double dx, const 
     double l = 0.0;
     cudaMemcpyAsync(&l, n->red, sizeof(double), cudaMemcpyDeviceToHost, n->stream);
     if (cudaStreamSynchronize(n->stream) != cudaSuccess) return nerr(n, KV_ERR_CUDA, "kv_net_train_step: CUDA error");
+    if ((st = kv::nn_take_timeout()) != KV_OK) return nerr(n, st, "kv_net_train_step: a convolution's bounded wait timed out");
     if (loss) *loss = l;
     return KV_OK;
 }
@@ -516,6 +518,7 @@ kv_status kv_net_predict(kv_net *n, int nx, int ny, int nz, double dx, const flo
     if (st != KV_OK) return nerr(n, st, "kv_net_predict: forward failed");
     k_out_extract<<<kEwBlocks, 256, 0, n->stream>>>(n->yout, phi, V, (float)(dx * dx / s), nx, ny, nz);
     if (cudaStreamSynchronize(n->stream) != cudaSuccess) return nerr(n, KV_ERR_CUDA, "kv_net_predict: CUDA error");
+    if ((st = kv::nn_take_timeout()) != KV_OK) return nerr(n, st, "kv_net_predict: a convolution's bounded wait timed out");
     return KV_OK;
 }
 

@@ -444,6 +444,16 @@ kv_status nn_conv_wgrad(int nx, int ny, int nz, int cin, int cout, const void *x
     }
     return KV_OK;
 }
+// KV_ERR_TIMEOUT if a convolution's bounded wait gave up since the last call
+// (the flag is cleared). Call after the stream has been synchronised.
+kv_status nn_take_timeout() {
+    int flag = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_conv_timeout, sizeof(int)) != cudaSuccess) return KV_ERR_CUDA;
+    if (!flag) return KV_OK;
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_conv_timeout, &zero, sizeof(int));
+    return KV_ERR_TIMEOUT;
+}
 kv_status nn_flip(int cin, int cout, const void *W, void *Wt, cudaStream_t s) {
     k_flip_weights<<<64, 256, 0, s>>>((const bf16 *)W, (bf16 *)Wt, cin, cout);
     return cudaGetLastError() == cudaSuccess ? KV_OK : KV_ERR_CUDA;
