@@ -48,9 +48,35 @@ struct Conv {
 };
 
 // ---- elementwise kernels (channel-last BF16) -------------------------------
+// Channel-last tensors move in 16-byte vectors of 8 channels (C is 16, 32 or 64).
+__device__ __forceinline__ void unpack8(const uint4 &q, float (&f)[8]) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 t = __bfloat1622float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 q;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    return q;
+}
+#define KV_GRID_LOOP(e, n) \
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (n); e += (long long)gridDim.x * blockDim.x)
+
 __global__ void k_in_prep(const float *__restrict__ b, bf16 *__restrict__ x, long long V, float s) {
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
-        for (int c = 0; c < kIO; ++c) x[v * kIO + c] = __float2bfloat16_rn(c == 0 ? b[v] * s : 0.f);
+    KV_GRID_LOOP(v, V) {
+        float f[8] = {b[v] * s, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint4 *o = reinterpret_cast<uint4 *>(x + v * kIO);
+        o[0] = pack8(f);
+        f[0] = 0.f;
+#pragma unroll
+        for (int c = 1; c < kIO / 8; ++c) o[c] = pack8(f);
+    }
 }
 
 __global__ void k_sumsq(const float *__restrict__ a, long long V, double *out) {
@@ -85,81 +111,115 @@ __global__ void k_out_extract(const float *__restrict__ y, float *__restrict__ p
     }
 }
 
-// avg pool 2x2x2 (ceil sizes; averages over the children that exist)
+// avg pool 2x2x2 (ceil sizes; averages over the children that exist); one
+// 8-channel vector per item
 __global__ void k_pool(const bf16 *__restrict__ a, bf16 *__restrict__ o, Dims da, Dims dout, int C) {
-    const long long n = dout.v() * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
+    const int nv = C / 8;
+    KV_GRID_LOOP(e, dout.v() * nv) {
+        const int cv = (int)(e % nv);
+        const long long v = e / nv;
         const int i = (int)(v % dout.x), j = (int)((v / dout.x) % dout.y), k = (int)(v / ((long long)dout.x * dout.y));
-        float s = 0.f;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
         for (int dz = 0; dz < 2; ++dz)
             for (int dy = 0; dy < 2; ++dy)
                 for (int dx = 0; dx < 2; ++dx) {
                     const int x = 2 * i + dx, y = 2 * j + dy, z = 2 * k + dz;
                     if (x < da.x && y < da.y && z < da.z) {
-                        s += __bfloat162float(a[(((long long)z * da.y + y) * da.x + x) * C + c]);
+                        float f[8];
+                        unpack8(reinterpret_cast<const uint4 *>(a + (((long long)z * da.y + y) * da.x + x) * C)[cv], f);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) s[q] += f[q];
                         ++cnt;
                     }
                 }
-        o[e] = __float2bfloat16_rn(s / (float)cnt);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s[q] /= (float)cnt;
+        reinterpret_cast<uint4 *>(o)[e] = pack8(s);
     }
 }
 
-// gradient of the pool: ga[child] += g[parent] / count(parent)
+// gradient of the pool: ga[child] (+)= g[parent] / count(parent)
 __global__ void k_pool_bwd(const bf16 *__restrict__ g, bf16 *__restrict__ ga, Dims da, Dims dg, int C, int accumulate) {
-    const long long n = da.v() * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
+    const int nv = C / 8;
+    KV_GRID_LOOP(e, da.v() * nv) {
+        const int cv = (int)(e % nv);
+        const long long v = e / nv;
         const int x = (int)(v % da.x), y = (int)((v / da.x) % da.y), z = (int)(v / ((long long)da.x * da.y));
         const int i = x / 2, j = y / 2, k = z / 2;
         const int cnt = (min(2 * i + 2, da.x) - 2 * i) * (min(2 * j + 2, da.y) - 2 * j) * (min(2 * k + 2, da.z) - 2 * k);
-        float val = __bfloat162float(g[(((long long)k * dg.y + j) * dg.x + i) * C + c]) / (float)cnt;
-        if (accumulate) val += __bfloat162float(ga[e]);
-        ga[e] = __float2bfloat16_rn(val);
+        float val[8];
+        unpack8(reinterpret_cast<const uint4 *>(g + (((long long)k * dg.y + j) * dg.x + i) * C)[cv], val);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) val[q] /= (float)cnt;
+        if (accumulate) {
+            float f[8];
+            unpack8(reinterpret_cast<const uint4 *>(ga)[e], f);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) val[q] += f[q];
+        }
+        reinterpret_cast<uint4 *>(ga)[e] = pack8(val);
     }
 }
 
 // nearest upsample: o[child] = a[parent]
 __global__ void k_up(const bf16 *__restrict__ a, bf16 *__restrict__ o, Dims da, Dims dout, int C) {
-    const long long n = dout.v() * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
+    const int nv = C / 8;
+    KV_GRID_LOOP(e, dout.v() * nv) {
+        const int cv = (int)(e % nv);
+        const long long v = e / nv;
         const int x = (int)(v % dout.x), y = (int)((v / dout.x) % dout.y), z = (int)(v / ((long long)dout.x * dout.y));
-        o[e] = a[(((long long)(z / 2) * da.y + y / 2) * da.x + x / 2) * C + c];
+        reinterpret_cast<uint4 *>(o)[e] =
+            reinterpret_cast<const uint4 *>(a + (((long long)(z / 2) * da.y + y / 2) * da.x + x / 2) * C)[cv];
     }
 }
 
 // gradient of the upsample: ga[parent] = sum over its children of g[child]
 __global__ void k_up_bwd(const bf16 *__restrict__ g, bf16 *__restrict__ ga, Dims da, Dims dg, int C) {
-    const long long n = da.v() * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
+    const int nv = C / 8;
+    KV_GRID_LOOP(e, da.v() * nv) {
+        const int cv = (int)(e % nv);
+        const long long v = e / nv;
         const int i = (int)(v % da.x), j = (int)((v / da.x) % da.y), k = (int)(v / ((long long)da.x * da.y));
-        float s = 0.f;
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int dz = 0; dz < 2; ++dz)
             for (int dy = 0; dy < 2; ++dy)
                 for (int dx = 0; dx < 2; ++dx) {
                     const int x = 2 * i + dx, y = 2 * j + dy, z = 2 * k + dz;
-                    if (x < dg.x && y < dg.y && z < dg.z) s += __bfloat162float(g[(((long long)z * dg.y + y) * dg.x + x) * C + c]);
+                    if (x < dg.x && y < dg.y && z < dg.z) {
+                        float f[8];
+                        unpack8(reinterpret_cast<const uint4 *>(g + (((long long)z * dg.y + y) * dg.x + x) * C)[cv], f);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) s[q] += f[q];
+                    }
                 }
-        ga[e] = __float2bfloat16_rn(s);
+        reinterpret_cast<uint4 *>(ga)[e] = pack8(s);
     }
 }
 
+// o = a + b over n elements (n a multiple of 8)
 __global__ void k_add(const bf16 *__restrict__ a, const bf16 *__restrict__ b, bf16 *__restrict__ o, long long n) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        o[e] = __float2bfloat16_rn(__bfloat162float(a[e]) + __bfloat162float(b[e]));
+    KV_GRID_LOOP(e, n / 8) {
+        float fa[8], fb[8];
+        unpack8(reinterpret_cast<const uint4 *>(a)[e], fa);
+        unpack8(reinterpret_cast<const uint4 *>(b)[e], fb);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) fa[q] += fb[q];
+        reinterpret_cast<uint4 *>(o)[e] = pack8(fa);
+    }
 }
 
 // g *= (y > 0)  (gradient through a ReLU whose output is y)
 __global__ void k_relu_bwd(bf16 *__restrict__ g, const bf16 *__restrict__ y, long long n) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        if (!(__bfloat162float(y[e]) > 0.f)) g[e] = __float2bfloat16_rn(0.f);
+    KV_GRID_LOOP(e, n / 8) {
+        float fg[8], fy[8];
+        unpack8(reinterpret_cast<const uint4 *>(g)[e], fg);
+        unpack8(reinterpret_cast<const uint4 *>(y)[e], fy);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (!(fy[q] > 0.f)) fg[q] = 0.f;
+        reinterpret_cast<uint4 *>(g)[e] = pack8(fg);
+    }
 }
 
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
