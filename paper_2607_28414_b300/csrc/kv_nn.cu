@@ -24,26 +24,26 @@ namespace kv {
 // ---------------------------------------------------------------------------
 // Forward (and input-gradient) convolution on the 5th-generation tensor cores
 //
-// Implicit GEMM: a block computes 2 x (128 voxels x COUT) outputs, the voxels
-// of an 8 (x) x 16 (y) tile on two consecutive z planes. Its input brick
-// (10 x 18 x 4 voxels with the one-voxel halo) is staged once in shared memory
+// Implicit GEMM: a block computes 4 x (128 voxels x COUT) outputs, the voxels
+// of an 8 (x) x 16 (y) tile on four consecutive z planes. Its input brick
+// (10 x 18 x 6 voxels with the one-voxel halo) is staged once in shared memory
 // in the canonical no-swizzle K-major layout of the tensor cores: channels in
 // chunks of 8 (16 bytes), brick[cc][z][y][x][8]. For tap (dx, dy, dz) the A
 // operand (128 voxels x 16 channels) is the brick seen from voxel offset
 // (dx, dy, dz + zt): 8-row core matrices are 8 consecutive x voxels (16-byte
 // rows), the 16 row groups step by one brick row (SBO = 160 bytes), and the two
-// 8-channel halves of K step by one channel chunk (LBO = 720 x 16 bytes). So
+// 8-channel halves of K step by one channel chunk (LBO = 1080 x 16 bytes). So
 // the 27 taps need no gather: each is a descriptor with a different start
 // address. The weights of the 9 taps of one dz are staged per group in the
 // same layout (B: COUT rows x 16 channels, SBO = 128 bytes, LBO = COUT x 16).
 // One thread issues tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators
-// in tensor memory: 2 x COUT columns), commits to an mbarrier, and the four
+// in tensor memory: 4 x COUT columns), commits to an mbarrier, and the four
 // warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes
 // 32w .. 32w + 31 = tile rows) for the bias / ReLU / store epilogue.
 // ---------------------------------------------------------------------------
-constexpr int kTcX = 8, kTcY = 16, kTcZ = 2;                      // 2 x 128 voxels per block
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;                      // 4 x 128 voxels per block
 constexpr int kTcBX = kTcX + 2, kTcBY = kTcY + 2, kTcBZ = kTcZ + 2;
-constexpr int kTcBrick = kTcBX * kTcBY * kTcBZ;                   // 720 voxels with halo
+constexpr int kTcBrick = kTcBX * kTcBY * kTcBZ;                   // 1080 voxels with halo
 
 template <int CIN, int COUT>
 struct ConvTc {
@@ -51,7 +51,8 @@ struct ConvTc {
     static constexpr size_t kTapBytes = (size_t)(CIN / 8) * COUT * 16;
     static constexpr size_t kWBytes = 9 * kTapBytes;
     static constexpr size_t kSmem = kBrickBytes + kWBytes + 16;  // + mbarrier, TMEM address
-    static constexpr uint32_t kCols = 2 * COUT < 32 ? 32 : 2 * COUT;  // power of two >= 32
+    static constexpr uint32_t kCols = kTcZ * COUT < 32 ? 32 : kTcZ * COUT;  // power of two >= 32
+    static_assert(kSmem <= 227 * 1024, "shared memory of a convolution block");
 };
 
 // Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8
