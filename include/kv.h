@@ -29,7 +29,11 @@
  * Streams   Every call is asynchronous on the handle's stream except those
  *           documented as synchronising (kv_create, kv_set_medium,
  *           kv_project_force, kv_read_*, kv_sync). Host inputs are copied
- *           before the call returns, so the caller may reuse them.
+ *           before the call returns, so the caller may reuse them. Device
+ *           inputs and output buffers are accessed on the handle's stream
+ *           only: the caller must have completed (or ordered before that
+ *           stream) any work of its own that writes them, e.g. by creating
+ *           the handle on its own stream or synchronising its stream first.
  * Errors    Every call returns a kv_status and never aborts. A CUDA error, a
  *           device-side timeout or a non-finite CG puts the handle in an
  *           error state; kv_last_error() gives a one-line description.

@@ -214,6 +214,7 @@ kv_status step_prepare(kv_handle *h);                  // TMA maps, smem attribu
 kv_status step_launch(kv_handle *h, int from_buffer);  // one step from state[from]
 kv_status step2_launch(kv_handle *h, int from_buffer); // two steps (variant 2), one buffer swap
 kv_status launch_wait_selftest(kv_handle *h);          // bounded wait on an mbarrier nothing completes
+void *tensor_map_encoder(kv_handle *h);                // cuTensorMapEncodeTiled (NULL if unavailable)
 
 // Step kernel kinds: homogeneous, pointwise heterogeneous (Sec. 3.1),
 // divergence-form heterogeneous.

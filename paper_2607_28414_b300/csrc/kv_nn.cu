@@ -9,6 +9,7 @@
 // W[t][ci][co], tap t = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padding of one voxel:
 //   out[v][co] = bias[co] + sum_{t,ci} in[v + d(t)][ci] W[t][ci][co].
 // The input gradient is the same convolution with Wt[t][co][ci] = W[26-t][ci][co].
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <mma.h>
 
@@ -50,7 +51,7 @@ struct ConvTc {
     static constexpr size_t kBrickBytes = (size_t)(CIN / 8) * kTcBrick * 16;
     static constexpr size_t kTapBytes = (size_t)(CIN / 8) * COUT * 16;
     static constexpr size_t kWBytes = 9 * kTapBytes;
-    static constexpr size_t kSmem = kBrickBytes + kWBytes + 16;  // + mbarrier, TMEM address
+    static constexpr size_t kSmem = kBrickBytes + kWBytes + 24;  // + 2 mbarriers, TMEM address
     static constexpr uint32_t kCols = kTcZ * COUT < 32 ? 32 : kTcZ * COUT;  // power of two >= 32
     static_assert(kSmem <= 227 * 1024, "shared memory of a convolution block");
 };
@@ -107,6 +108,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 __device__ int g_conv_timeout;  // set when a bounded wait of a convolution gave up
 
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
 template <typename OutT>
 __device__ __forceinline__ void store16(OutT *dst, const float (&v)[16]);
 template <>
@@ -129,17 +139,18 @@ __device__ __forceinline__ void store16<bf16>(bf16 *dst, const float (&v)[16]) {
 
 template <int CIN, int COUT, typename OutT>
 __global__ void __launch_bounds__(128)
-k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const float *__restrict__ bias,
+k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ W, const float *__restrict__ bias,
            OutT *__restrict__ out, int nx, int ny, int nz, int relu) {
     using C = ConvTc<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char sm[];
     bf16 *brick = reinterpret_cast<bf16 *>(sm);
     bf16 *wts = reinterpret_cast<bf16 *>(sm + C::kBrickBytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kBrickBytes + C::kWBytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kBrickBytes + C::kWBytes);  // MMA completion
+    uint64_t *bar_in = bar + 1;                                                        // input brick
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int x0 = blockIdx.x * kTcX, y0 = blockIdx.y * kTcY, z0 = blockIdx.z * kTcZ;
-    const uint32_t bar_a = smem_u32(bar);
+    const uint32_t bar_a = smem_u32(bar), bar_b = smem_u32(bar_in);
 
     if (warp == 0) {  // tensor memory for the two accumulators
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -149,17 +160,12 @@ k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const float 
     }
     if (tid == 0) {
         mbar_init(bar_a, 1);
+        mbar_init(bar_b, 1);
         mbar_init_fence();
-    }
-    // input brick, channel-chunked
-    for (int i = tid; i < kTcBrick * (CIN / 8); i += 128) {
-        const int cc = i / kTcBrick, vox = i % kTcBrick;
-        const int bx = vox % kTcBX, by = (vox / kTcBX) % kTcBY, bz = vox / (kTcBX * kTcBY);
-        const int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-            v = *reinterpret_cast<const uint4 *>(in + (((size_t)gz * ny + gy) * nx + gx) * CIN + cc * 8);
-        *reinterpret_cast<uint4 *>(brick + ((size_t)cc * kTcBrick + vox) * 8) = v;
+        // the input brick, channel-chunked [cc][z][y][x][8], by one 5D TMA box
+        // (zero fill outside the grid); the weights are staged meanwhile
+        mbar_expect_tx(bar_b, (uint32_t)C::kBrickBytes);
+        tma_load_5d(smem_u32(brick), &tm_in, 0, x0 - 1, y0 - 1, z0 - 1, 0, bar_b);
     }
     tc_fence_before();
     __syncthreads();
@@ -190,6 +196,7 @@ k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const float 
                 make_uint4(w[0], w[1], w[2], w[3]);
         }
         fence_proxy_async();  // generic-proxy writes of the operands -> tensor-core reads
+        if (g == 0) ok &= mbar_wait_bounded(bar_b, 0);  // the brick has landed
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
@@ -215,7 +222,8 @@ k_conv_fwd(const bf16 *__restrict__ in, const bf16 *__restrict__ W, const float 
     ok &= mbar_wait_bounded(bar_a, phase);
     if (!ok) {
         if (tid == 0) atomicExch(&g_conv_timeout, 1);
-        mbar_wait_bounded(bar_a, phase);  // give in-flight MMAs a second chance before freeing TMEM
+        mbar_wait_bounded(bar_b, 0);      // the brick copy and in-flight MMAs get a second
+        mbar_wait_bounded(bar_a, phase);  // chance before TMEM and shared memory are freed
     }
     tc_fence_after();
     // epilogue: TMEM lane 32w + lane = tile row m = y * 8 + x
@@ -374,8 +382,20 @@ static kv_status launch_fwd_t(int nx, int ny, int nz, const bf16 *in, const bf16
             return KV_ERR_CUDA;
         attr = true;
     }
+    // 5D view of the channel-last input: (8 channels, x, y, z, channel chunk)
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder(nullptr));
+    if (!enc || (reinterpret_cast<uintptr_t>(in) & 15)) return KV_ERR_ARG;
+    CUtensorMap tm;
+    cuuint64_t dims[5] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(CIN / 8)};
+    cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)nx * CIN * 2, (cuuint64_t)nx * ny * CIN * 2, 16};
+    cuuint32_t box[5] = {8, kTcBX, kTcBY, kTcBZ, CIN / 8};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return KV_ERR_CUDA;
     dim3 grid((nx + kTcX - 1) / kTcX, (ny + kTcY - 1) / kTcY, (nz + kTcZ - 1) / kTcZ);
-    k_conv_fwd<CIN, COUT, OutT><<<grid, 128, smem, s>>>(in, W, bias, out, nx, ny, nz, relu);
+    k_conv_fwd<CIN, COUT, OutT><<<grid, 128, smem, s>>>(tm, W, bias, out, nx, ny, nz, relu);
     return cudaGetLastError() == cudaSuccess ? KV_OK : KV_ERR_CUDA;
 }
 

@@ -869,6 +869,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn(kv_handle *h) {
     return fn;
 }
 
+// The driver's tensor-map encoder (also used by the convolution kernels).
+void *tensor_map_encoder(kv_handle *h) { return reinterpret_cast<void *>(encode_fn(h)); }
+
 kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by,
                            int fields_box) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn(h);

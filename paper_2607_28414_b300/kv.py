@@ -161,9 +161,18 @@ def _check(st, h=None):
         raise KvError(st, msg)
 
 
+def _producers_done(t):
+    """libkv works on its handle's own stream, which is not ordered with
+    torch's: wait until the work torch has queued on the tensor's device
+    (which may still be writing `t`, or may later overwrite it) is done."""
+    import torch
+    torch.cuda.current_stream(t.device).synchronize()
+
+
 def field(x, keep):
     """KvField for a scalar, NumPy array or torch tensor (float32, dense,
-    C-contiguous). `keep` collects objects that must outlive the call."""
+    C-contiguous). `keep` collects objects that must outlive the call. A CUDA
+    tensor is complete on torch's current stream before libkv reads it."""
     if x is None:
         return KvField(None, 0.0, KV_SCALAR)
     if isinstance(x, (int, float, np.floating, np.integer)):
@@ -180,6 +189,8 @@ def field(x, keep):
         if x.dtype != torch.float32 or not x.is_contiguous():
             x = x.contiguous().to(torch.float32)
         keep.append(x)
+        if x.is_cuda:
+            _producers_done(x)
         return KvField(x.data_ptr(), 0.0, KV_DEVICE if x.is_cuda else KV_HOST)
     raise TypeError(f"unsupported field type {type(x)}")
 
@@ -192,6 +203,8 @@ def _ptr(x, keep):
     import torch
     if isinstance(x, torch.Tensor):
         keep.append(x)
+        if x.is_cuda:
+            _producers_done(x)
         return x.data_ptr(), (KV_DEVICE if x.is_cuda else KV_HOST)
     raise TypeError(f"unsupported buffer type {type(x)}")
 
@@ -448,6 +461,7 @@ def _dptr(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")
+    _producers_done(t)
     return t.data_ptr()
 
 
