@@ -349,7 +349,8 @@ kv_status kv_get_step_config(kv_handle *h, int *cfg);
 kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms);
 
 /* Launch shape of the FP32 CG passes (Sec. 3.2.3 iteration): zc planes per
- * block of the TMA z-march (0: default 16). A value giving more blocks than
+ * block of the TMA z-march (0: the default, about one wave of blocks:
+ * 148 x 4 blocks of 64 x 8 columns over the grid, between 8 and 128 planes). A value giving more blocks than
  * the handle's reduction buffer holds is refused (KV_ERR_ARG). The arithmetic
  * and its order do not depend on zc except through the order of the block
  * partial sums. kv_get_cg_config: the current zc. */

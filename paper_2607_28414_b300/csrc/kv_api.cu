@@ -572,7 +572,7 @@ kv_status kv_set_cg_config(kv_handle *h, int zc) {
     if (!h || zc < 0) return set_error(h, KV_ERR_ARG, "kv_set_cg_config: invalid arguments");
     if (h->sticky) return KV_ERR_STATE;
     const long long gx = (h->px + 63) / 64, gy = (h->ny - 2 + 7) / 8;
-    const int z = zc > 0 ? zc : 16;
+    const int z = zc > 0 ? zc : cg_auto_zc(h);
     if (gx * gy * ((h->nz - 2 + z - 1) / z) > h->partials_len)
         return set_error(h, KV_ERR_ARG, "kv_set_cg_config: z chunk %d gives too many blocks", zc);
     h->cg_zc = zc;
@@ -581,7 +581,7 @@ kv_status kv_set_cg_config(kv_handle *h, int zc) {
 
 kv_status kv_get_cg_config(kv_handle *h, int *zc) {
     if (!h || !zc) return KV_ERR_ARG;
-    *zc = h->cg_zc > 0 ? h->cg_zc : 16;
+    *zc = h->cg_zc > 0 ? h->cg_zc : cg_auto_zc(h);
     return KV_OK;
 }
 

@@ -253,7 +253,7 @@ k_cg_upd(const T *__restrict__ p0, const T *__restrict__ p1, T *__restrict__ r, 
 // tiles. Per-node arithmetic is the same sequence as the plain kernels above.
 // Reductions: float-float per thread and across the block, double per block.
 // ---------------------------------------------------------------------------
-constexpr int kCgTX = 64, kCgTY = 8, kCgNS = 8, kCgTZc = 16;
+constexpr int kCgTX = 64, kCgTY = 8, kCgNS = 8;
 constexpr int kCgNT = kCgTX * kCgTY / 4;
 constexpr int kCgGX = kCgTX / 4;
 constexpr int kCgBXh = kCgTX + 8, kCgBYh = kCgTY + 2;
@@ -677,6 +677,15 @@ static CgParams cg_params(kv_handle *h, dim3 grid, int zc) {
 
 int cg_zc(const kv_handle *h) { return kCgZc; }
 
+// Default z chunk of the TMA CG passes: about one wave of blocks (148 SMs x 4
+// resident blocks of 64 x 8 columns), at least 8 and at most 128 planes.
+int cg_auto_zc(const kv_handle *h) {
+    const long long cols = (long long)((h->px + kCgTX - 1) / kCgTX) * ((h->ny - 2 + kCgTY - 1) / kCgTY);
+    const long long per_col = std::max(1ll, 592 / std::max(1ll, cols));
+    const long long zc = (h->nz - 2 + per_col - 1) / per_col;
+    return (int)std::min(128ll, std::max(8ll, zc));
+}
+
 dim3 cg_grid(const kv_handle *h) {
     const int zc = cg_zc(h);
     return dim3((h->nx + kCgBX - 1) / kCgBX, (h->ny + kCgBY - 1) / kCgBY, (h->nz + zc - 1) / zc);
@@ -774,7 +783,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     cudaError_t e;
     // FP32: the two CG passes run as TMA-staged z-march kernels
     const bool use_tma = (h->precision == KV_FP32);
-    const int tzc = h->cg_zc > 0 ? h->cg_zc : kCgTZc;
+    const int tzc = h->cg_zc > 0 ? h->cg_zc : cg_auto_zc(h);
     const dim3 tgrid((h->px + kCgTX - 1) / kCgTX, (h->ny - 2 + kCgTY - 1) / kCgTY,
                      (h->nz - 2 + tzc - 1) / tzc);
     CgParams pt = cg_params(h, tgrid, tzc);

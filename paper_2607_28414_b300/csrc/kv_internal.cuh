@@ -239,6 +239,7 @@ kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_ou
 
 // Multigrid preconditioner (kv_mg.cu): level setup and one application
 // z = M r from mg[0].r into cgv field 1, with r.z reduced into scal[kRR].
+int cg_auto_zc(const kv_handle *h);  // default z chunk of the TMA CG passes
 kv_status mg_prepare(kv_handle *h);
 void mg_apply(kv_handle *h, const CgParams &p);
 
