@@ -273,7 +273,10 @@ kv_status kv_attach_net(kv_handle *h, kv_net *net);
  *   kv_nn_conv3d_flip: Wt[t][co][ci] = W[26-t][ci][co] (input gradient =
  *     kv_nn_conv3d_fwd of the output gradient with Wt, cin/cout swapped).
  *   kv_nn_conv3d_bwd_weight: gW[t][ci][co] += sum_v x[v+d(t)][ci] g[v][co],
- *     gb[co] += sum_v g[v][co] (FP32, accumulating; gb may be NULL).
+ *     gb[co] += sum_v g[v][co] (FP32, accumulating with atomics, so the sum
+ *     order and the last bits vary from call to call; gb may be NULL).
+ * x, g, W and gW are device pointers, 16-byte aligned (KV_ERR_ARG otherwise);
+ * the calls are asynchronous on `stream`.
  */
 kv_status kv_nn_conv3d_fwd(int nx, int ny, int nz, int cin, int cout, const void *x, const void *W,
                            const float *bias, void *out, int out_f32, int relu, void *stream);

@@ -1,9 +1,8 @@
 // kv_nn.cu -- tensor-core building blocks of the learned warm start: 3x3x3
-// convolution forward and input gradient as implicit GEMMs on the
-// 5th-generation tensor cores (tcgen05.mma, BF16 operands from shared memory,
-// FP32 accumulators in tensor memory), the weight gradient as an implicit GEMM
-// with WMMA 16x16x16 tiles (its M = CIN is below the 64/128 rows of a tcgen05
-// tile), and the bias gradient and weight flip.
+// convolution forward, input gradient and weight gradient as implicit GEMMs on
+// the 5th-generation tensor cores (tcgen05.mma, BF16 operands staged by TMA in
+// shared memory, FP32 accumulators in tensor memory), and the bias gradient and
+// weight flip.
 //
 // Tensors are channel-last [z][y][x][C] BF16 with C in {16, 32, 64}. Weights
 // W[t][ci][co], tap t = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padding of one voxel:
@@ -11,14 +10,12 @@
 // The input gradient is the same convolution with Wt[t][co][ci] = W[26-t][ci][co].
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
-#include <mma.h>
 
 #include <algorithm>
 
 #include "kv_internal.cuh"
 
 using bf16 = __nv_bfloat16;
-namespace wm = nvcuda::wmma;
 
 namespace kv {
 
@@ -253,95 +250,175 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ W
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient: gW[t][ci][co] += sum_v in[v + d(t)][ci] g[v][co] (FP32),
-// gb[co] += sum_v g[v][co]. Block (chunk, tap) sweeps its rows of 16 voxels.
+// Weight gradient on the 5th-generation tensor cores
+//
+// gW[t][ci][co] = sum_v in[v + d(t)][ci] g[v][co]: a GEMM whose contraction
+// runs over voxels. Both operands are taken MN-major straight from the
+// channel-last tensors: a core matrix is 8 consecutive z voxels (the K rows,
+// 16 bytes apart) x 8 channels (16 contiguous bytes). A block owns one dz
+// (blockIdx.y) and sweeps chunks of XT x YT x 16 voxels. Per chunk, a 2-stage
+// TMA ring lands
+//   the input brick [y (YT+2)][x (XT+2)][channel chunk][z 16][8] from the
+//     planes z + dz (zero fill outside the grid), and
+//   the output-gradient tile [y][x][channel chunk][z 16][8];
+// then, for every voxel column (x, y) and every dy, one thread issues MMAs with
+//   A: 128 rows (dx, ci) = the brick seen from (x + dx, y + dy): consecutive dx
+//      are NCC core matrices apart, so the three dx taps stack along M at one
+//      uniform 256-byte stride (rows beyond 3 CIN are never stored);
+//   B: N = COUT rows co of the gradient at (x, y);
+//   K: the column's 16 z voxels (two core matrices, 128 bytes apart);
+// into FP32 accumulators in tensor memory, one (128 x COUT) block per (dy, row
+// chunk), kept across all chunks of the block. The epilogue reads them with
+// tcgen05.ld and adds them to gW with vector atomics.
 // ---------------------------------------------------------------------------
-constexpr int kWgRows = 8;  // rows of 16 voxels staged per step
+constexpr int kWgZ = 16;  // z voxels per chunk: two core matrices along K
+
+template <int CIN, int COUT, int XT, int YT>
+struct WgradTile {
+    static constexpr int NCC = CIN / 8, NCO = COUT / 8;
+    static constexpr int XB = XT + 2, YB = YT + 2;
+    static constexpr size_t kBrick = (size_t)YB * XB * NCC * kWgZ * 16;
+    static constexpr size_t kGrad = (size_t)YT * XT * NCO * kWgZ * 16;
+    static constexpr size_t kStage = (kBrick + kGrad + 1023) / 1024 * 1024;
+    static constexpr size_t kSmem = 2 * kStage + 64;  // + 4 mbarriers, TMEM address
+    static constexpr bool fits() { return kSmem <= 227 * 1024; }
+};
 
 template <int CIN, int COUT>
-constexpr size_t conv_wgrad_smem() {
-    return (size_t)kWgRows * 16 * (CIN + COUT) * 2 + 8 * 16 * 16 * 4;
-}
+struct WgradTc {
+    // the largest voxel-column tile (8x8, 8x4, 4x4) whose two stages fit in shared memory
+    static constexpr bool k88 = WgradTile<CIN, COUT, 8, 8>::fits(), k84 = WgradTile<CIN, COUT, 8, 4>::fits();
+    static constexpr int TX = (k88 || k84) ? 8 : 4, TY = k88 ? 8 : 4;
+    using T = WgradTile<CIN, COUT, TX, TY>;
+    static constexpr int NQ = (3 * T::NCC + 15) / 16;  // 128-row chunks of the (dx, ci) rows
+    static constexpr int kUsedCols = 3 * NQ * COUT;
+    static constexpr uint32_t kCols = kUsedCols <= 32 ? 32 : kUsedCols <= 64 ? 64 : kUsedCols <= 128 ? 128
+                                    : kUsedCols <= 256 ? 256 : 512;
+    static_assert(T::fits(), "shared memory of a weight-gradient block");
+    static_assert(kUsedCols <= 512, "tensor memory of a weight-gradient block");
+    static_assert(kCols <= 256 || T::kSmem > 114 * 1024, "one block per SM when it takes all tensor memory");
+};
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256)
-k_conv_wgrad(const bf16 *__restrict__ in, const bf16 *__restrict__ g, float *__restrict__ gW,
-             int nx, int ny, int nz, int rows_per_block) {
-    extern __shared__ __align__(128) unsigned char sm[];
-    bf16 *As = reinterpret_cast<bf16 *>(sm);             // [rows][16 voxels][CIN]
-    bf16 *Bs = As + kWgRows * 16 * CIN;                   // [rows][16 voxels][COUT]
-    float *tmp = reinterpret_cast<float *>(Bs + kWgRows * 16 * COUT);  // 8 warps x 16x16
+__global__ void __launch_bounds__(128)
+k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_g,
+                float *__restrict__ gW, int nx, int ny, int nz, int chunks_per_block) {
+    using C = WgradTc<CIN, COUT>;
+    using T = typename C::T;
+    constexpr int TX = C::TX, TY = C::TY, NCC = T::NCC, NCO = T::NCO, NQ = C::NQ;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * T::kStage);  // full[2], empty[2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t = blockIdx.y;
-    const int ddx = t % 3 - 1, ddy = (t / 3) % 3 - 1, ddz = t / 9 - 1;
-    const int xtiles = (nx + 15) / 16;
-    const long long nrows = (long long)xtiles * ny * nz;
-    const long long r0 = (long long)blockIdx.x * rows_per_block;
-    const long long r1 = min(r0 + rows_per_block, nrows);
-    constexpr int NCI = CIN / 16, NCO = COUT / 16, NP = NCI * NCO;
-    constexpr int PPW = (NP + 7) / 8;  // (ci-tile, co-tile) pairs per warp
-    wm::fragment<wm::accumulator, 16, 16, 16, float> acc[PPW];
+    const int dz = (int)blockIdx.y - 1;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntz = (nz + kWgZ - 1) / kWgZ;
+    const long long total = (long long)ntx * nty * ntz;
+    const long long c0 = (long long)blockIdx.x * chunks_per_block;
+    const int n = (int)max(0ll, min((long long)chunks_per_block, total - c0));
+    const uint32_t bar0 = smem_u32(bars), sm0 = smem_u32(sm);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(C::kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) mbar_init(bar0 + 8 * b, 1);
+        mbar_init_fence();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (tid == 0 && n > 0) {
+        auto load = [&](int i, int s) {  // chunk c0 + i into stage s
+            const long long c = c0 + i;
+            const int xt = (int)(c % ntx), yt = (int)((c / ntx) % nty), zt = (int)(c / ((long long)ntx * nty));
+            const int x0 = xt * TX, y0 = yt * TY, z0 = zt * kWgZ;
+            const uint32_t full = bar0 + 8 * s, st = sm0 + (uint32_t)(s * T::kStage);
+            mbar_expect_tx(full, (uint32_t)(T::kBrick + T::kGrad));
+            tma_load_5d(st, &tm_in, 0, z0 + dz, 0, x0 - 1, y0 - 1, full);
+            tma_load_5d(st + (uint32_t)T::kBrick, &tm_g, 0, z0, 0, x0, y0, full);
+        };
+        constexpr uint32_t idesc = umma_idesc_bf16(128, COUT) | (1u << 15) | (1u << 16);  // A, B MN-major
+        int loaded = 0, committed = 0;  // chunks whose copies / MMAs were issued
+        load(0, 0);
+        loaded = 1;
+        for (int i = 0; i < n; ++i) {
+            const int s = i & 1;
+            ok &= mbar_wait_bounded(bar0 + 8 * s, (uint32_t)((i >> 1) & 1));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t brick = sm0 + (uint32_t)(s * T::kStage), grad = brick + (uint32_t)T::kBrick;
+#pragma unroll 1
+            for (int p = 0; p < TX * TY; ++p) {
+                const int y = p / TX, x = p % TX;
+                const uint64_t bd = umma_desc(grad + (uint32_t)(p * NCO * kWgZ * 16), 128, 256);
 #pragma unroll
-    for (int q = 0; q < PPW; ++q) wm::fill_fragment(acc[q], 0.f);
-    for (long long rb = r0; rb < r1; rb += kWgRows) {
-        __syncthreads();
-        constexpr int VA = CIN / 8, VB = COUT / 8;
-        for (int i = tid; i < kWgRows * 16 * (VA + VB); i += 256) {
-            const int isB = i >= kWgRows * 16 * VA;
-            const int ii = isB ? i - kWgRows * 16 * VA : i;
-            const int V8 = isB ? VB : VA;
-            const int rr = ii / (16 * V8), vx = (ii / V8) % 16, part = ii % V8;
-            const long long row = rb + rr;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (row < r1) {
-                const int xt = (int)(row % xtiles);
-                const long long yz = row / xtiles;
-                const int y = (int)(yz % ny), z = (int)(yz / ny);
-                const int x = xt * 16 + vx;
-                if (x < nx) {
-                    if (isB) {
-                        val = *reinterpret_cast<const uint4 *>(g + (((size_t)z * ny + y) * nx + x) * COUT + part * 8);
-                    } else {
-                        const int xx = x + ddx, yy = y + ddy, zz = z + ddz;
-                        if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz)
-                            val = *reinterpret_cast<const uint4 *>(
-                                in + (((size_t)zz * ny + yy) * nx + xx) * CIN + part * 8);
+                for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const uint32_t a = brick + (uint32_t)((((y + dy) * T::XB + x) * NCC + 16 * q) * kWgZ * 16);
+                        umma_bf16(tmem + (uint32_t)((dy * NQ + q) * COUT), umma_desc(a, 128, 256), bd, idesc,
+                                  (i | p) != 0);
                     }
                 }
             }
-            bf16 *dst = isB ? Bs + ((size_t)rr * 16 + vx) * COUT + part * 8
-                            : As + ((size_t)rr * 16 + vx) * CIN + part * 8;
-            *reinterpret_cast<uint4 *>(dst) = val;
+            umma_commit(bar0 + 8 * (2 + s));  // stage s is free once these MMAs are done
+            committed = i + 1;
+            if (i + 1 < n) {
+                if (i >= 1) ok &= mbar_wait_bounded(bar0 + 8 * (2 + (s ^ 1)), (uint32_t)(((i - 1) >> 1) & 1));
+                if (!ok) break;
+                load(i + 1, s ^ 1);
+                loaded = i + 2;
+            }
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PPW; ++q) {
-            const int pidx = warp + 8 * q;
-            if (pidx >= NP) break;
-            const int cit = pidx / NCO, cot = pidx % NCO;
-            for (int rr = 0; rr < kWgRows; ++rr) {
-                wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::col_major> a;  // (ci, voxel)
-                wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> b;  // (voxel, co)
-                wm::load_matrix_sync(a, As + (size_t)rr * 16 * CIN + cit * 16, CIN);
-                wm::load_matrix_sync(b, Bs + (size_t)rr * 16 * COUT + cot * 16, COUT);
-                wm::mma_sync(acc[q], a, b, acc[q]);
+        if (ok) ok = mbar_wait_bounded(bar0 + 8 * (2 + ((n - 1) & 1)), (uint32_t)(((n - 1) >> 1) & 1));
+        if (!ok) {
+            atomicExch(&g_conv_timeout, 1);
+            // the copies and MMAs still in flight get a second chance before the memory is released:
+            // the last chunk loaded into / computed from each stage
+            for (int s = 0; s < 2; ++s) {
+                const int l = loaded - 1 - ((loaded - 1 - s) & 1), c = committed - 1 - ((committed - 1 - s) & 1);
+                if (l >= 0) mbar_wait_bounded(bar0 + 8 * s, (uint32_t)((l >> 1) & 1));
+                if (c >= 0) mbar_wait_bounded(bar0 + 8 * (2 + s), (uint32_t)((c >> 1) & 1));
             }
         }
     }
-    float *mine = tmp + warp * 256;
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (n > 0 && ok) {
+        // TMEM lane m = 32 warp + lane is row m of each accumulator block
+        const int m = 32 * warp + lane;
 #pragma unroll
-    for (int q = 0; q < PPW; ++q) {
-        const int pidx = warp + 8 * q;
-        if (pidx >= NP) break;
-        const int cit = pidx / NCO, cot = pidx % NCO;
-        wm::store_matrix_sync(mine, acc[q], 16, wm::mem_row_major);
-        __syncwarp();
-        for (int e = lane; e < 256; e += 32) {
-            const int ci = cit * 16 + e / 16, co = cot * 16 + e % 16;
-            atomicAdd(gW + ((size_t)t * CIN + ci) * COUT + co, mine[e]);
+        for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int j = 16 * q + m / 8;  // core-matrix row group: (dx, channel chunk)
+                const bool valid = j < 3 * NCC;
+                const int dx = j / NCC, ci = (j % NCC) * 8 + m % 8;
+                const int t = (dz + 1) * 9 + dy * 3 + dx;
+#pragma unroll
+                for (int cb = 0; cb < COUT; cb += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((dy * NQ + q) * COUT + cb), v);
+                    if (valid) {
+                        float4 *dst = reinterpret_cast<float4 *>(gW + ((size_t)t * CIN + ci) * COUT + cb);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            atomicAdd(dst + e, make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]));
+                    }
+                }
+            }
         }
-        __syncwarp();
     }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kCols) : "memory");
 }
 
 // gb[c] += sum_v g[v][c]
@@ -414,20 +491,47 @@ static kv_status launch_fwd(int nx, int ny, int nz, int cin, int cout, const bf1
 template <int CIN, int COUT>
 static kv_status launch_wgrad_t(int nx, int ny, int nz, const bf16 *in, const bf16 *g, float *gW,
                                 cudaStream_t s) {
-    const size_t smem = conv_wgrad_smem<CIN, COUT>();
+    using C = WgradTc<CIN, COUT>;
+    const size_t smem = C::T::kSmem;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_conv_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return KV_ERR_CUDA;
         attr = true;
     }
-    const long long nrows = (long long)((nx + 15) / 16) * ny * nz;
-    const int chunks = (int)std::min<long long>(64, std::max<long long>(1, nrows / kWgRows));
-    int rows_per_block = (int)((nrows + chunks - 1) / chunks);
-    rows_per_block = (rows_per_block + kWgRows - 1) / kWgRows * kWgRows;
-    const int nblk = (int)((nrows + rows_per_block - 1) / rows_per_block);
-    k_conv_wgrad<CIN, COUT><<<dim3(nblk, 27), 256, smem, s>>>(in, g, gW, nx, ny, nz, rows_per_block);
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder(nullptr));
+    if (!enc || (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(g) & 15) ||
+        (reinterpret_cast<uintptr_t>(gW) & 15))
+        return KV_ERR_ARG;
+    // 5D view (8 channels, z, channel chunk, x, y) of a channel-last tensor: a box
+    // lands in shared memory as [y][x][chunk][z][8], the MN-major core matrices
+    auto encode = [&](CUtensorMap *tm, const bf16 *base, int ch, int bx, int by) {
+        cuuint64_t dims[5] = {8, (cuuint64_t)nz, (cuuint64_t)(ch / 8), (cuuint64_t)nx, (cuuint64_t)ny};
+        cuuint64_t strides[4] = {(cuuint64_t)nx * ny * ch * 2, 16, (cuuint64_t)ch * 2, (cuuint64_t)nx * ch * 2};
+        cuuint32_t box[5] = {8, (cuuint32_t)kWgZ, (cuuint32_t)(ch / 8), (cuuint32_t)bx, (cuuint32_t)by};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap tm_in, tm_g;
+    if (!encode(&tm_in, in, CIN, C::TX + 2, C::TY + 2) || !encode(&tm_g, g, COUT, C::TX, C::TY))
+        return KV_ERR_CUDA;
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+    }
+    // one wave: a block per SM (the two stages fill its shared memory), a third of them per dz
+    const long long total = (long long)((nx + C::TX - 1) / C::TX) * ((ny + C::TY - 1) / C::TY) *
+                            ((nz + kWgZ - 1) / kWgZ);
+    const long long per_dz = std::max(1, sms / 3);
+    const int cpb = (int)((total + per_dz - 1) / per_dz);
+    const int nblk = (int)((total + cpb - 1) / cpb);
+    k_conv_wgrad_tc<CIN, COUT><<<dim3(nblk, 3), 128, smem, s>>>(tm_in, tm_g, gW, nx, ny, nz, cpb);
     return cudaGetLastError() == cudaSuccess ? KV_OK : KV_ERR_CUDA;
 }
 

@@ -8,6 +8,7 @@ mode 4 (multigrid-preconditioned CG) and mode 5 (learned start with the
 preconditioned CG) at the same tolerance. This module only orchestrates calls through the binding.
 
     python -m paper_2607_28414_b300.learned --train 2000 --train-n 128 --eval 200 --eval-n 256
+    python -m paper_2607_28414_b300.learned --conv-bench 64,64,96 --reps 3   # one layer's kernels
 """
 from __future__ import annotations
 
@@ -106,9 +107,46 @@ def evaluate(net, shape, forces, tol=1e-8, dx=DX, device="cuda:0", modes=(0, 1, 
     return out
 
 
+def conv_bench(cin, cout, n, reps=20, warmup=3, seed=0):
+    """Event-timed forward and weight-gradient convolutions of one layer
+    (cin -> cout channels on n^3 voxels, random BF16 tensors) on the current
+    stream: mean ms per call and TFLOP/s (2 n^3 27 cin cout per call)."""
+    import torch
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    shape = (n, n, n)
+    x = torch.randn((n, n, n, cin), device=dev, generator=gen).to(torch.bfloat16)
+    g = torch.randn((n, n, n, cout), device=dev, generator=gen).to(torch.bfloat16)
+    W = (0.1 * torch.randn((27, cin, cout), device=dev, generator=gen)).to(torch.bfloat16)
+    y = torch.empty((n, n, n, cout), device=dev, dtype=torch.bfloat16)
+    gW = torch.zeros((27, cin, cout), device=dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    flop = 2.0 * n ** 3 * 27 * cin * cout
+    out = {"cin": cin, "cout": cout, "n": n, "reps": reps}
+    for name, fn in (("fwd", lambda: kv.kv_nn_conv3d_fwd(shape, cin, cout, x, W, None, y, stream=st)),
+                     ("wgrad", lambda: kv.kv_nn_conv3d_bwd_weight(shape, cin, cout, x, g, gW, stream=st))):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(reps):
+            fn()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        out[f"{name}_ms"] = ms
+        out[f"{name}_tflops"] = flop / ms / 1e9
+    return out
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
+    ap.add_argument("--conv-bench", default=None, metavar="CIN,COUT,N",
+                    help="time one layer's forward and weight-gradient kernels and exit")
+    ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--train-n", type=int, default=128)
     ap.add_argument("--eval", type=int, default=200)
@@ -119,6 +157,10 @@ def main():
     ap.add_argument("--seed", type=int, default=104)
     ap.add_argument("--out", default=None, help="write the trained parameters (.npy)")
     args = ap.parse_args()
+    if args.conv_bench:
+        cin, cout, n = (int(v) for v in args.conv_bench.split(","))
+        print(json.dumps(conv_bench(cin, cout, n, reps=args.reps)))
+        return
     device = torch.device("cuda:0")
     tshape = (args.train_n,) * 3
     eshape = (args.eval_n,) * 3

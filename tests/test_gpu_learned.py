@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-SHAPE = (21, 10, 7)  # not a multiple of the 16 x 4 x 2 voxel tile
+SHAPE = (21, 10, 7)  # a multiple of no convolution tile in any axis
 
 
 def bf16_tensor(rng, shape, device, scale=1.0):
@@ -46,10 +46,15 @@ def test_conv_forward_matches_oracle(device, cin, cout):
     assert np.abs(to64(out16) - np.maximum(ref, 0)).max() <= 5e-3 * scale
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (64, 16)])
-def test_conv_gradients_match_oracle(device, cin, cout):
-    rng = np.random.default_rng(7 + cin + cout)
-    nx, ny, nz = SHAPE
+@pytest.mark.parametrize("cin,cout,shape", [
+    (16, 16, SHAPE), (16, 32, SHAPE), (16, 64, SHAPE), (32, 16, SHAPE), (32, 32, SHAPE), (32, 64, SHAPE),
+    (64, 16, SHAPE), (64, 32, SHAPE), (64, 64, SHAPE),
+    # several chunks of 8 x 8 (x 4) x 16 voxels per block, ragged in x, y and z
+    (16, 16, (61, 37, 35)), (32, 32, (29, 23, 41)), (64, 64, (26, 21, 37)),
+])
+def test_conv_gradients_match_oracle(device, cin, cout, shape):
+    rng = np.random.default_rng(7 + cin + cout + shape[2])
+    nx, ny, nz = shape
     x = bf16_tensor(rng, (nz, ny, nx, cin), device)
     W = bf16_tensor(rng, (27, cin, cout), device, 0.1)
     g = bf16_tensor(rng, (nz, ny, nx, cout), device)
@@ -57,11 +62,11 @@ def test_conv_gradients_match_oracle(device, cin, cout):
     Wt = torch.empty((27, cout, cin), dtype=torch.bfloat16, device=device)
     kv.kv_nn_conv3d_flip(cin, cout, W, Wt)
     gin = torch.empty((nz, ny, nx, cin), dtype=torch.float32, device=device)
-    kv.kv_nn_conv3d_fwd(SHAPE, cout, cin, g, Wt, None, gin)
+    kv.kv_nn_conv3d_fwd(shape, cout, cin, g, Wt, None, gin)
     assert np.abs(gin.cpu().numpy() - gin_ref).max() <= 1e-4 * np.abs(gin_ref).max()
     gW = torch.zeros((27, cin, cout), dtype=torch.float32, device=device)
     gb = torch.zeros(cout, dtype=torch.float32, device=device)
-    kv.kv_nn_conv3d_bwd_weight(SHAPE, cin, cout, x, g, gW, gb)
+    kv.kv_nn_conv3d_bwd_weight(shape, cin, cout, x, g, gW, gb)
     assert np.abs(gW.cpu().numpy() - gW_ref).max() <= 1e-4 * np.abs(gW_ref).max()
     assert np.abs(gb.cpu().numpy() - gb_ref).max() <= 1e-4 * np.abs(gb_ref).max()
 
