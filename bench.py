@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 N_TIME_STEPS = 2000
 GRID = 256
 STEP_BYTES_PER_CELL = 56  # (u, d) read + write 48 B, coefficients A', B' 8 B
+CLASS_STEP_BYTES_PER_CELL = 49  # (u, d) 48 B + one class byte (class-encoded medium)
 DIV_STEP_BYTES_PER_CELL = 60  # divergence form: coefficients m, e, 1/rho 12 B
 FORCE_BYTES_PER_CELL = 12  # projected force on force steps
 PLAIN_CG_ITERS = {"inclusions256": 874, "bone512": 1621, "sweep": 557}
@@ -65,19 +66,19 @@ def job_rate(world, cell_updates_per_rank, t_max):
     return world * cell_updates_per_rank / t_max / 1e9
 
 
-def step_traffic(w, step_cfg, operator, n_force_steps):
+def step_traffic(w, step_cfg, operator, n_force_steps, medium="fields"):
     """DRAM bytes per step launch from the committed ncu capture
     (profiles/kv_step_traffic.json: dram__bytes_read.sum + dram__bytes_write.sum
     of force and plain steps), averaged over this pass's launches like
-    `achieved`; None unless the capture is of this grid, operator and kernel
-    configuration."""
+    `achieved`; None unless the capture is of this grid, operator, medium
+    encoding ("fields" or "classes") and kernel configuration."""
     tfile = os.path.join(ROOT, "profiles", "kv_step_traffic.json")
     if not os.path.exists(tfile):
         return None
     try:
         for c in json.load(open(tfile))["captures"]:
             if (c["grid"] == [w.nx, w.ny, w.nz] and c["operator"] == operator
-                    and c["step_config"] == step_cfg):
+                    and c.get("medium", "fields") == medium and c["step_config"] == step_cfg):
                 nf = n_force_steps
                 return (nf * c["bytes_force_step"] + (w.n_steps - nf) * c["bytes_plain_step"]) / w.n_steps
     except (KeyError, ValueError, TypeError):
@@ -101,6 +102,10 @@ def parse():
     ap.add_argument("--operator", default="pointwise", choices=["pointwise", "divergence"],
                     help="spatial operator of the heterogeneous step: pointwise (G/rho) L u "
                          "(Sec. 3.1) or the flux form (1/rho) div(G grad u)")
+    ap.add_argument("--medium-encoding", default="fields", choices=["auto", "fields"],
+                    help="auto: a medium of at most 256 distinct (A', B') pairs is read as one "
+                         "class byte per node (bit for bit the same step); fields: always read "
+                         "the two coefficient fields")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
     ap.add_argument("--step-config", default=None,
@@ -392,7 +397,8 @@ def main():
     h = kv.kv_create(w.nx, w.ny, w.nz, w.dx, dt, *medium_d, stream=stream.cuda_stream)
     if div:
         kv.kv_set_operator(h, kv.KV_OP_DIVERGENCE, *medium_d)
-    bytes_per_cell = DIV_STEP_BYTES_PER_CELL if div else STEP_BYTES_PER_CELL
+    kv.kv_set_medium_encoding(h, kv.KV_MEDIUM_AUTO if args.medium_encoding == "auto"
+                              else kv.KV_MEDIUM_FIELDS)
     if args.step_config:
         vals = [int(v) for v in args.step_config.split(",")]
         variant, (tx, ty, zc, ns) = (vals[0], vals[1:]) if len(vals) == 5 else (0, vals)
@@ -401,6 +407,10 @@ def main():
     else:
         tune_ms = kv.kv_autotune_step(h, 8)  # picks tile / stages / z chunk; resets the state
     step_cfg = kv.kv_get_step_config(h)
+    classes = kv.kv_medium_classes(h) if step_cfg["variant"] == 0 else 0
+    medium_enc = "classes" if classes > 0 else "fields"
+    bytes_per_cell = (DIV_STEP_BYTES_PER_CELL if div else
+                      CLASS_STEP_BYTES_PER_CELL if classes > 0 else STEP_BYTES_PER_CELL)
     if args.cg_config is not None:
         kv.kv_set_cg_config(h, args.cg_config)
         cg_tune_ms = None
@@ -469,7 +479,7 @@ def main():
         / w.n_steps
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = step_traffic(w, step_cfg, args.operator, n_force_steps)
+    traffic = step_traffic(w, step_cfg, args.operator, n_force_steps, medium_enc)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -525,6 +535,8 @@ def main():
                                   if args.workload == "inclusions256" else
                                   "bone shell over smooth soft tissue (seed 105), speckled beam"),
                        "operator": args.operator,
+                       "medium_encoding": (f"{classes} classes: 1 byte per node + (A', B') table"
+                                           if classes > 0 else "coefficient fields A', B' (FP32)"),
                        "projection": ("CG preconditioned by a multigrid V(1,1)-cycle (mode 4)"
                                       if proj_mode == 4 else "plain CG from zero (mode 0)"),
                        "reductions": "f64", "parallelism": f"replicas{world}",

@@ -175,7 +175,8 @@ kv_status fold(kv_handle *h, const kv_field &G, const kv_field &rho, const kv_fi
     for (int q = 0; q < 3; ++q) ptr[q] = fs[q]->where != KV_SCALAR ? h->fstage + q * h->Np : nullptr;
     kv_status st = launch_fold(h, ptr[0], G.value, ptr[1], rho.value, ptr[2], eta.value);
     if (st != KV_OK) return st;
-    return cuda_check(h, cudaStreamSynchronize(h->stream), "medium fold");
+    if ((st = cuda_check(h, cudaStreamSynchronize(h->stream), "medium fold")) != KV_OK) return st;
+    return medium_classify(h);
 }
 
 // Copy the medium's dense fields (host or device) into the handle's pitched
@@ -249,6 +250,7 @@ kv_status kv_destroy(kv_handle *h) {
     if (!h) return KV_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_graphs(h);
+    medium_labels_free(h);
     void *dev[] = {h->state[0], h->state[1], h->F, h->coef, h->S, h->g_dev, h->sens_dev,
                    h->traces, h->ctrl, h->cgv, h->phi, h->b, h->scal,
                    h->partials, h->fstage, h->dtmin, h->mg_pool};
@@ -307,6 +309,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     h->esize = precision == KV_FP64 ? 8 : 4;
     h->het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
     h->op = KV_OP_POINTWISE;
+    h->medium_encoding = KV_MEDIUM_FIELDS;
     h->variant = 0;
     h->tx = 64;
     h->ty = 8;
@@ -387,6 +390,21 @@ kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta) {
     free_graphs(h);
     return fold(h, G, rho, eta);
 }
+
+kv_status kv_set_medium_encoding(kv_handle *h, int encoding) {
+    if (!h) return KV_ERR_ARG;
+    if (h->sticky) return KV_ERR_STATE;
+    if (encoding != KV_MEDIUM_AUTO && encoding != KV_MEDIUM_FIELDS)
+        return set_error(h, KV_ERR_ARG, "kv_set_medium_encoding: unknown encoding %d", encoding);
+    kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_medium_encoding");
+    if (st != KV_OK) return st;
+    h->medium_encoding = encoding;
+    free_graphs(h);
+    h->tma_ready = 0;
+    return medium_classify(h);  // the folded fields are still there
+}
+
+int kv_medium_classes(kv_handle *h) { return h ? h->n_labels : -1; }
 
 kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_field eta) {
     if (!h) return KV_ERR_ARG;

@@ -75,6 +75,8 @@ struct StepParams {
     int cap;
     int zc;              // planes per block (z chunk)
     int nblocks;         // blocks in the launch
+    const float2 *lab_tab;  // (A', B') per class (kKindLabel)
+    int n_lab;
 };
 
 // One case of a batched step (device table entry; CUtensorMap carries its own
@@ -133,6 +135,11 @@ struct kv_handle {
     double A_s, B_s, S_s;  // homogeneous scalars (A, B already divided by dx^2)
     void *coef;            // het: [2][Np] (A', B') pointwise, [3][Np] (m, e, 1/rho) divergence form
     int coef_fields;       // fields allocated in coef
+    unsigned char *labels; // [Np] class of each node's (A', B') pair when n_labels > 0
+    float2 *lab_tab;       // [kMaxLabels] (A', B') of each class
+    unsigned long long *lab_keys;  // classification scratch: hash slots, slot ids, counters
+    int n_labels;          // distinct (A', B') pairs of a pointwise FP32 medium (0: fields are read)
+    int medium_encoding;   // KV_MEDIUM_AUTO / KV_MEDIUM_FIELDS
     void *S;               // [Np] dt^2/rho when het
     double dt_max;
 
@@ -218,9 +225,15 @@ void *tensor_map_encoder(kv_handle *h);                // cuTensorMapEncodeTiled
 
 // Step kernel kinds: homogeneous, pointwise heterogeneous (Sec. 3.1),
 // divergence-form heterogeneous.
-enum { kKindHomo = 0, kKindPoint = 1, kKindDiv = 2 };
+enum { kKindHomo = 0, kKindPoint = 1, kKindDiv = 2, kKindLabel = 3 };
 inline int step_kind(const kv_handle *h) {
     return !h->het ? kKindHomo : (h->op == KV_OP_DIVERGENCE ? kKindDiv : kKindPoint);
+}
+// Kind of the single-step TMA kernel: a pointwise medium with few distinct
+// (A', B') pairs is read as one class byte per node plus a table (kKindLabel).
+inline int tma_kind(const kv_handle *h) {
+    const int k = step_kind(h);
+    return (k == kKindPoint && h->n_labels > 0) ? kKindLabel : k;
 }
 
 // Batched step (kv_step.cu)
@@ -233,6 +246,15 @@ kv_status batch_launch(void *kernel, const struct BatchCase *table, int ncases, 
 // 4D float32 tensor map over [fields][nz][ny][px] with box (bx, by, 1, fields_box)
 kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by,
                            int fields_box);
+
+// Class encoding of a pointwise FP32 medium (kv_label.cu): after the fold,
+// count the distinct (A', B') pairs; with at most kMaxLabels of them, write
+// one class byte per node and the class table, else read the fields.
+// Synchronises the handle's stream. medium_labels_free releases the arrays.
+constexpr int kMaxLabels = 256;
+constexpr int kLabSlots = 1024;  // open-addressing slots of the pair hash
+kv_status medium_classify(kv_handle *h);
+void medium_labels_free(kv_handle *h);
 
 // Projection kernels (kv_cg.cu)
 kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_out, kv_cg_stats *st);

@@ -149,7 +149,10 @@ struct TmaTile {
     static constexpr int BY = TY + 2;
     static constexpr int FIELD = BX * BY;
     static constexpr int STATE = 6 * FIELD;
-    static constexpr int COEF = K == kKindPoint ? 2 * TX * TY : K == kKindDiv ? 3 * FIELD : 0;
+    static constexpr int COEF = K == kKindPoint   ? 2 * TX * TY
+                                : K == kKindDiv   ? 3 * FIELD
+                                : K == kKindLabel ? TX * TY / 4  // one class byte per node
+                                                  : 0;
     static constexpr int STAGE = (STATE + COEF + 31) / 32 * 32;  // floats, 128 B multiple
 };
 
@@ -221,6 +224,10 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
     const bool force = (g != 0.f);
     const uint32_t bar0 = smem_u32(bars);
 
+    // class table of a class-encoded medium: (A', B') of every class
+    __shared__ float2 s_tab[K == kKindLabel ? kMaxLabels : 1];
+    if (K == kKindLabel)
+        for (int i = threadIdx.x; i < p.n_lab; i += TT::NT) s_tab[i] = p.lab_tab[i];
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
         mbar_init_fence();
@@ -231,11 +238,12 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
         const int s = (q - kb) % NS;
         float *st = smem + s * TT::STAGE;
         const uint32_t bar = bar0 + 8 * s;
-        const bool wc = (K == kKindPoint && q >= k0 && q < k1) || K == kKindDiv;
+        const bool wc = ((K == kKindPoint || K == kKindLabel) && q >= k0 && q < k1) || K == kKindDiv;
         const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0);
         mbar_expect_tx(bar, bytes);
         tma_load_4d(smem_u32(st), tm_in, x0 - 4, y0 - 1, q, 0, bar);
-        if (K == kKindPoint && wc) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0, y0, q, 0, bar);
+        if ((K == kKindPoint || K == kKindLabel) && wc)
+            tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0, y0, q, 0, bar);
         if (K == kKindDiv) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0 - 4, y0 - 1, q, 0, bar);
     };
 
@@ -364,6 +372,13 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
             if (K == kKindPoint) {
                 A4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + gy * TX + 4 * gx);
                 B4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + TX * TY + gy * TX + 4 * gx);
+            } else if (K == kKindLabel) {
+                const uint32_t l4 = *reinterpret_cast<const uint32_t *>(
+                    reinterpret_cast<const unsigned char *>(sc + TT::STATE) + gy * TX + 4 * gx);
+                const float2 c0 = s_tab[l4 & 255u], c1 = s_tab[(l4 >> 8) & 255u];
+                const float2 c2 = s_tab[(l4 >> 16) & 255u], c3 = s_tab[l4 >> 24];
+                A4 = make_float4(c0.x, c1.x, c2.x, c3.x);
+                B4 = make_float4(c0.y, c1.y, c2.y, c3.y);
             } else {
                 A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
                 B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
@@ -906,6 +921,7 @@ static bool pick(int tx, int ty, int ns, int kind, TmaKernel *k, size_t *smem, i
         case kKindHomo: pick_kind<TX, TY, NS, kKindHomo>(k, smem); break;
         case kKindPoint: pick_kind<TX, TY, NS, kKindPoint>(k, smem); break;
         case kKindDiv: pick_kind<TX, TY, NS, kKindDiv>(k, smem); break;
+        case kKindLabel: pick_kind<TX, TY, NS, kKindLabel>(k, smem); break;
         default: return false;
     }
     *nt = TX * TY / 4;
@@ -983,11 +999,29 @@ static bool tma_kernel_for(int tx, int ty, int ns, int kind, TmaKernel *k, size_
     }
 }
 
+// Tensor map of the class bytes [nz][ny][px] of a class-encoded medium, box
+// (tx, ty, 1, 1): the centre tile of one plane (tx bytes, a multiple of 16).
+static kv_status encode_labels(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
+    auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder(h));
+    if (!fn) return set_error(h, KV_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[4] = {(cuuint64_t)h->px, (cuuint64_t)h->ny, (cuuint64_t)h->nz, 1};
+    cuuint64_t strides[3] = {(cuuint64_t)h->px, (cuuint64_t)h->px * h->ny, (cuuint64_t)h->Np};
+    cuuint32_t box[4] = {(cuuint32_t)tx, (cuuint32_t)ty, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, h->labels, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(h, KV_ERR_CUDA, "cuTensorMapEncodeTiled (classes) failed (%d) box %dx%d", (int)r, tx, ty);
+    return KV_OK;
+}
+
 // Tensor map of the coefficient fields for a tile (tx, ty): the centre tile
 // of (A', B') for the pointwise operator, the haloed tile of (m, e, 1/rho)
 // for the divergence form; unused placeholder for a homogeneous medium.
 static kv_status encode_coef_map(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
-    switch (step_kind(h)) {
+    switch (tma_kind(h)) {
+        case kKindLabel: return encode_labels(h, tm, tx, ty);
         case kKindPoint: return encode_tensor_4d(h, tm, h->coef, 2, tx, ty, 2);
         case kKindDiv: return encode_tensor_4d(h, tm, h->coef, 3, tx + 8, ty + 2, 3);
         default: *tm = h->tm_state[0]; return KV_OK;
@@ -1021,12 +1055,13 @@ kv_status step_prepare(kv_handle *h) {
         h->tma_ready = 1;
         return KV_OK;
     }
-    if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, step_kind(h), &k, &smem, &nt))
+    if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, tma_kind(h), &k, &smem, &nt))
         return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d with %d stages", h->tx,
                          h->ty, h->ns_stages);
-    if (smem > 227 * 1024)
+    const size_t static_smem = tma_kind(h) == kKindLabel ? kMaxLabels * sizeof(float2) : 0;  // class table
+    if (smem + static_smem > 227 * 1024)
         return set_error(h, KV_ERR_ARG, "tile %dx%d with %d stages needs %zu bytes of shared memory",
-                         h->tx, h->ty, h->ns_stages, smem);
+                         h->tx, h->ty, h->ns_stages, smem + static_smem);
     kv_status st;
     for (int b = 0; b < 2; ++b)
         if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 2, 6)) != KV_OK)
@@ -1060,6 +1095,8 @@ static StepParams make_params(kv_handle *h, int nblocks) {
     p.cap = h->cap;
     p.zc = h->zc;
     p.nblocks = nblocks;
+    p.lab_tab = h->lab_tab;
+    p.n_lab = h->n_labels;
     return p;
 }
 
@@ -1092,7 +1129,7 @@ kv_status step_launch(kv_handle *h, int from) {
         TmaKernel k;
         size_t smem;
         int nt;
-        tma_kernel_for(h->tx, h->ty, h->ns_stages, step_kind(h), &k, &smem, &nt);
+        tma_kernel_for(h->tx, h->ty, h->ns_stages, tma_kind(h), &k, &smem, &nt);
         dim3 grid((h->px + h->tx - 1) / h->tx, (h->ny - 2 + h->ty - 1) / h->ty,
                   (h->nz - 2 + h->zc - 1) / h->zc);
         StepParams p = make_params(h, grid.x * grid.y * grid.z);

@@ -37,6 +37,8 @@ KV_HOST = 1
 KV_DEVICE = 2
 KV_OP_POINTWISE = 0
 KV_OP_DIVERGENCE = 1
+KV_MEDIUM_AUTO = 0
+KV_MEDIUM_FIELDS = 1
 
 FIELD_U, FIELD_D, FIELD_PHI, FIELD_F = 0, 1, 2, 3
 
@@ -87,6 +89,9 @@ def lib():
         L.kv_load_state.argtypes = [H, vp, i, ctypes.c_longlong]
         L.kv_stable_dt_op.argtypes = [i, i, i, d, F, F, F, i, ctypes.POINTER(d)]
         L.kv_set_operator.argtypes = [H, i, F, F, F]
+        L.kv_set_medium_encoding.argtypes = [H, i]
+        L.kv_medium_classes.argtypes = [H]
+        L.kv_medium_classes.restype = i
         L.kv_set_envelope.argtypes = [H, vp, i, i]
         L.kv_set_sensors.argtypes = [H, vp, i, i]
         L.kv_reset.argtypes = [H]
@@ -242,6 +247,16 @@ def kv_set_medium(h, G, rho, eta):
 def kv_set_operator(h, op, G, rho, eta):
     keep = []
     _check(lib().kv_set_operator(h, int(op), field(G, keep), field(rho, keep), field(eta, keep)), h)
+
+
+def kv_set_medium_encoding(h, encoding):
+    """KV_MEDIUM_AUTO (class bytes for a medium of at most 256 (A', B') pairs) or KV_MEDIUM_FIELDS."""
+    _check(lib().kv_set_medium_encoding(h, int(encoding)), h)
+
+
+def kv_medium_classes(h):
+    """Number of medium classes the step reads (0: the coefficient fields)."""
+    return int(lib().kv_medium_classes(h))
 
 
 def kv_selftest_wait(h):
