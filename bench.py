@@ -102,7 +102,7 @@ def parse():
     ap.add_argument("--operator", default="pointwise", choices=["pointwise", "divergence"],
                     help="spatial operator of the heterogeneous step: pointwise (G/rho) L u "
                          "(Sec. 3.1) or the flux form (1/rho) div(G grad u)")
-    ap.add_argument("--medium-encoding", default="fields", choices=["auto", "fields"],
+    ap.add_argument("--medium-encoding", default="auto", choices=["auto", "fields"],
                     help="auto: a medium of at most 256 distinct (A', B') pairs is read as one "
                          "class byte per node (bit for bit the same step); fields: always read "
                          "the two coefficient fields")

@@ -309,7 +309,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     h->esize = precision == KV_FP64 ? 8 : 4;
     h->het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
     h->op = KV_OP_POINTWISE;
-    h->medium_encoding = KV_MEDIUM_FIELDS;
+    h->medium_encoding = KV_MEDIUM_AUTO;
     h->variant = 0;
     h->tx = 64;
     h->ty = 8;
