@@ -75,7 +75,7 @@ struct StepParams {
     int cap;
     int zc;              // planes per block (z chunk)
     int nblocks;         // blocks in the launch
-    const float2 *lab_tab;  // (A', B') per class (kKindLabel)
+    const float4 *lab_tab;  // per class: (A', B', -, -) pointwise, (m, e, 1/rho, -) flux form
     int n_lab;
 };
 
@@ -135,10 +135,10 @@ struct kv_handle {
     double A_s, B_s, S_s;  // homogeneous scalars (A, B already divided by dx^2)
     void *coef;            // het: [2][Np] (A', B') pointwise, [3][Np] (m, e, 1/rho) divergence form
     int coef_fields;       // fields allocated in coef
-    unsigned char *labels; // [Np] class of each node's (A', B') pair when n_labels > 0
-    float2 *lab_tab;       // [kMaxLabels] (A', B') of each class
+    unsigned char *labels; // [Np] class of each node's coefficients when n_labels > 0
+    float4 *lab_tab;       // [kMaxLabels] coefficients of each class (see StepParams)
     unsigned long long *lab_keys;  // classification scratch: hash slots, slot ids, counters
-    int n_labels;          // distinct (A', B') pairs of a pointwise FP32 medium (0: fields are read)
+    int n_labels;          // distinct coefficient tuples of an FP32 medium (0: fields are read)
     int medium_encoding;   // KV_MEDIUM_AUTO / KV_MEDIUM_FIELDS
     void *S;               // [Np] dt^2/rho when het
     double dt_max;
@@ -225,15 +225,18 @@ void *tensor_map_encoder(kv_handle *h);                // cuTensorMapEncodeTiled
 
 // Step kernel kinds: homogeneous, pointwise heterogeneous (Sec. 3.1),
 // divergence-form heterogeneous.
-enum { kKindHomo = 0, kKindPoint = 1, kKindDiv = 2, kKindLabel = 3 };
+enum { kKindHomo = 0, kKindPoint = 1, kKindDiv = 2, kKindLabel = 3, kKindDivLabel = 4 };
 inline int step_kind(const kv_handle *h) {
     return !h->het ? kKindHomo : (h->op == KV_OP_DIVERGENCE ? kKindDiv : kKindPoint);
 }
-// Kind of the single-step TMA kernel: a pointwise medium with few distinct
-// (A', B') pairs is read as one class byte per node plus a table (kKindLabel).
+// Kind of the single-step TMA kernel: a medium with few distinct folded
+// coefficient tuples is read as one class byte per node plus a table
+// (kKindLabel for the pointwise operator, kKindDivLabel for the flux form).
 inline int tma_kind(const kv_handle *h) {
     const int k = step_kind(h);
-    return (k == kKindPoint && h->n_labels > 0) ? kKindLabel : k;
+    if (h->n_labels > 0 && k == kKindPoint) return kKindLabel;
+    if (h->n_labels > 0 && k == kKindDiv) return kKindDivLabel;
+    return k;
 }
 
 // Batched step (kv_step.cu)
@@ -247,9 +250,10 @@ kv_status batch_launch(void *kernel, const struct BatchCase *table, int ncases, 
 kv_status encode_tensor_4d(kv_handle *h, CUtensorMap *tm, void *base, int fields, int bx, int by,
                            int fields_box);
 
-// Class encoding of a pointwise FP32 medium (kv_label.cu): after the fold,
-// count the distinct (A', B') pairs; with at most kMaxLabels of them, write
-// one class byte per node and the class table, else read the fields.
+// Class encoding of an FP32 medium (kv_label.cu): after the fold, count the
+// distinct folded coefficient tuples ((A', B') pointwise, (m, e, 1/rho) flux
+// form); with at most kMaxLabels of them, write one class byte per node and
+// the class table, else read the fields.
 // Synchronises the handle's stream. medium_labels_free releases the arrays.
 constexpr int kMaxLabels = 256;
 constexpr int kLabSlots = 1024;  // open-addressing slots of the pair hash

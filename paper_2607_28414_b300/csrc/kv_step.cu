@@ -149,10 +149,12 @@ struct TmaTile {
     static constexpr int BY = TY + 2;
     static constexpr int FIELD = BX * BY;
     static constexpr int STATE = 6 * FIELD;
-    static constexpr int COEF = K == kKindPoint   ? 2 * TX * TY
-                                : K == kKindDiv   ? 3 * FIELD
-                                : K == kKindLabel ? TX * TY / 4  // one class byte per node
-                                                  : 0;
+    static constexpr int BXB = TX + 32;  // class-byte rows of the flux form: x0-16 .. x0+TX+15
+    static constexpr int COEF = K == kKindPoint      ? 2 * TX * TY
+                                : K == kKindDiv      ? 3 * FIELD
+                                : K == kKindLabel    ? TX * TY / 4   // one class byte per node
+                                : K == kKindDivLabel ? BXB * BY / 4  // class bytes with the halo
+                                                     : 0;
     static constexpr int STAGE = (STATE + COEF + 31) / 32 * 32;  // floats, 128 B multiple
 };
 
@@ -202,6 +204,47 @@ __device__ __forceinline__ void nb_of(const Nb7 &n, int q, float (&v)[6]) {
     v[5] = lane4(n.zp, q);
 }
 
+// Class-encoded flux form: the (m, e, 1/rho) of four consecutive nodes from
+// their four class bytes (one 32-bit word) and the class table.
+__device__ __forceinline__ void class_quad(uint32_t q, const float4 *tab, float4 &m, float4 &e, float4 &r) {
+    const float4 t0 = tab[q & 255u], t1 = tab[(q >> 8) & 255u], t2 = tab[(q >> 16) & 255u], t3 = tab[q >> 24];
+    m = make_float4(t0.x, t1.x, t2.x, t3.x);
+    e = make_float4(t0.y, t1.y, t2.y, t3.y);
+    r = make_float4(t0.z, t1.z, t2.z, t3.z);
+}
+
+// gather7 of m and e (and the centre 1/rho) from class-byte tiles: bc the
+// centre plane, bp the next plane (row stride BXB, this thread's first node at
+// byte offset off); the z-1 neighbours are the previous plane's centre values.
+template <int GX>
+__device__ __forceinline__ void gather7_cls(const unsigned char *bc, const unsigned char *bp, int off, int BXB,
+                                            int gx, const float4 *tab, const float4 &zm_m, const float4 &zm_e,
+                                            Nb7 &m, Nb7 &e, float4 &r4) {
+    float4 unused;
+    class_quad(*reinterpret_cast<const uint32_t *>(bc + off), tab, m.c, e.c, r4);
+    class_quad(*reinterpret_cast<const uint32_t *>(bc + off - BXB), tab, m.ym, e.ym, unused);
+    class_quad(*reinterpret_cast<const uint32_t *>(bc + off + BXB), tab, m.yp, e.yp, unused);
+    class_quad(*reinterpret_cast<const uint32_t *>(bp + off), tab, m.zp, e.zp, unused);
+    m.zm = zm_m;
+    e.zm = zm_e;
+    float lm = __shfl_up_sync(0xffffffffu, m.c.w, 1), rm = __shfl_down_sync(0xffffffffu, m.c.x, 1);
+    float le = __shfl_up_sync(0xffffffffu, e.c.w, 1), re = __shfl_down_sync(0xffffffffu, e.c.x, 1);
+    if (gx == 0) {
+        const float4 t = tab[bc[off - 1]];
+        lm = t.x;
+        le = t.y;
+    }
+    if (gx == GX - 1) {
+        const float4 t = tab[bc[off + 4]];
+        rm = t.x;
+        re = t.y;
+    }
+    m.xm = make_float4(lm, m.c.x, m.c.y, m.c.z);
+    m.xp = make_float4(m.c.y, m.c.z, m.c.w, rm);
+    e.xm = make_float4(le, e.c.x, e.c.y, e.c.z);
+    e.xp = make_float4(e.c.y, e.c.z, e.c.w, re);
+}
+
 // One block's work: the TX x TY column (bx, by) over planes of z chunk bz.
 // tm_in / tm_coef: addresses of tensor maps in parameter or global memory.
 template <int TX, int TY, int NS, int K>
@@ -225,8 +268,9 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
     const uint32_t bar0 = smem_u32(bars);
 
     // class table of a class-encoded medium: (A', B') of every class
-    __shared__ float2 s_tab[K == kKindLabel ? kMaxLabels : 1];
-    if (K == kKindLabel)
+    constexpr bool CLS = K == kKindLabel || K == kKindDivLabel;
+    __shared__ float4 s_tab[CLS ? kMaxLabels : 1];
+    if (CLS)
         for (int i = threadIdx.x; i < p.n_lab; i += TT::NT) s_tab[i] = p.lab_tab[i];
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
@@ -238,13 +282,15 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
         const int s = (q - kb) % NS;
         float *st = smem + s * TT::STAGE;
         const uint32_t bar = bar0 + 8 * s;
-        const bool wc = ((K == kKindPoint || K == kKindLabel) && q >= k0 && q < k1) || K == kKindDiv;
+        const bool wc =
+            ((K == kKindPoint || K == kKindLabel) && q >= k0 && q < k1) || K == kKindDiv || K == kKindDivLabel;
         const uint32_t bytes = TT::STATE * 4 + (wc ? TT::COEF * 4 : 0);
         mbar_expect_tx(bar, bytes);
         tma_load_4d(smem_u32(st), tm_in, x0 - 4, y0 - 1, q, 0, bar);
         if ((K == kKindPoint || K == kKindLabel) && wc)
             tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0, y0, q, 0, bar);
         if (K == kKindDiv) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0 - 4, y0 - 1, q, 0, bar);
+        if (K == kKindDivLabel) tma_load_4d(smem_u32(st + TT::STATE), tm_coef, x0 - 16, y0 - 1, q, 0, bar);
     };
 
     if (tid == 0) {
@@ -267,9 +313,15 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
     ok &= mbar_wait_bounded(bar0, 0);  // plane kb, slot 0, first phase
 #pragma unroll
     for (int f = 0; f < 6; ++f) prev[f] = *reinterpret_cast<const float4 *>(smem + f * TT::FIELD + o);
+    const int ob = (gy + 1) * TT::BXB + 16 + 4 * gx;  // this thread's first node in a class-byte tile
     if (K == kKindDiv) {
         prevc[0] = *reinterpret_cast<const float4 *>(smem + TT::STATE + o);
         prevc[1] = *reinterpret_cast<const float4 *>(smem + TT::STATE + TT::FIELD + o);
+    }
+    if constexpr (K == kKindDivLabel) {
+        float4 r_unused;
+        class_quad(*reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(smem + TT::STATE) + ob),
+                   s_tab, prevc[0], prevc[1], r_unused);
     }
     __syncthreads();  // every thread has read plane kb: its slot is free
     if (tid == 0 && kb + NS <= k1) {
@@ -300,13 +352,21 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
         const float *sc = smem + ((k - kb) % NS) * TT::STAGE;
         const float *sp = smem + ((k + 1 - kb) % NS) * TT::STAGE;
 
-        if constexpr (K == kKindDiv) {
+        if constexpr (K == kKindDiv || K == kKindDivLabel) {
             // face weights of the four nodes, shared by the three components
-            const Nb7 mn = gather7<TT::BX, TT::GX>(sc, prevc[0], sp, TT::STATE + o, gx);
-            const Nb7 en = gather7<TT::BX, TT::GX>(sc, prevc[1], sp, TT::STATE + TT::FIELD + o, gx);
+            Nb7 mn, en;
+            float4 r4;
+            if constexpr (K == kKindDivLabel) {
+                gather7_cls<TT::GX>(reinterpret_cast<const unsigned char *>(sc + TT::STATE),
+                                    reinterpret_cast<const unsigned char *>(sp + TT::STATE), ob, TT::BXB, gx,
+                                    s_tab, prevc[0], prevc[1], mn, en, r4);
+            } else {
+                mn = gather7<TT::BX, TT::GX>(sc, prevc[0], sp, TT::STATE + o, gx);
+                en = gather7<TT::BX, TT::GX>(sc, prevc[1], sp, TT::STATE + TT::FIELD + o, gx);
+                r4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + 2 * TT::FIELD + o);
+            }
             prevc[0] = mn.c;
             prevc[1] = en.c;
-            const float4 r4 = *reinterpret_cast<const float4 *>(sc + TT::STATE + 2 * TT::FIELD + o);
             float wm[4][6], we[4][6];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -375,8 +435,8 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
             } else if (K == kKindLabel) {
                 const uint32_t l4 = *reinterpret_cast<const uint32_t *>(
                     reinterpret_cast<const unsigned char *>(sc + TT::STATE) + gy * TX + 4 * gx);
-                const float2 c0 = s_tab[l4 & 255u], c1 = s_tab[(l4 >> 8) & 255u];
-                const float2 c2 = s_tab[(l4 >> 16) & 255u], c3 = s_tab[l4 >> 24];
+                const float4 c0 = s_tab[l4 & 255u], c1 = s_tab[(l4 >> 8) & 255u];
+                const float4 c2 = s_tab[(l4 >> 16) & 255u], c3 = s_tab[l4 >> 24];
                 A4 = make_float4(c0.x, c1.x, c2.x, c3.x);
                 B4 = make_float4(c0.y, c1.y, c2.y, c3.y);
             } else {
@@ -922,6 +982,7 @@ static bool pick(int tx, int ty, int ns, int kind, TmaKernel *k, size_t *smem, i
         case kKindPoint: pick_kind<TX, TY, NS, kKindPoint>(k, smem); break;
         case kKindDiv: pick_kind<TX, TY, NS, kKindDiv>(k, smem); break;
         case kKindLabel: pick_kind<TX, TY, NS, kKindLabel>(k, smem); break;
+        case kKindDivLabel: pick_kind<TX, TY, NS, kKindDivLabel>(k, smem); break;
         default: return false;
     }
     *nt = TX * TY / 4;
@@ -1022,6 +1083,7 @@ static kv_status encode_labels(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
 static kv_status encode_coef_map(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
     switch (tma_kind(h)) {
         case kKindLabel: return encode_labels(h, tm, tx, ty);
+        case kKindDivLabel: return encode_labels(h, tm, tx + 32, ty + 2);
         case kKindPoint: return encode_tensor_4d(h, tm, h->coef, 2, tx, ty, 2);
         case kKindDiv: return encode_tensor_4d(h, tm, h->coef, 3, tx + 8, ty + 2, 3);
         default: *tm = h->tm_state[0]; return KV_OK;
@@ -1058,7 +1120,8 @@ kv_status step_prepare(kv_handle *h) {
     if (!tma_kernel_for(h->tx, h->ty, h->ns_stages, tma_kind(h), &k, &smem, &nt))
         return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d with %d stages", h->tx,
                          h->ty, h->ns_stages);
-    const size_t static_smem = tma_kind(h) == kKindLabel ? kMaxLabels * sizeof(float2) : 0;  // class table
+    const int tk = tma_kind(h);
+    const size_t static_smem = (tk == kKindLabel || tk == kKindDivLabel) ? kMaxLabels * sizeof(float4) : 0;
     if (smem + static_smem > 227 * 1024)
         return set_error(h, KV_ERR_ARG, "tile %dx%d with %d stages needs %zu bytes of shared memory",
                          h->tx, h->ty, h->ns_stages, smem + static_smem);
