@@ -409,8 +409,8 @@ def main():
     step_cfg = kv.kv_get_step_config(h)
     classes = kv.kv_medium_classes(h) if step_cfg["variant"] == 0 else 0
     medium_enc = "classes" if classes > 0 else "fields"
-    bytes_per_cell = (DIV_STEP_BYTES_PER_CELL if div else
-                      CLASS_STEP_BYTES_PER_CELL if classes > 0 else STEP_BYTES_PER_CELL)
+    bytes_per_cell = (CLASS_STEP_BYTES_PER_CELL if classes > 0 else
+                      DIV_STEP_BYTES_PER_CELL if div else STEP_BYTES_PER_CELL)
     if args.cg_config is not None:
         kv.kv_set_cg_config(h, args.cg_config)
         cg_tune_ms = None

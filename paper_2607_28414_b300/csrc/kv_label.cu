@@ -127,7 +127,7 @@ void medium_labels_free(kv_handle *h) {
 }
 
 // Flux-form media are classified as well (their class path is kKindDivLabel).
-constexpr bool kClassifyDiv = false;
+constexpr bool kClassifyDiv = true;
 
 kv_status medium_classify(kv_handle *h) {
     const int before = h->n_labels;

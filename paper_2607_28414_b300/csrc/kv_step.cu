@@ -1077,11 +1077,14 @@ static kv_status encode_labels(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
     return KV_OK;
 }
 
-// Tensor map of the coefficient fields for a tile (tx, ty): the centre tile
-// of (A', B') for the pointwise operator, the haloed tile of (m, e, 1/rho)
-// for the divergence form; unused placeholder for a homogeneous medium.
-static kv_status encode_coef_map(kv_handle *h, CUtensorMap *tm, int tx, int ty) {
-    switch (tma_kind(h)) {
+// Tensor map of the coefficients that a kernel of `kind` stages for a tile
+// (tx, ty): the centre tile of (A', B') for the pointwise operator, the haloed
+// tile of (m, e, 1/rho) for the divergence form, the class bytes (centre tile
+// or haloed 16-byte aligned tile) for the class kinds; unused placeholder for
+// a homogeneous medium. The map's element type must match the kernel's kind:
+// a class-byte map read with a float kernel's coordinates is misaligned.
+static kv_status encode_coef_map(kv_handle *h, CUtensorMap *tm, int tx, int ty, int kind) {
+    switch (kind) {
         case kKindLabel: return encode_labels(h, tm, tx, ty);
         case kKindDivLabel: return encode_labels(h, tm, tx + 32, ty + 2);
         case kKindPoint: return encode_tensor_4d(h, tm, h->coef, 2, tx, ty, 2);
@@ -1129,7 +1132,7 @@ kv_status step_prepare(kv_handle *h) {
     for (int b = 0; b < 2; ++b)
         if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 2, 6)) != KV_OK)
             return st;
-    if ((st = encode_coef_map(h, &h->tm_coef, h->tx, h->ty)) != KV_OK) return st;
+    if ((st = encode_coef_map(h, &h->tm_coef, h->tx, h->ty, tma_kind(h))) != KV_OK) return st;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(step)");
     h->tma_ready = 1;
@@ -1277,7 +1280,8 @@ kv_status batch_fill_case(kv_handle *h, BatchCase *bc, int tx, int ty, int zc, i
         if ((st = encode_tensor_4d(h, &bc->tm_state[b], h->state[b], 6, tx + 8, ty + 2, 6)) != KV_OK)
             return st;
     if (h->het) {
-        if ((st = encode_coef_map(h, &bc->tm_coef, tx, ty)) != KV_OK) return st;
+        // the batch kernels read the coefficient fields (kinds 1 and 2), never class bytes
+        if ((st = encode_coef_map(h, &bc->tm_coef, tx, ty, step_kind(h))) != KV_OK) return st;
     } else {
         bc->tm_coef = bc->tm_state[0];
     }

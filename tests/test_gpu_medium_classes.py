@@ -1,6 +1,7 @@
-"""Class-encoded media: a pointwise FP32 medium with at most 256 distinct folded
-(A', B') pairs is read by the TMA step kernel as one class byte per node plus
-a table of the FP32 pairs (Sec. 3.1 coefficients, stored differently).
+"""Class-encoded media: an FP32 medium with at most 256 distinct folded
+coefficient tuples ((A', B') for the pointwise operator of Sec. 3.1, (m, e,
+1/rho) for the flux form) is read by the TMA step kernel as one class byte per
+node plus a table of the FP32 tuples.
 
 The table holds the folded values bit for bit, so the class path must agree
 bit for bit with the field path (KV_MEDIUM_FIELDS) and with the plain per-node
@@ -18,8 +19,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def run(w, n_steps, encoding=kv.KV_MEDIUM_AUTO, step_config=None):
-    s = Solver(w, n_steps=n_steps, step_config=step_config)
+def run(w, n_steps, encoding=kv.KV_MEDIUM_AUTO, step_config=None, operator=kv.KV_OP_POINTWISE):
+    s = Solver(w, n_steps=n_steps, step_config=step_config, operator=operator)
     kv.kv_set_medium_encoding(s.h, encoding)
     classes = kv.kv_medium_classes(s.h)
     s.project()
@@ -74,6 +75,30 @@ def test_classes_match_fields_and_plain_kernel_bitwise(device, cfg):
     assert np.array_equal(tr, tr_p) and np.array_equal(f, f_p)
 
 
+@pytest.mark.parametrize("op", [kv.KV_OP_POINTWISE, kv.KV_OP_DIVERGENCE])
+def test_batch_of_class_encoded_handles_reads_the_fields(device, op):
+    """Batched stepping of handles whose step reads class bytes: the batch
+    kernel reads the coefficient fields and matches each handle's own step."""
+    cases = [inclusion_workload(70, 37, 45, seed=3), inclusion_workload(45, 40, 33, seed=8)]
+    n = 64
+    cfg = {"variant": 0, "tx": 64, "ty": 8, "zc": 16, "ns": 4}
+    singles = [run(w, n, kv.KV_MEDIUM_AUTO, cfg, op)[1] for w in cases]
+    stream = torch.cuda.Stream(device)
+    solvers = [Solver(w, n_steps=n, operator=op, stream=stream.cuda_stream) for w in cases]
+    for s in solvers:
+        kv.kv_set_medium_encoding(s.h, kv.KV_MEDIUM_AUTO)
+        assert kv.kv_medium_classes(s.h) > 0
+        s.project()
+    b = kv.kv_batch_create([s.h for s in solvers])
+    kv.kv_batch_set_config(b, 64, 8, 16, 4)
+    kv.kv_batch_step(b, n)
+    for s, ref in zip(solvers, singles):
+        assert np.array_equal(s.read_traces().cpu().numpy(), ref)
+    kv.kv_batch_destroy(b)
+    for s in solvers:
+        s.close()
+
+
 def test_class_count_limit(device):
     c256, tr, f = run(banded_workload(256), 40)
     c257, _, _ = run(banded_workload(257), 40)
@@ -82,7 +107,38 @@ def test_class_count_limit(device):
     assert np.array_equal(tr, tr_f) and np.array_equal(f, f_f)
 
 
-def test_field_path_for_continuous_divergence_and_fp64_media(device):
+@pytest.mark.parametrize("cfg", [None, {"variant": 0, "tx": 32, "ty": 8, "zc": 7, "ns": 6},
+                                 {"variant": 0, "tx": 64, "ty": 8, "zc": 64, "ns": 4},
+                                 {"variant": 0, "tx": 128, "ty": 4, "zc": 16, "ns": 4}])
+def test_flux_form_classes_match_fields_and_plain_kernel_bitwise(device, cfg):
+    w = inclusion_workload(seed=4)
+    div = kv.KV_OP_DIVERGENCE
+    c_auto, tr, f = run(w, 60, kv.KV_MEDIUM_AUTO, cfg, div)
+    c_fld, tr_f, f_f = run(w, 60, kv.KV_MEDIUM_FIELDS, cfg, div)
+    _, tr_p, f_p = run(w, 60, kv.KV_MEDIUM_AUTO, {"variant": 1}, div)
+    assert 2 <= c_auto <= 8 and c_fld == 0
+    assert np.abs(f).max() > 0
+    assert np.array_equal(tr, tr_f) and np.array_equal(f, f_f)
+    assert np.array_equal(tr, tr_p) and np.array_equal(f, f_p)
+
+
+def test_flux_form_keeps_fields_when_density_is_not_fixed_by_the_moduli(device):
+    """Two regions with the same G and eta but different rho share (m, e) and
+    differ in 1/rho: the flux form reads the fields, the pointwise operator
+    (A' = m/rho) still has two classes."""
+    w = inclusion_workload(48, 24, 30)
+    rho = np.full((w.nz, w.ny, w.nx), 1000.0, np.float32)
+    rho[:, :, w.nx // 2:] = 1100.0
+    w2 = inputs.Workload("rho_step", w.nx, w.ny, w.nz, w.dx, np.full_like(rho, 3e3), rho,
+                         np.full_like(rho, 0.5), w.force, w.t_push, 20, w.sensors, w.tol)
+    c_div, tr, f = run(w2, 20, kv.KV_MEDIUM_AUTO, None, kv.KV_OP_DIVERGENCE)
+    c_pt, _, _ = run(w2, 20, kv.KV_MEDIUM_AUTO)
+    assert c_div == 0 and c_pt >= 2
+    _, tr_f, f_f = run(w2, 20, kv.KV_MEDIUM_FIELDS, None, kv.KV_OP_DIVERGENCE)
+    assert np.array_equal(tr, tr_f) and np.array_equal(f, f_f)
+
+
+def test_field_path_for_continuous_and_fp64_media(device):
     w = inclusion_workload(40, 33, 35)
     rng = np.random.default_rng(11)
     G = (3e3 * (1 + 0.1 * rng.random((w.nz, w.ny, w.nx)))).astype(np.float32)
@@ -95,7 +151,7 @@ def test_field_path_for_continuous_divergence_and_fp64_media(device):
     kv.kv_set_medium(s.h, *s.medium)  # back to the inclusions
     assert kv.kv_medium_classes(s.h) > 0
     kv.kv_set_operator(s.h, kv.KV_OP_DIVERGENCE, *s.medium)
-    assert kv.kv_medium_classes(s.h) == 0
+    assert kv.kv_medium_classes(s.h) > 0  # (m, e, 1/rho) of the flux form
     kv.kv_set_operator(s.h, kv.KV_OP_POINTWISE, *s.medium)
     assert kv.kv_medium_classes(s.h) > 0
     kv.kv_set_medium_encoding(s.h, kv.KV_MEDIUM_FIELDS)
