@@ -103,9 +103,9 @@ def parse():
                     help="spatial operator of the heterogeneous step: pointwise (G/rho) L u "
                          "(Sec. 3.1) or the flux form (1/rho) div(G grad u)")
     ap.add_argument("--medium-encoding", default="auto", choices=["auto", "fields"],
-                    help="auto: a medium of at most 256 distinct (A', B') pairs is read as one "
-                         "class byte per node (bit for bit the same step); fields: always read "
-                         "the two coefficient fields")
+                    help="auto: a medium of at most 256 distinct folded coefficient tuples is "
+                         "read as one class byte per node (bit for bit the same step); fields: "
+                         "always read the coefficient fields")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
     ap.add_argument("--step-config", default=None,
@@ -535,8 +535,8 @@ def main():
                                   if args.workload == "inclusions256" else
                                   "bone shell over smooth soft tissue (seed 105), speckled beam"),
                        "operator": args.operator,
-                       "medium_encoding": (f"{classes} classes: 1 byte per node + (A', B') table"
-                                           if classes > 0 else "coefficient fields A', B' (FP32)"),
+                       "medium_encoding": (f"{classes} classes: 1 byte per node + coefficient table"
+                                           if classes > 0 else "coefficient fields (FP32)"),
                        "projection": ("CG preconditioned by a multigrid V(1,1)-cycle (mode 4)"
                                       if proj_mode == 4 else "plain CG from zero (mode 0)"),
                        "reductions": "f64", "parallelism": f"replicas{world}",

@@ -140,16 +140,18 @@ kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta);
  * handle starts with KV_OP_POINTWISE. Synchronising. */
 kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_field eta);
 
-/* How the FP32 step reads a heterogeneous pointwise medium (Sec. 3.1 folded
- * coefficients A' = dt^2 G/(rho dx^2), B' = dt eta/(rho dx^2)).
+/* How the FP32 step reads a heterogeneous medium (Sec. 3.1 folded
+ * coefficients: A' = dt^2 G/(rho dx^2), B' = dt eta/(rho dx^2) for the
+ * pointwise operator; m = dt^2 G/dx^2, e = dt eta/dx^2, 1/rho for the flux form).
  * KV_MEDIUM_AUTO (the default): after each fold the handle counts the
- * distinct (A', B') pairs on the device; if there are at most 256 (a
+ * distinct coefficient tuples on the device; if there are at most 256 (a
  * segmented medium: background and inclusions, layers), it stores one class
- * byte per node and a table of the FP32 pairs, and the TMA step kernel
- * (variant 0) reads the byte and the table instead of the two FP32 fields:
- * 49 instead of 56 bytes per node and step, with results bit for bit those
- * of the fields. More pairs, the divergence form, FP64 handles and the other
- * step variants read the fields. KV_MEDIUM_FIELDS always reads the fields.
+ * byte per node and a table of the FP32 tuples, and the TMA step kernel
+ * (variant 0) reads the byte and the table instead of the FP32 fields: 49
+ * instead of 56 (pointwise) or 60 (flux form) bytes per node and step, with
+ * results bit for bit those of the fields. More tuples, a flux-form medium
+ * where (m, e) does not fix 1/rho, FP64 handles, the other step variants and
+ * batches read the fields. KV_MEDIUM_FIELDS always reads the fields.
  * The class bytes take nx_pitched * ny * nz bytes of device memory.
  * Synchronising; the state and traces are kept. KV_ERR_ARG for another value. */
 typedef enum { KV_MEDIUM_AUTO = 0, KV_MEDIUM_FIELDS = 1 } kv_medium_encoding;
