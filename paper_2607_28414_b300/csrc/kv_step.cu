@@ -204,38 +204,46 @@ __device__ __forceinline__ void nb_of(const Nb7 &n, int q, float (&v)[6]) {
     v[5] = lane4(n.zp, q);
 }
 
-// Class-encoded flux form: the (m, e, 1/rho) of four consecutive nodes from
-// their four class bytes (one 32-bit word) and the class table.
-__device__ __forceinline__ void class_quad(uint32_t q, const float4 *tab, float4 &m, float4 &e, float4 &r) {
-    const float4 t0 = tab[q & 255u], t1 = tab[(q >> 8) & 255u], t2 = tab[(q >> 16) & 255u], t3 = tab[q >> 24];
-    m = make_float4(t0.x, t1.x, t2.x, t3.x);
-    e = make_float4(t0.y, t1.y, t2.y, t3.y);
-    r = make_float4(t0.z, t1.z, t2.z, t3.z);
+// Class-encoded media: the first two coefficients ((A', B') or (m, e)) and
+// the third (1/rho of the flux form) of four consecutive nodes from their four
+// class bytes (one 32-bit word) and the class tables.
+__device__ __forceinline__ void class_quad2(uint32_t q, const float2 *tab, float4 &a, float4 &b) {
+    const float2 t0 = tab[q & 255u], t1 = tab[(q >> 8) & 255u], t2 = tab[(q >> 16) & 255u], t3 = tab[q >> 24];
+    a = make_float4(t0.x, t1.x, t2.x, t3.x);
+    b = make_float4(t0.y, t1.y, t2.y, t3.y);
+}
+__device__ __forceinline__ float4 class_quad1(uint32_t q, const float *tab) {
+    return make_float4(tab[q & 255u], tab[(q >> 8) & 255u], tab[(q >> 16) & 255u], tab[q >> 24]);
 }
 
-// gather7 of m and e (and the centre 1/rho) from class-byte tiles: bc the
-// centre plane, bp the next plane (row stride BXB, this thread's first node at
-// byte offset off); the z-1 neighbours are the previous plane's centre values.
+// gather7 of m and e from class-byte tiles (row stride BXB, this thread's
+// first node at byte offset off): the centre values cm, ce were decoded one
+// plane earlier (as that plane's z+ neighbours), the z-1 neighbours are the
+// previous plane's centre values, the y neighbours come from the centre
+// plane's bytes and the x neighbours from the warp or the edge bytes; nzm,
+// nze are this plane's decoded z+ neighbours.
 template <int GX>
-__device__ __forceinline__ void gather7_cls(const unsigned char *bc, const unsigned char *bp, int off, int BXB,
-                                            int gx, const float4 *tab, const float4 &zm_m, const float4 &zm_e,
-                                            Nb7 &m, Nb7 &e, float4 &r4) {
-    float4 unused;
-    class_quad(*reinterpret_cast<const uint32_t *>(bc + off), tab, m.c, e.c, r4);
-    class_quad(*reinterpret_cast<const uint32_t *>(bc + off - BXB), tab, m.ym, e.ym, unused);
-    class_quad(*reinterpret_cast<const uint32_t *>(bc + off + BXB), tab, m.yp, e.yp, unused);
-    class_quad(*reinterpret_cast<const uint32_t *>(bp + off), tab, m.zp, e.zp, unused);
+__device__ __forceinline__ void gather7_cls(const unsigned char *bc, int off, int BXB, int gx, const float2 *tab,
+                                            const float4 &cm, const float4 &ce, const float4 &zm_m,
+                                            const float4 &zm_e, const float4 &nzm, const float4 &nze, Nb7 &m,
+                                            Nb7 &e) {
+    m.c = cm;
+    e.c = ce;
+    class_quad2(*reinterpret_cast<const uint32_t *>(bc + off - BXB), tab, m.ym, e.ym);
+    class_quad2(*reinterpret_cast<const uint32_t *>(bc + off + BXB), tab, m.yp, e.yp);
     m.zm = zm_m;
     e.zm = zm_e;
+    m.zp = nzm;
+    e.zp = nze;
     float lm = __shfl_up_sync(0xffffffffu, m.c.w, 1), rm = __shfl_down_sync(0xffffffffu, m.c.x, 1);
     float le = __shfl_up_sync(0xffffffffu, e.c.w, 1), re = __shfl_down_sync(0xffffffffu, e.c.x, 1);
     if (gx == 0) {
-        const float4 t = tab[bc[off - 1]];
+        const float2 t = tab[bc[off - 1]];
         lm = t.x;
         le = t.y;
     }
     if (gx == GX - 1) {
-        const float4 t = tab[bc[off + 4]];
+        const float2 t = tab[bc[off + 4]];
         rm = t.x;
         re = t.y;
     }
@@ -269,9 +277,14 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
 
     // class table of a class-encoded medium: (A', B') of every class
     constexpr bool CLS = K == kKindLabel || K == kKindDivLabel;
-    __shared__ float4 s_tab[CLS ? kMaxLabels : 1];
+    __shared__ float2 s_tab[CLS ? kMaxLabels : 1];                     // (A', B') or (m, e)
+    __shared__ float s_tab3[K == kKindDivLabel ? kMaxLabels : 1];       // 1/rho of the flux form
     if (CLS)
-        for (int i = threadIdx.x; i < p.n_lab; i += TT::NT) s_tab[i] = p.lab_tab[i];
+        for (int i = threadIdx.x; i < p.n_lab; i += TT::NT) {
+            const float4 t = p.lab_tab[i];
+            s_tab[i] = make_float2(t.x, t.y);
+            if (K == kKindDivLabel) s_tab3[i] = t.z;
+        }
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
         mbar_init_fence();
@@ -318,17 +331,24 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
         prevc[0] = *reinterpret_cast<const float4 *>(smem + TT::STATE + o);
         prevc[1] = *reinterpret_cast<const float4 *>(smem + TT::STATE + TT::FIELD + o);
     }
-    if constexpr (K == kKindDivLabel) {
-        float4 r_unused;
-        class_quad(*reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(smem + TT::STATE) + ob),
-                   s_tab, prevc[0], prevc[1], r_unused);
-    }
+    if constexpr (K == kKindDivLabel)
+        class_quad2(*reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(smem + TT::STATE) + ob),
+                    s_tab, prevc[0], prevc[1]);
     __syncthreads();  // every thread has read plane kb: its slot is free
     if (tid == 0 && kb + NS <= k1) {
         fence_proxy_async();
         issue(kb + NS);
     }
     ok &= mbar_wait_bounded(bar0 + 8 * ((k0 - kb) % NS), ((k0 - kb) / NS) & 1);
+    // class-encoded flux form: plane k0's centre coefficients (later planes'
+    // are decoded one plane ahead, as z+ neighbours)
+    float4 cur_m, cur_e, cur_r;
+    if constexpr (K == kKindDivLabel) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(
+            reinterpret_cast<const unsigned char *>(smem + ((k0 - kb) % NS) * TT::STAGE + TT::STATE) + ob);
+        class_quad2(w, s_tab, cur_m, cur_e);
+        cur_r = class_quad1(w, s_tab3);
+    }
 
     // Force steps: the projected force of the next plane is loaded one plane
     // ahead, so its latency overlaps the current plane's work.
@@ -357,9 +377,16 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
             Nb7 mn, en;
             float4 r4;
             if constexpr (K == kKindDivLabel) {
-                gather7_cls<TT::GX>(reinterpret_cast<const unsigned char *>(sc + TT::STATE),
-                                    reinterpret_cast<const unsigned char *>(sp + TT::STATE), ob, TT::BXB, gx,
-                                    s_tab, prevc[0], prevc[1], mn, en, r4);
+                const uint32_t wz = *reinterpret_cast<const uint32_t *>(
+                    reinterpret_cast<const unsigned char *>(sp + TT::STATE) + ob);
+                float4 nzm, nze;
+                class_quad2(wz, s_tab, nzm, nze);
+                gather7_cls<TT::GX>(reinterpret_cast<const unsigned char *>(sc + TT::STATE), ob, TT::BXB, gx, s_tab,
+                                    cur_m, cur_e, prevc[0], prevc[1], nzm, nze, mn, en);
+                r4 = cur_r;
+                cur_m = nzm;
+                cur_e = nze;
+                cur_r = class_quad1(wz, s_tab3);
             } else {
                 mn = gather7<TT::BX, TT::GX>(sc, prevc[0], sp, TT::STATE + o, gx);
                 en = gather7<TT::BX, TT::GX>(sc, prevc[1], sp, TT::STATE + TT::FIELD + o, gx);
@@ -435,10 +462,7 @@ __device__ __forceinline__ void step_tile(const CUtensorMap *tm_in, const CUtens
             } else if (K == kKindLabel) {
                 const uint32_t l4 = *reinterpret_cast<const uint32_t *>(
                     reinterpret_cast<const unsigned char *>(sc + TT::STATE) + gy * TX + 4 * gx);
-                const float4 c0 = s_tab[l4 & 255u], c1 = s_tab[(l4 >> 8) & 255u];
-                const float4 c2 = s_tab[(l4 >> 16) & 255u], c3 = s_tab[l4 >> 24];
-                A4 = make_float4(c0.x, c1.x, c2.x, c3.x);
-                B4 = make_float4(c0.y, c1.y, c2.y, c3.y);
+                class_quad2(l4, s_tab, A4, B4);
             } else {
                 A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
                 B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
@@ -1124,7 +1148,9 @@ kv_status step_prepare(kv_handle *h) {
         return set_error(h, KV_ERR_ARG, "no TMA step kernel for tile %dx%d with %d stages", h->tx,
                          h->ty, h->ns_stages);
     const int tk = tma_kind(h);
-    const size_t static_smem = (tk == kKindLabel || tk == kKindDivLabel) ? kMaxLabels * sizeof(float4) : 0;
+    const size_t static_smem = tk == kKindLabel      ? kMaxLabels * sizeof(float2)
+                               : tk == kKindDivLabel ? kMaxLabels * (sizeof(float2) + sizeof(float))
+                                                     : 0;  // class tables
     if (smem + static_smem > 227 * 1024)
         return set_error(h, KV_ERR_ARG, "tile %dx%d with %d stages needs %zu bytes of shared memory",
                          h->tx, h->ty, h->ns_stages, smem + static_smem);
