@@ -132,6 +132,9 @@ constexpr bool kClassifyDiv = true;
 kv_status medium_classify(kv_handle *h) {
     const int before = h->n_labels;
     h->n_labels = 0;
+    // the step kernel's kind follows n_labels: its tensor maps are re-encoded
+    // before the next step whenever the classes change, also on an error below
+    if (before != 0) h->tma_ready = 0;
     const int kind = step_kind(h);
     if (!h->het || h->precision != KV_FP32 || h->medium_encoding == KV_MEDIUM_FIELDS ||
         !(kind == kKindPoint || (kind == kKindDiv && kClassifyDiv))) {
