@@ -140,6 +140,13 @@ k_step_plain(const T *__restrict__ in, T *__restrict__ out, const T *__restrict_
 // Divergence form (K = kKindDiv): the face weights need the moduli of the six
 // neighbours, so every staged plane also carries the three coefficient fields
 // (m, e, 1/rho) with the same halo, in a second box (TX+8, TY+2, 1, 3).
+//
+// Class-encoded media (K = kKindLabel, kKindDivLabel): the coefficient box is a
+// tile of class bytes instead ((TX, TY) of the centre plane; for the flux form
+// (TX+32, TY+2) from x0-16, so the byte box starts on a 16-byte boundary), and
+// the folded coefficients come from tables in shared memory filled at block
+// start. The table values are the folded FP32 values, so both kinds compute
+// bit for bit what kKindPoint and kKindDiv compute from the fields.
 // ---------------------------------------------------------------------------
 template <int TX, int TY, int K>
 struct TmaTile {
