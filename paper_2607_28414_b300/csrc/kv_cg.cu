@@ -1037,7 +1037,10 @@ extern "C" kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx,
     double *b = (double *)(sb + kNaB);
     cudaStream_t s = (cudaStream_t)stream;
 
-    CgParams p;
+    CgParams p{};  // every field defined: plain (unpreconditioned) CG, no TMA residual buffer
+    p.pcg = 0;
+    p.rbuf = nullptr;
+    p.rfield = 0;
     p.nx = nx;
     p.ny = ny;
     p.nz = nz;

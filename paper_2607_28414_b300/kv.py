@@ -214,6 +214,19 @@ def _ptr(x, keep):
     raise TypeError(f"unsupported buffer type {type(x)}")
 
 
+def _check_f32_buffer(fn, name, t, numel):
+    """Raise ValueError unless t is a contiguous float32 torch tensor of numel elements."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{fn}: {name} must be a torch tensor, got {type(t).__name__}")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{fn}: {name} must be float32, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{fn}: {name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{fn}: {name} holds {t.numel()} elements, expected {numel}")
+
+
 def kv_stable_dt(nx, ny, nz, dx, G, rho, eta):
     keep = []
     out = ctypes.c_double()
@@ -328,7 +341,14 @@ def kv_project_force(h, fx, fy, fz, tol, max_iter=0, mode=0, fs_out=None, check=
 def kv_project_force_noalloc(nx, ny, nz, dx, fx, fy, fz, tol, fs_out, max_iter=0, stream=None):
     """Projection without device allocation (working set in libkv's static
     device array; see include/kv.h). fx, fy, fz, fs_out: CUDA tensors.
-    Returns the stats dict."""
+    Returns the stats dict.
+
+    The library reads nx*ny*nz contiguous float32 values per force component
+    and writes 3*nx*ny*nz to fs_out, so every buffer is checked for type, dtype,
+    contiguity, element count and device here, before any pointer is passed."""
+    n = int(nx) * int(ny) * int(nz)
+    for name, t, want in (("fx", fx, n), ("fy", fy, n), ("fz", fz, n), ("fs_out", fs_out, 3 * n)):
+        _check_f32_buffer("kv_project_force_noalloc", name, t, want)
     keep = []
     ptrs = []
     for t in (fx, fy, fz, fs_out):

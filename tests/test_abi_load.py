@@ -68,3 +68,34 @@ def test_argument_errors_without_gpu(lib):
 def test_status_strings(lib):
     assert kv._status_name(kv.KV_CG_MAXITER) == "KV_CG_MAXITER"
     assert kv._status_name(99) == "KV_UNKNOWN"
+
+
+def test_noalloc_wrapper_rejects_bad_buffers_before_the_call(lib, monkeypatch):
+    """The allocation-free projection reads nx*ny*nz float32 values per force
+    component and writes 3*nx*ny*nz: the binding refuses anything else before
+    a pointer reaches the library (which is replaced here by a trap)."""
+    torch = pytest.importorskip("torch")
+
+    class Trap:
+        def __getattr__(self, name):
+            raise AssertionError(f"library called: {name}")
+
+    monkeypatch.setattr(kv, "lib", lambda: Trap())
+    n = (5, 4, 3)
+    good = torch.zeros(n[::-1], dtype=torch.float32)
+    out = torch.zeros((3,) + n[::-1], dtype=torch.float32)
+    bad = [
+        (good.double(), good, good, out, "float32"),
+        (good, torch.zeros((3, 4, 2), dtype=torch.float32), good, out, "elements"),
+        (good, good, good.transpose(0, 2).contiguous().transpose(0, 2), out, "contiguous"),
+        (good, good, good, out[:2], "elements"),
+        (good, good, good.numpy(), out, "torch tensor"),
+    ]
+    for fx, fy, fz, fo, what in bad:
+        with pytest.raises(ValueError) as e:
+            kv.kv_project_force_noalloc(*n, 2e-4, fx, fy, fz, 1e-8, fo)
+        assert what in str(e.value)
+    # well-formed host tensors pass these checks and are refused as host memory
+    with pytest.raises(ValueError) as e:
+        kv.kv_project_force_noalloc(*n, 2e-4, good, good, good, 1e-8, out)
+    assert "device" in str(e.value)

@@ -5,12 +5,15 @@ another allocator, or they run on a stream that must not be stalled by the
 device-wide synchronisation of cudaFree. For them libkv keeps the projection's
 working set in a static device array. This file checks, through the C ABI,
 that two calls in a row give the same projected force as kv_project_force on a
-handle (within the FP32 parity tolerance used for f_S elsewhere) and that grids
-beyond the array's limit are refused. pytest collects it last.
+handle and as the FP64 oracle's projection, node by node (within the FP32
+parity tolerance used for f_S elsewhere), that the oracle re-evaluates the
+true residual of the call from the returned f_S, and that grids beyond the
+array's limit are refused. pytest collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle as orc
 from paper_2607_28414_b300 import inputs, kv
 
 torch = pytest.importorskip("torch")
@@ -48,6 +51,11 @@ def test_noalloc_projection_matches_handle_projection(device):
     assert st_ref["rel_res_true"] < 1e-10
     f = [torch.from_numpy(a).to(device) for a in w.force]
     scale = np.abs(ref).max()
+    # the oracle's projection of the same force (CG to 1e-13, FP64)
+    _, fs_orc, status, _ = orc.project(*w.force, w.dx, tol=1e-13)
+    assert status == "converged"
+    fs_orc = np.stack(fs_orc)
+    b = -orc.div_minus(*w.force, w.dx)
     for call in range(2):
         out = torch.full((3, w.nz, w.ny, w.nx), float("nan"), dtype=torch.float32, device=device)
         st = kv.kv_project_force_noalloc(w.nx, w.ny, w.nz, w.dx, *f, 1e-10, out)
@@ -56,6 +64,19 @@ def test_noalloc_projection_matches_handle_projection(device):
         assert st["status"] == kv.KV_OK and st["rel_res_true"] < 1e-10, (call, st)
         assert np.abs(got - ref).max() <= FS_REL_TOL * scale, call
         assert abs(st["iters"] - st_ref["iters"]) <= 2, (call, st, st_ref)
+        err_orc = np.abs(got - fs_orc).max() / np.abs(fs_orc).max()
+        # D-.f_S = -(b - A phi): the oracle's divergence of the returned f_S is
+        # the call's residual, up to the float32 rounding of the stored f_S
+        # (|delta| <= 2^-24 |f_S| per component, ||D-|| <= 2/dx per component)
+        div_fs = orc.div_minus(*got, w.dx)
+        res = np.linalg.norm(div_fs) / np.linalg.norm(b)
+        round_bound = (2.0 ** -24 * (2.0 / w.dx) * np.sqrt(3.0)
+                       * np.sqrt((got.astype(np.float64) ** 2).sum()) / np.linalg.norm(b))
+        print(f"no-alloc call {call}: {st['iters']} iterations, true residual "
+              f"{st['rel_res_true']:.3e}, oracle residual {res:.3e} (rounding bound "
+              f"{round_bound:.1e}), f_S vs oracle {err_orc:.2e} of max|f_S|")
+        assert err_orc <= FS_REL_TOL, call
+        assert res <= 1e-10 + round_bound, call
 
 
 def test_noalloc_rejects_grids_beyond_the_limit(device):
