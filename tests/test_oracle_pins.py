@@ -556,3 +556,153 @@ def test_divergence_form_energy_decays_with_viscosity():
                              u_in=u0, uprev_in=um, want_state=True, divform=True)
         es.append(E(ua, uam))
     assert es[0] > es[1] > es[2] > 0
+
+
+# ---------------------------------------------------------------------------
+# Body force and initial velocity (Sec. 3.1 a^n with f_S/rho, Sec. 3.3, Sec. 3.5)
+# ---------------------------------------------------------------------------
+
+def test_first_forced_step_from_rest_is_dt2_f_over_rho():
+    """From rest (u^0 = u^-1 = 0) the Laplacian terms vanish, so one step gives
+    u^1 = dt^2 g_0 f_S / rho on every interior node and 0 on the Dirichlet
+    layer, node by node, with a heterogeneous rho (a dropped 1/rho, a dt in
+    place of dt^2 or a shifted index fails)."""
+    nx, ny, nz = 9, 8, 7
+    rng = np.random.default_rng(31)
+    mu = rng.uniform(1e3, 10e3, (nz, ny, nx))
+    rho = rng.uniform(900.0, 2000.0, (nz, ny, nx))
+    eta = rng.uniform(0.0, 1.5, (nz, ny, nx))
+    fs = [rng.standard_normal((nz, ny, nx)) * 1e3 for _ in range(3)]
+    dt = 0.5 * orc.stable_dt(mu, rho, eta, DX)
+    g0 = 0.7
+    _, u1, u0 = orc.run(nx, ny, nz, DX, dt, mu, rho, eta, 1, np.zeros((1, 3), np.int32), fs=fs,
+                        g=[g0], want_state=True)
+    m = interior_mask(nx, ny, nz)
+    for c in range(3):
+        expect = np.where(m, dt * dt * g0 * fs[c] / rho, 0.0)
+        np.testing.assert_allclose(u1[c], expect, rtol=1e-14, atol=0)
+        assert not u0[c].any()
+
+
+def test_second_forced_step_by_hand():
+    """u^2 = 2u^1 - u^0 + dt^2 [(mu/rho) L u^1 + (eta/rho) L (u^1 - u^0)/dt + g_1 f_S/rho]
+    with u^0 = 0 and u^1 = dt^2 g_0 f_S/rho, the Laplacian written here with
+    numpy slicing; heterogeneous mu, rho, eta."""
+    nx, ny, nz = 10, 9, 8
+    rng = np.random.default_rng(32)
+    mu = rng.uniform(1e3, 10e3, (nz, ny, nx))
+    rho = rng.uniform(900.0, 2000.0, (nz, ny, nx))
+    eta = rng.uniform(0.0, 1.5, (nz, ny, nx))
+    fs = [rng.standard_normal((nz, ny, nx)) * 1e3 for _ in range(3)]
+    dt = 0.5 * orc.stable_dt(mu, rho, eta, DX)
+    g = [1.0, 0.4]
+    _, u2, _ = orc.run(nx, ny, nz, DX, dt, mu, rho, eta, 2, np.zeros((1, 3), np.int32), fs=fs,
+                       g=g, want_state=True)
+    m = interior_mask(nx, ny, nz)
+
+    def lap(q):
+        out = np.zeros_like(q)
+        out[1:-1, 1:-1, 1:-1] = (q[2:, 1:-1, 1:-1] + q[:-2, 1:-1, 1:-1] + q[1:-1, 2:, 1:-1]
+                                 + q[1:-1, :-2, 1:-1] + q[1:-1, 1:-1, 2:] + q[1:-1, 1:-1, :-2]
+                                 - 6 * q[1:-1, 1:-1, 1:-1]) / DX ** 2
+        return out
+
+    for c in range(3):
+        u1 = np.where(m, dt * dt * g[0] * fs[c] / rho, 0.0)
+        a = (mu / rho) * lap(u1) + (eta / rho) * lap(u1 / dt) + g[1] * fs[c] / rho
+        expect = np.where(m, 2.0 * u1 + dt * dt * a, 0.0)
+        np.testing.assert_allclose(u2[c], expect, rtol=1e-12, atol=1e-12 * np.abs(expect).max())
+
+
+def forced_mode_coefficients(a_lam, b_lam, s, n_push, n_steps):
+    """One Laplacian eigenmode driven from rest by a constant force of mode
+    amplitude F for the first n_push steps, s = dt^2 F / rho:
+    c_{n+1} = (2 - (a+b) lam) c_n - (1 - b lam) c_{n-1} + s [n < n_push].
+    Closed form: during the push c_n = c_p + P z1^n + Q z2^n with the static
+    part c_p = s / (a lam) (the constant solution) and P, Q from c_0 = c_-1 = 0;
+    after it, the free recurrence from (c_{n_push}, c_{n_push - 1})."""
+    p = 2.0 - a_lam - b_lam
+    q = 1.0 - b_lam
+    disc = np.sqrt(complex(p * p - 4 * q))
+    z1, z2 = (p + disc) / 2, (p - disc) / 2
+    cp = s / a_lam
+    M = np.array([[1, 1], [1 / z1, 1 / z2]])
+    P, Q = np.linalg.solve(M, np.array([-cp, -cp], complex))
+    n = np.arange(0, n_push + 1)
+    during = (cp + P * z1 ** n + Q * z2 ** n).real  # c_0 .. c_{n_push}
+    # free part: c_{n_push + m} = R z1^m + T z2^m from (c_{n_push}, c_{n_push - 1})
+    R, T = np.linalg.solve(M, np.array([during[-1], during[-2]], complex))
+    m = np.arange(1, n_steps - n_push + 1)
+    after = (R * z1 ** m + T * z2 ** m).real
+    return np.concatenate([during[1:], after])  # c_1 .. c_{n_steps}
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.6])
+def test_forced_sine_mode_closed_form(eta):
+    """Sec. 3.1 + 3.3: a projected force equal to one sine mode (per component,
+    different modes) with a step envelope g = 1 for the first 9 steps keeps u
+    in that mode; its amplitude follows the forced closed form above, whose
+    static part F / (G lam) is the solution of G (-L) u = F. This fixes the
+    body-force term's 1/rho and dt^2, G and eta, and the envelope's timing."""
+    n = (12, 11, 13)
+    G, rho = 4e3, 1300.0
+    dt = 0.5 * orc.stable_dt(G, rho, eta, DX)
+    modes = [(1, 1, 2), (2, 1, 1), (1, 2, 1)]
+    amps = [3e2, -5e2, 7e2]
+    fs = [amp * sine_mode(*n, *mk) for amp, mk in zip(amps, modes)]
+    n_steps, n_push = 50, 9
+    g = np.r_[np.ones(n_push), np.zeros(n_steps - n_push)]
+    sensors = np.array([[3, 4, 5], [7, 2, 9], [5, 5, 2]], np.int32)
+    tr = orc.run(*n, DX, dt, G, rho, eta, n_steps, sensors, fs=fs, g=g)
+    for c, (amp, mk) in enumerate(zip(amps, modes)):
+        lam = sine_eigenvalue(n, mk)
+        coef = forced_mode_coefficients(dt * dt * G / rho * lam, dt * eta / rho * lam,
+                                        dt * dt * amp / rho, n_push, n_steps)
+        for s, (i, j, k) in enumerate(sensors):
+            shape = sine_mode(*n, *mk)[k, j, i]
+            np.testing.assert_allclose(tr[:, s, c], coef * shape, rtol=0,
+                                       atol=1e-10 * np.abs(coef).max())
+    # the static part: a long push with viscosity settles at u = F / (G lam)
+    if eta > 0:
+        n_long = 3000
+        tr = orc.run(*n, DX, dt, G, rho, eta, n_long, sensors, fs=fs, g=np.ones(n_long))
+        for c, (amp, mk) in enumerate(zip(amps, modes)):
+            i, j, k = sensors[0]
+            static = amp * sine_mode(*n, *mk)[k, j, i] / (G * sine_eigenvalue(n, mk))
+            assert tr[-1, 0, c] == pytest.approx(static, rel=1e-6)
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.5])
+def test_initial_velocity_sine_mode_closed_form(eta):
+    """Sec. 3.5 start with an initial velocity v0: u^0 = 0, u^-1 = -dt v0, so a
+    v0 equal to a sine mode of amplitude V gives mode coefficients with c_0 = 0
+    and c_-1 = -dt V (a sign slip or a missing dt fails); on top of a nonzero
+    u^0 the start is u^-1 = u^0 - dt v0."""
+    n = (11, 12, 10)
+    G, rho = 4e3, 1000.0
+    dt = 0.5 * orc.stable_dt(G, rho, eta, DX)
+    modes = [(2, 1, 1), (1, 1, 1), (1, 3, 2)]
+    V = [1e-3, 2e-3, -1.5e-3]
+    v0 = [v * sine_mode(*n, *mk) for v, mk in zip(V, modes)]
+    n_steps = 40
+    sensors = np.array([[3, 4, 5], [6, 8, 2]], np.int32)
+    tr = orc.run(*n, DX, dt, G, rho, eta, n_steps, sensors, v0=v0)
+    u_start = [0.25e-6 * sine_mode(*n, *mk) for mk in modes]
+    tr2 = orc.run(*n, DX, dt, G, rho, eta, n_steps, sensors, v0=v0, u_in=u_start)
+    for c, (v, mk) in enumerate(zip(V, modes)):
+        lam = sine_eigenvalue(n, mk)
+        a, b = dt * dt * G / rho * lam, dt * eta / rho * lam
+        coef = mode_coefficients(a, b, n_steps, 0.0, -dt * v)
+        coef2 = mode_coefficients(a, b, n_steps, 0.25e-6, 0.25e-6 - dt * v)
+        for s, (i, j, k) in enumerate(sensors):
+            shape = sine_mode(*n, *mk)[k, j, i]
+            np.testing.assert_allclose(tr[:, s, c], coef * shape, rtol=0,
+                                       atol=1e-10 * np.abs(coef).max())
+            np.testing.assert_allclose(tr2[:, s, c], coef2 * shape, rtol=0,
+                                       atol=1e-10 * np.abs(coef2).max())
+    # first step: u^1 = dt v0 + dt^2 a^0 with a^0 = (eta/rho) L v0 (u^0 = 0)
+    c = 0
+    lam = sine_eigenvalue(n, modes[c])
+    i, j, k = sensors[0]
+    expect = dt * V[c] * sine_mode(*n, *modes[c])[k, j, i] * (1.0 - dt * eta / rho * lam)
+    assert tr[0, 0, c] == pytest.approx(expect, rel=1e-12)
