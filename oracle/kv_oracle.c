@@ -92,6 +92,7 @@ void or_apply_A(int nx, int ny, int nz, double dx, const double *q, double *out)
 {
     size_t N = (size_t)nx * ny * nz;
     or_laplacian(nx, ny, nz, dx, q, out);
+    #pragma omp parallel for schedule(static)
     for (size_t c = 0; c < N; ++c) out[c] = -out[c];
 }
 
@@ -184,6 +185,7 @@ int or_cg(int nx, int ny, int nz, double dx, const double *b, double *phi, doubl
 
     apply_mask(nx, ny, nz, phi);
     or_apply_A(nx, ny, nz, dx, phi, Ap);
+    #pragma omp parallel for schedule(static)
     for (size_t c = 0; c < N; ++c) r[c] = b[c] - Ap[c];
     apply_mask(nx, ny, nz, r);
     memcpy(p, r, N * sizeof(double));
@@ -206,8 +208,10 @@ int or_cg(int nx, int ny, int nz, double dx, const double *b, double *phi, doubl
             break;
         }
         double alpha = rr / pAp;
+        #pragma omp parallel for schedule(static)
         for (size_t c = 0; c < N; ++c) phi[c] = phi[c] + alpha * p[c];
         apply_mask(nx, ny, nz, phi);
+        #pragma omp parallel for schedule(static)
         for (size_t c = 0; c < N; ++c) r[c] = r[c] - alpha * Ap[c];
         apply_mask(nx, ny, nz, r);
         double rr_new = dot(N, r, r);
@@ -226,6 +230,7 @@ int or_cg(int nx, int ny, int nz, double dx, const double *b, double *phi, doubl
             break;
         }
         double beta = rr_new / rr;
+        #pragma omp parallel for schedule(static)
         for (size_t c = 0; c < N; ++c) p[c] = r[c] + beta * p[c];
         apply_mask(nx, ny, nz, p);
         rr = rr_new;
@@ -234,6 +239,7 @@ done:
     if (out_stats) {
         double bb = dot(N, b, b);
         or_apply_A(nx, ny, nz, dx, phi, Ap);
+        #pragma omp parallel for schedule(static)
         for (size_t c = 0; c < N; ++c) r[c] = b[c] - Ap[c];
         apply_mask(nx, ny, nz, r);
         out_stats[0] = (double)it;
@@ -259,10 +265,12 @@ int or_project(int nx, int ny, int nz, double dx, const double *f /*3N*/, double
     size_t N = (size_t)nx * ny * nz;
     double *b = (double *)malloc(N * sizeof(double));
     or_div_minus(nx, ny, nz, dx, f, f + N, f + 2 * N, b);
+    #pragma omp parallel for schedule(static)
     for (size_t c = 0; c < N; ++c) b[c] = -b[c];
     memset(phi, 0, N * sizeof(double));
     int st = or_cg(nx, ny, nz, dx, b, phi, tol, max_iter, out_stats);
     or_grad_plus(nx, ny, nz, dx, phi, fs, fs + N, fs + 2 * N);
+    #pragma omp parallel for schedule(static)
     for (size_t c = 0; c < 3 * N; ++c) fs[c] = f[c] - fs[c];
     free(b);
     return st;
@@ -327,6 +335,7 @@ int or_run(int nx, int ny, int nz, double dx, double dt, const double *mu, const
     if (u_in) memcpy(u0, u_in, 3 * N * sizeof(double));
     if (uprev_in) memcpy(um, uprev_in, 3 * N * sizeof(double));
     if (v0 && !uprev_in)
+        #pragma omp parallel for schedule(static)
         for (size_t c = 0; c < 3 * N; ++c) um[c] = u0[c] - dt * v0[c];
     for (int c = 0; c < 3; ++c) {
         apply_mask(nx, ny, nz, u0 + c * N);
@@ -335,6 +344,7 @@ int or_run(int nx, int ny, int nz, double dx, double dt, const double *mu, const
 
     for (int n = 0; n < n_steps; ++n) {
         const double gn = (g && n < n_g) ? g[n] : 0.0;
+        #pragma omp parallel for schedule(static)
         for (size_t c = 0; c < 3 * N; ++c) w[c] = (u0[c] - um[c]) / dt;
         for (int comp = 0; comp < 3; ++comp) {
             const double *uc = u0 + comp * N;

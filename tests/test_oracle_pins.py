@@ -706,3 +706,59 @@ def test_initial_velocity_sine_mode_closed_form(eta):
     i, j, k = sensors[0]
     expect = dt * V[c] * sine_mode(*n, *modes[c])[k, j, i] * (1.0 - dt * eta / rho * lam)
     assert tr[0, 0, c] == pytest.approx(expect, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Exact discrete projection by sine transforms (large-grid reference)
+# ---------------------------------------------------------------------------
+
+def test_poisson_direct_matches_dense_solve_and_cg():
+    """The transform solve equals the dense Kronecker solve of -L (tiny grid),
+    the explicit sine-matrix solve and the oracle's CG at 1e-13."""
+    nx, ny, nz = 7, 6, 8
+    rng = np.random.default_rng(41)
+    b = rng.standard_normal((nz, ny, nx))
+    b[~interior_mask(nx, ny, nz)] = 0
+    A = dense_negative_laplacian(nx, ny, nz)
+    ref = np.zeros_like(b)
+    ref[1:-1, 1:-1, 1:-1] = np.linalg.solve(A, b[1:-1, 1:-1, 1:-1].ravel()).reshape(
+        nz - 2, ny - 2, nx - 2)
+    np.testing.assert_allclose(orc.poisson_direct(b, DX), ref, rtol=0,
+                               atol=1e-12 * np.abs(ref).max())
+    nx, ny, nz = 26, 22, 30
+    b = rng.standard_normal((nz, ny, nx))
+    b[~interior_mask(nx, ny, nz)] = 0
+    direct = orc.poisson_direct(b, DX)
+    np.testing.assert_allclose(direct, dst_solve(b), rtol=0, atol=1e-12 * np.abs(direct).max())
+    phi, status, _ = orc.cg(b, DX, 1e-13, 5000)
+    assert status == "converged"
+    np.testing.assert_allclose(direct, phi, rtol=0, atol=1e-10 * np.abs(direct).max())
+    # values on the outer layer of b are ignored, as by the masked CG
+    b2 = b.copy()
+    b2[0] = 5.0
+    np.testing.assert_array_equal(orc.poisson_direct(b2, DX), direct)
+
+
+def test_project_direct_matches_cg_projection_and_is_solenoidal():
+    from paper_2607_28414_b300 import inputs
+    rng = np.random.default_rng(42)
+    n = (33, 29, 31)
+    f = inputs.beam_push(*n, DX, rng, focal_depth=2e-3, focal_len=1e-3)
+    f = (f[2] * 0.5 + 10.0, f[1], f[2])
+    phi_d, fs_d, res = orc.project_direct(*f, DX)
+    assert res < 1e-13
+    phi_c, fs_c, status, st = orc.project(*f, DX, tol=1e-13)
+    assert status == "converged"
+    np.testing.assert_allclose(phi_d, phi_c, rtol=0, atol=1e-11 * np.abs(phi_d).max())
+    top = max(np.abs(a).max() for a in fs_d)
+    for a, c in zip(fs_d, fs_c):
+        np.testing.assert_allclose(a, c, rtol=0, atol=1e-11 * top)
+    # D- . f_S = -(b - A phi): the divergence left is the residual
+    b = -orc.div_minus(*f, DX)
+    assert np.linalg.norm(orc.div_minus(*fs_d, DX)) <= 1e-13 * np.linalg.norm(b)
+    # a gradient is removed entirely
+    s = sine_mode(*n, 2, 3, 1)
+    g = orc.grad_plus(s, DX)
+    _, fs_g, _ = orc.project_direct(*g, DX)
+    for a, ga in zip(fs_g, g):
+        assert np.abs(a).max() <= 1e-12 * np.abs(ga).max()
