@@ -1,12 +1,15 @@
 """Benchmark of the reduced Kelvin-Voigt hot path on one B300 per rank.
 
 One bench step is one whole pass of the pre-computed-projection pipeline over
-the 256^3 heterogeneous workload (8 seeded spherical inclusions, speckled axial
-beam, dx = 0.2 mm, dt = 0.5 x the stability limit): fold the medium into the
-step coefficients, zero the state, project the force (CG to a true relative
-residual of 1e-8; by default preconditioned by a multigrid V-cycle, with
---projection cg the paper's plain CG), run 2000 fused time steps with sensor
-recording and read the traces.
+the largest single-GPU workload, the 512 x 512 x 384 bone shell (dx = 0.15 mm,
+curved bone shell over smooth soft tissue, speckled focused beam, dt = 0.5 x
+the stability limit): fold the medium into the step coefficients, zero the
+state, project the force (CG to a true relative residual of 1e-8; by default
+preconditioned by a multigrid V-cycle, started from the learned network's
+potential when one is given with --net; with --projection cg the paper's plain
+CG), run 5000 fused time steps with sensor recording and read the traces.
+`--workload inclusions256` times the 256^3 inclusions medium (2000 steps) and
+`--workload sweep` the 26-case batched sweep instead.
 
 value  = cell-updates of the pass (nx*ny*nz*2000) / pass time, in Gcell/s,
          inputs resident on the device.
@@ -40,12 +43,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_TIME_STEPS = 2000
+DEFAULT_STEPS = {"inclusions256": 2000, "bone512": 5000, "sweep": 1000}
 GRID = 256
-STEP_BYTES_PER_CELL = 56  # (u, d) read + write 48 B, coefficients A', B' 8 B
-CLASS_STEP_BYTES_PER_CELL = 49  # (u, d) 48 B + one class byte (class-encoded medium)
-DIV_STEP_BYTES_PER_CELL = 60  # divergence form: coefficients m, e, 1/rho 12 B
-FORCE_BYTES_PER_CELL = 12  # projected force on force steps
+# Algorithmic bytes of one cell-update of the method as printed (3-level
+# recurrence of Sec. 3.1): read u^n and u^n-1 (24 B), write u^n+1 (12 B),
+# heterogeneous media add the two folded coefficients (8 B); force steps add
+# the projected force (12 B). These are the roofline's numerator.
+ALG_BYTES_HOMOG = 36
+ALG_BYTES_HETEROG = 44
+FORCE_BYTES_PER_CELL = 12
+# Bytes the storage form of this library moves per cell-update: (u, d) read +
+# write 48 B plus the medium (fields A', B' 8 B; one class byte; flux-form
+# fields m, e, 1/rho 12 B). Reported beside the algorithmic fraction.
+STEP_BYTES_PER_CELL = 56
+CLASS_STEP_BYTES_PER_CELL = 49
+DIV_STEP_BYTES_PER_CELL = 60
 PLAIN_CG_ITERS = {"inclusions256": 874, "bone512": 1621, "sweep": 557}
 
 
@@ -94,11 +106,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="inclusions256",
+    ap.add_argument("--workload", default="bone512",
                     choices=["inclusions256", "bone512", "sweep"],
-                    help="inclusions256: 256^3 inclusions, 2000 steps (the headline); bone512: "
-                         "512x512x384 bone shell, 5000 steps; sweep: 26 homogeneous cases on "
-                         "uneven grids, 1000 batched steps")
+                    help="bone512: 512x512x384 bone shell, 5000 steps (the headline, the largest "
+                         "single-GPU configuration); inclusions256: 256^3 inclusions, 2000 steps; "
+                         "sweep: 26 homogeneous cases on uneven grids, 1000 batched steps")
     ap.add_argument("--operator", default="pointwise", choices=["pointwise", "divergence"],
                     help="spatial operator of the heterogeneous step: pointwise (G/rho) L u "
                          "(Sec. 3.1) or the flux form (1/rho) div(G grad u)")
@@ -107,7 +119,8 @@ def parse():
                          "read as one class byte per node (bit for bit the same step); fields: "
                          "always read the coefficient fields")
     ap.add_argument("--grid", type=int, default=GRID)
-    ap.add_argument("--time-steps", type=int, default=N_TIME_STEPS)
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="time steps of the pass (default: the workload's own)")
     ap.add_argument("--step-config", default=None,
                     help="[variant,]tx,ty,zc,ns of the step kernel instead of autotuning "
                          "(profiling runs; variant 0 one step per sweep, 2 two steps per sweep)")
@@ -177,10 +190,11 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def workload(grid, n_steps, kind="inclusions256"):
+def workload(grid, n_steps, kind="bone512"):
     from paper_2607_28414_b300 import inputs
+    n_steps = DEFAULT_STEPS[kind] if n_steps is None else n_steps
     if kind == "bone512":
-        return inputs.bone_shell(n_steps=n_steps if n_steps != N_TIME_STEPS else 5000)
+        return inputs.bone_shell(n_steps=n_steps)
     return inputs.heterogeneous_inclusions(n=grid, n_steps=n_steps)
 
 
@@ -212,7 +226,7 @@ def run_reference(args, rank, world):
     if args.workload == "sweep":
         # the oracle on the sweep's first case (128 x 128 x 192), whose rate per
         # cell-update stands for the sweep's
-        n_steps = args.time_steps if args.time_steps != N_TIME_STEPS else 1000
+        n_steps = args.time_steps if args.time_steps is not None else DEFAULT_STEPS["sweep"]
         w = inputs.sweep_cases(n_steps=n_steps)[0]
     else:
         w = workload(args.grid, args.time_steps, args.workload)
@@ -222,7 +236,8 @@ def run_reference(args, rank, world):
     cg_iters = PLAIN_CG_ITERS.get(args.workload if args.grid == GRID else None, 400)
     vals = []
     for it in range(args.warmup + args.steps):
-        v, info = cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=3, n_sample_iters=3,
+        k = 1 if w.n_cells > 50_000_000 else 3  # keeps the whole run within a few minutes
+        v, info = cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=k, n_sample_iters=k,
                                     divform=args.operator == "divergence")
         if it >= args.warmup:
             vals.append(v)
@@ -265,7 +280,7 @@ def run_sweep(args, rank, world):
         dist.init_process_group("nccl", device_id=device)
     stream = torch.cuda.Stream(device)
     torch.cuda.set_stream(stream)
-    n_steps = args.time_steps if args.time_steps != N_TIME_STEPS else 1000
+    n_steps = args.time_steps if args.time_steps is not None else DEFAULT_STEPS["sweep"]
     cases = inputs.sweep_cases(n_steps=n_steps)
     hs, forces, owner = [], [], {}
     for w in cases:
@@ -332,8 +347,12 @@ def run_sweep(args, rank, world):
     for h in hs:
         kv.kv_destroy(h)
     value = job_rate(world, N * n_steps * args.steps, t)
-    bytes_per_step = 48.0 * N  # homogeneous: (u, d) read + write
-    achieved = bytes_per_step / (t_steps / n_steps) / 1e9
+    # homogeneous cases: 36 B/cell algorithmic, 48 B/cell moved by the (u, d) form
+    n_force = sum(int(inputs.push_envelope(n_steps, 0.5 * kv.kv_stable_dt(
+        w.nx, w.ny, w.nz, w.dx, w.G, w.rho, w.eta), w.t_push).sum()) * w.n_cells for w in cases)
+    launch_s = t_steps / n_steps
+    achieved = (ALG_BYTES_HOMOG * N + FORCE_BYTES_PER_CELL * n_force / n_steps) / launch_s / 1e9
+    achieved_storage = (48.0 * N + FORCE_BYTES_PER_CELL * n_force / n_steps) / launch_s / 1e9
     peak, peak_kind = peaks()
     if rank == 0:
         print(json.dumps({
@@ -350,7 +369,13 @@ def run_sweep(args, rank, world):
             "kv_step_gcells": N * n_steps / t_steps / 1e9, "autotune_ms_per_step": tune_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_step_batch",
-                         "peak_kind": peak_kind, "bytes_model": "48 B/cell (homogeneous)"},
+                         "peak_kind": peak_kind,
+                         "bytes_model": (f"algorithmic {ALG_BYTES_HOMOG} B/cell (homogeneous, "
+                                         f"3-level recurrence) + {FORCE_BYTES_PER_CELL} B/cell "
+                                         "on force steps"),
+                         "achieved_storage_form": achieved_storage,
+                         "frac_storage_form": achieved_storage / peak,
+                         "storage_bytes_model": "48 B/cell ((u, d) read + write)"},
             "gpu_launches": int(launches), "clocks": clk, "e2e": None, "cpu_baseline": None}),
             flush=True)
     if world > 1:
@@ -475,9 +500,10 @@ def main():
     value = job_rate(world, N * w.n_steps * args.steps, t_max)
     step_gcells = N * w.n_steps * args.steps / t_steps / 1e9
     launch_s = t_steps / (w.n_steps * args.steps)
-    alg_bytes = (N * bytes_per_cell * w.n_steps + N * FORCE_BYTES_PER_CELL * n_force_steps) \
-        / w.n_steps
+    force_bytes = N * FORCE_BYTES_PER_CELL * n_force_steps / w.n_steps  # per launch, averaged
+    alg_bytes = N * ALG_BYTES_HETEROG + force_bytes
     achieved = alg_bytes / launch_s / 1e9
+    achieved_storage = (N * bytes_per_cell + force_bytes) / launch_s / 1e9
     peak, peak_kind = peaks()
     traffic = step_traffic(w, step_cfg, args.operator, n_force_steps, medium_enc)
 
@@ -511,12 +537,13 @@ def main():
         v, info = cpu_oracle_sample(w, dt, by_mode["cg"]["iters"], divform=div)
         cpu = {"value": v, "unit": "Gcell-updates/s", "cores": info["cores"], "kind": "oracle",
                "sample": info["sample"]}
-        # the same oracle on one host core (a smaller sample: 2 iterations + 2 steps)
+        # the same oracle on one host core (a smaller sample: 1-2 iterations + 1-2 steps)
         import oracle as orc
         n_all = orc.get_threads()
         orc.set_threads(1)
         try:
-            v1, info1 = cpu_oracle_sample(w, dt, by_mode["cg"]["iters"], 2, 2, divform=div)
+            k1 = 1 if N > 50_000_000 else 2
+            v1, info1 = cpu_oracle_sample(w, dt, by_mode["cg"]["iters"], k1, k1, divform=div)
         finally:
             orc.set_threads(n_all)
         cpu.update({"value_1_core": v1, "sample_1_core": info1["sample"]})
@@ -548,9 +575,22 @@ def main():
             "cg_zc": cg_zc, "cg_autotune_ms_40_iters": cg_tune_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": ("stored ncu capture (dram__bytes_read.sum + "
+                                            "dram__bytes_write.sum per launch) of this grid, "
+                                            "operator, medium encoding and kernel configuration, "
+                                            "profiles/kv_step_traffic.json; not measured in "
+                                            "this run" if traffic is not None else
+                                            "no stored capture for this configuration"),
                          "kernel": "k_step_tma", "peak_kind": peak_kind,
-                         "bytes_model": f"{bytes_per_cell} B/cell + {FORCE_BYTES_PER_CELL} "
-                                        "B/cell on force steps"},
+                         "bytes_model": (f"algorithmic {ALG_BYTES_HETEROG} B/cell (heterogeneous, "
+                                         f"3-level recurrence) + {FORCE_BYTES_PER_CELL} B/cell "
+                                         "on force steps"),
+                         "launch_us": launch_s * 1e6,
+                         "achieved_storage_form": achieved_storage,
+                         "frac_storage_form": achieved_storage / peak,
+                         "storage_bytes_model": (f"{bytes_per_cell} B/cell ((u, d) read + write "
+                                                 f"48 B + medium) + {FORCE_BYTES_PER_CELL} B/cell "
+                                                 "on force steps")},
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": e2e,
