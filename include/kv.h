@@ -135,7 +135,7 @@ kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta);
  * handle's dt must not exceed kv_stable_dt_op for that operator (else
  * KV_ERR_UNSTABLE_DT and nothing changes). The divergence form stores three
  * coefficient fields (dt^2 G/dx^2, dt eta/dx^2, 1/rho) instead of two; the
- * two-step kernel (kv_set_step_config variant 2) supports only the pointwise
+ * two-step kernels (kv_set_step_config variants 2 and 3) support only the pointwise
  * operator (KV_ERR_UNSUPPORTED). The state and traces are kept. A kv_create
  * handle starts with KV_OP_POINTWISE. Synchronising. */
 kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_field eta);
@@ -264,7 +264,13 @@ kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx, const floa
  * per level two 3x3x3 conv + ReLU, 2x average pooling down, nearest 2x
  * upsampling + conv + ReLU + skip addition + conv + ReLU up, a final conv.
  * The input is b scaled to unit RMS; the target phi * s / dx^2 with the same
- * scale s; the loss the mean squared error (Adam on FP32 master weights).
+ * scale s; the loss (Adam on FP32 master weights) is chosen by kv_net_set_loss:
+ * KV_LOSS_MSE (default), the mean squared error of the potential, or
+ * KV_LOSS_RESIDUAL, the mean squared residual of the prediction,
+ * |L^(y - t)|^2 / V with L^ the unscaled 7-point Laplacian on interior nodes,
+ * i.e. |s (b - A phi_hat)|^2 / V (Sec. 3.2.3: A phi = b is what the CG solves;
+ * this loss weights the error as the CG's stopping test does). Neither is in
+ * the paper, whose projection has no learned part.
  * kv_net_create allocates activations for grids up to max_n* (each axis);
  * b, phi: dense nx*ny*nz float device arrays. stream: cudaStream_t or NULL.
  * kv_net_get/set_params: kv_net_num_params floats on the host.
@@ -277,6 +283,8 @@ kv_status kv_net_create(kv_net **out, int levels, const int *channels, int max_n
 kv_status kv_net_destroy(kv_net *n);
 long long kv_net_num_params(kv_net *n);
 kv_status kv_net_init(kv_net *n, unsigned long long seed);
+enum { KV_LOSS_MSE = 0, KV_LOSS_RESIDUAL = 1 };
+kv_status kv_net_set_loss(kv_net *n, int kind);
 kv_status kv_net_get_params(kv_net *n, float *host);
 kv_status kv_net_set_params(kv_net *n, const float *host);
 kv_status kv_net_train_step(kv_net *n, int nx, int ny, int nz, double dx, const float *b,
@@ -353,7 +361,13 @@ kv_status kv_sync(kv_handle *h);
 /* Kernel selection and launch shape of the FP32 step (autotuning and tests).
  * variant 0: TMA-staged z-march kernel (default); 1: plain per-node kernel;
  * 2: two steps per z sweep (temporal blocking, pointwise operator only;
- * tiles 32x4, 32x8, 64x4, 64x8, 128x4 with ns in {4, 6}).
+ * tiles 32x4, 32x8, 64x4, 64x8, 128x4 with ns in {4, 6});
+ * 3: two steps per z sweep with one displacement component per block (the
+ * pointwise operator couples the components only through the shared
+ * coefficients; pointwise operator only; tiles 32x8, 32x16, 64x4, 64x8,
+ * 64x16, 128x4, 128x8 with ns in {4, 6}). Variants 2 and 3 read the
+ * coefficient fields, never class bytes, and give bit for bit the result of
+ * two single steps.
  * tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in [64, 512];
  * zc >= 1 planes per block; ns in {4, 6, 8} shared-memory stages (ns - 3
  * planes in flight per block). Values <= 0 keep the current choice. A shape

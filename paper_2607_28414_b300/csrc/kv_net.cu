@@ -102,6 +102,52 @@ __global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t,
     if (threadIdx.x == 0) atomicAdd(loss, acc / (double)V);
 }
 
+// Residual loss (option KV_LOSS_RESIDUAL): with e = y - t ts on interior nodes
+// (0 on the outer layer, where the potential is fixed) and r = L^ e the
+// unscaled 7-point Laplacian of e on interior nodes, loss = sum r^2 / V. Since
+// A = -L^/dx^2 and the target is phi s/dx^2, r = -s (A phi_hat - b): the loss
+// is the squared residual of the prediction, scaled to a unit-RMS b. Its
+// gradient is dloss/dy = (2/V) L^ r on interior nodes (L^ is symmetric with the
+// Dirichlet layer).
+__device__ __forceinline__ bool interior_v(long long v, int nx, int ny, int nz, int &i, int &j, int &k) {
+    i = (int)(v % nx);
+    j = (int)((v / nx) % ny);
+    k = (int)(v / ((long long)nx * ny));
+    return i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+}
+__global__ void k_res_err(const float *__restrict__ y, const float *__restrict__ t, float ts, float *__restrict__ e,
+                          int nx, int ny, int nz) {
+    const long long V = (long long)nx * ny * nz;
+    KV_GRID_LOOP(v, V) {
+        int i, j, k;
+        e[v] = interior_v(v, nx, ny, nz, i, j, k) ? y[v * kIO] - t[v] * ts : 0.f;
+    }
+}
+__device__ __forceinline__ float lap7(const float *__restrict__ a, long long v, long long sy, long long sz) {
+    return ((a[v - 1] + a[v + 1]) + (a[v - sy] + a[v + sy])) + (a[v - sz] + a[v + sz]) - 6.f * a[v];
+}
+__global__ void k_res_lap(const float *__restrict__ e, float *__restrict__ r, int nx, int ny, int nz, double *loss) {
+    __shared__ double sh[33];
+    const long long V = (long long)nx * ny * nz, sy = nx, sz = (long long)nx * ny;
+    double acc = 0.0;
+    KV_GRID_LOOP(v, V) {
+        int i, j, k;
+        const float q = interior_v(v, nx, ny, nz, i, j, k) ? lap7(e, v, sy, sz) : 0.f;
+        r[v] = q;
+        acc += (double)q * q;
+    }
+    acc = block_sum_d(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(loss, acc / (double)V);
+}
+__global__ void k_res_grad(const float *__restrict__ r, bf16 *__restrict__ g, int nx, int ny, int nz) {
+    const long long V = (long long)nx * ny * nz, sy = nx, sz = (long long)nx * ny;
+    KV_GRID_LOOP(v, V) {
+        int i, j, k;
+        const float q = interior_v(v, nx, ny, nz, i, j, k) ? 2.f * lap7(r, v, sy, sz) / (float)V : 0.f;
+        for (int c = 0; c < kIO; ++c) g[v * kIO + c] = __float2bfloat16_rn(c == 0 ? q : 0.f);
+    }
+}
+
 __global__ void k_out_extract(const float *__restrict__ y, float *__restrict__ phi, long long V, float scale,
                               int nx, int ny, int nz) {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
@@ -249,6 +295,7 @@ struct kv_net {
     int ch[8];
     std::vector<Conv> conv;  // order: encoder A0,B0,A1,B1,..., decoder U_{L-2},D_{L-2},...,U_0,D_0, final
     long long nparams;
+    int loss_kind;                // KV_LOSS_MSE or KV_LOSS_RESIDUAL
     float *w32, *g32, *m, *v;     // parameters, gradients, Adam moments (FP32)
     bf16 *wbf, *wflip;            // BF16 weights and flipped-transposed copies
     long long adam_t;
@@ -445,6 +492,7 @@ kv_status kv_net_create(kv_net **out, int levels, const int *channels, int max_n
     add(channels[0], kIO, 0);
     n->nparams = off;
     n->adam_t = 0;
+    n->loss_kind = KV_LOSS_MSE;
     n->maxd = {max_nx, max_ny, max_nz};
     if (stream) {
         n->stream = (cudaStream_t)stream;
@@ -499,6 +547,13 @@ kv_status kv_net_destroy(kv_net *n) {
 
 long long kv_net_num_params(kv_net *n) { return n ? n->nparams : 0; }
 
+kv_status kv_net_set_loss(kv_net *n, int kind) {
+    if (!n || (kind != KV_LOSS_MSE && kind != KV_LOSS_RESIDUAL))
+        return nerr(n, KV_ERR_ARG, "kv_net_set_loss: unknown loss");
+    n->loss_kind = kind;
+    return KV_OK;
+}
+
 kv_status kv_net_init(kv_net *n, unsigned long long seed) {
     if (!n) return KV_ERR_ARG;
     std::vector<float> w(n->nparams, 0.f);
@@ -550,7 +605,14 @@ kv_status kv_net_train_step(kv_net *n, int nx, int ny, int nz, double dx, const 
     kv_status st = forward(n, d0);
     if (st != KV_OK) return nerr(n, st, "kv_net_train_step: forward failed");
     cudaMemsetAsync(n->red, 0, sizeof(double), n->stream);
-    k_loss<<<kEwBlocks, 256, 0, n->stream>>>(n->yout, phi, (float)(s / (dx * dx)), n->gout, V, n->red);
+    if (n->loss_kind == KV_LOSS_RESIDUAL) {
+        // tmp_phi holds e, tmp_b holds r (the handle path's staging is idle here)
+        k_res_err<<<kEwBlocks, 256, 0, n->stream>>>(n->yout, phi, (float)(s / (dx * dx)), n->tmp_phi, nx, ny, nz);
+        k_res_lap<<<kEwBlocks, 256, 0, n->stream>>>(n->tmp_phi, n->tmp_b, nx, ny, nz, n->red);
+        k_res_grad<<<kEwBlocks, 256, 0, n->stream>>>(n->tmp_b, n->gout, nx, ny, nz);
+    } else {
+        k_loss<<<kEwBlocks, 256, 0, n->stream>>>(n->yout, phi, (float)(s / (dx * dx)), n->gout, V, n->red);
+    }
     cudaMemsetAsync(n->g32, 0, n->nparams * 4, n->stream);
     if ((st = backward(n, d0)) != KV_OK) return nerr(n, st, "kv_net_train_step: backward failed");
     n->adam_t += 1;

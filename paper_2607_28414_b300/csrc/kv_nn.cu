@@ -22,35 +22,65 @@ namespace kv {
 // ---------------------------------------------------------------------------
 // Forward (and input-gradient) convolution on the 5th-generation tensor cores
 //
-// Implicit GEMM: a block computes 4 x (128 voxels x COUT) outputs, the voxels
-// of an 8 (x) x 16 (y) tile on four consecutive z planes. Its input brick
-// (10 x 18 x 6 voxels with the one-voxel halo) is staged once in shared memory
-// in the canonical no-swizzle K-major layout of the tensor cores: channels in
-// chunks of 8 (16 bytes), brick[cc][z][y][x][8]. For tap (dx, dy, dz) the A
-// operand (128 voxels x 16 channels) is the brick seen from voxel offset
-// (dx, dy, dz + zt): 8-row core matrices are 8 consecutive x voxels (16-byte
-// rows), the 16 row groups step by one brick row (SBO = 160 bytes), and the two
-// 8-channel halves of K step by one channel chunk (LBO = 1080 x 16 bytes). So
-// the 27 taps need no gather: each is a descriptor with a different start
-// address. The weights of the 9 taps of one dz are staged per group in the
-// same layout (B: COUT rows x 16 channels, SBO = 128 bytes, LBO = COUT x 16).
-// One thread issues tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators
-// in tensor memory: 4 x COUT columns), commits to an mbarrier, and the four
-// warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes
-// 32w .. 32w + 31 = tile rows) for the bias / ReLU / store epilogue.
+// Implicit GEMM over output tiles of 4 x (128 voxels x COUT): the voxels of an
+// 8 (x) x 16 (y) tile on four consecutive z planes. A tile's input brick (10 x
+// 18 x 6 voxels with the one-voxel halo) arrives by one 5D TMA box in the
+// canonical no-swizzle K-major layout of the tensor cores: channels in chunks of
+// 8 (16 bytes), brick[cc][z][y][x][8]. For tap (dx, dy, dz) the A operand (128
+// voxels x 16 channels) is the brick seen from voxel offset (dx, dy, dz + zt):
+// 8-row core matrices are 8 consecutive x voxels (16-byte rows), the 16 row
+// groups step by one brick row (SBO = 160 bytes), and the two 8-channel halves
+// of K step by one channel chunk (LBO = 1080 x 16 bytes). So the 27 taps need no
+// gather: each is a descriptor with a different start address.
+//
+// The weights W[t][ci][co] arrive by TMA straight from their own layout: a 4D
+// view (8 co, ci, co chunk, tap) lands as [tap][co chunk][ci][8], the MN-major
+// core matrices of the B operand (8 ci rows x 8 co, 128 contiguous bytes; LBO =
+// 128 bytes along K, SBO = CIN x 16 bytes along N). All 27 taps stay resident
+// when they fit beside the bricks; otherwise the nine (dz, dy) groups of three
+// taps stream through a 3-slot ring, refilled while the tensor cores work.
+//
+// Persistent, warp-specialised blocks walk the tiles (tile = first + i x grid):
+//   warp 4  (one thread) issues the TMA copies: bricks into a ring of NB
+//           buffers (two when they fit, so the next tile's brick lands while
+//           this one is multiplied), weights once or per group;
+//   warp 5  (one thread) issues tcgen05.mma (kind::f16, BF16 operands, FP32
+//           accumulators in tensor memory) into one of two accumulator sets
+//           of 4 x COUT columns, and commits to mbarriers that free the brick,
+//           the weight slot and hand the accumulators to the epilogue;
+//   warps 0-3 read the accumulators with tcgen05.ld (warp w owns TMEM lanes
+//           32w .. 32w + 31 = tile rows m = y x 8 + x), add the bias, apply
+//           ReLU, store, and free the accumulator set, so the epilogue of
+//           tile i overlaps the MMAs of tile i + 1.
+// Every wait is bounded (~1 s of SM clocks); a wait that gives up sets a
+// shared abort flag and the device timeout flag, every role stops issuing,
+// the copies and MMAs in flight are awaited (bounded) and the tensor memory
+// is freed before the block exits.
 // ---------------------------------------------------------------------------
-constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;                      // 4 x 128 voxels per block
+constexpr int kTcX = 8, kTcY = 16, kTcZ = 4;                      // 4 x 128 voxels per tile
 constexpr int kTcBX = kTcX + 2, kTcBY = kTcY + 2, kTcBZ = kTcZ + 2;
 constexpr int kTcBrick = kTcBX * kTcBY * kTcBZ;                   // 1080 voxels with halo
+constexpr int kConvThreads = 192;                                 // 4 epilogue warps + TMA + MMA
 
 template <int CIN, int COUT>
 struct ConvTc {
+    static constexpr size_t kBudget = 220 * 1024;
     static constexpr size_t kBrickBytes = (size_t)(CIN / 8) * kTcBrick * 16;
-    static constexpr size_t kTapBytes = (size_t)(CIN / 8) * COUT * 16;
-    static constexpr size_t kWBytes = 9 * kTapBytes;
-    static constexpr size_t kSmem = kBrickBytes + kWBytes + 24;  // + 2 mbarriers, TMEM address
-    static constexpr uint32_t kCols = kTcZ * COUT < 32 ? 32 : kTcZ * COUT;  // power of two >= 32
+    static constexpr size_t kTapBytes = (size_t)CIN * COUT * 2;
+    static constexpr size_t kAllW = 27 * kTapBytes;
+    static constexpr size_t kGroupBytes = 3 * kTapBytes;          // one (dz, dy) group of taps
+    static constexpr int NB = 2 * kBrickBytes + 3 * kGroupBytes <= kBudget ? 2 : 1;
+    static constexpr bool kResident = NB * kBrickBytes + kAllW <= kBudget;
+    static constexpr int NWS = kResident ? 1 : 3;                 // weight slots
+    static constexpr size_t kWBytes = kResident ? kAllW : 3 * kGroupBytes;
+    static constexpr int kBars = 2 * NB + 2 * NWS + 4;
+    static constexpr size_t kSmem = NB * kBrickBytes + kWBytes + 8 * kBars + 16;
+    static constexpr uint32_t kAccCols = kTcZ * COUT;             // one accumulator set
+    static constexpr uint32_t kCols = 2 * kAccCols < 32 ? 32 : 2 * kAccCols;
     static_assert(kSmem <= 227 * 1024, "shared memory of a convolution block");
+    static_assert(kCols <= 512, "tensor memory of a convolution block");
+    // a block that takes all tensor memory must also take more than half the shared memory
+    static_assert(kCols < 512 || kSmem > 114 * 1024, "one block per SM when it takes all tensor memory");
 };
 
 // Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8
@@ -134,113 +164,214 @@ __device__ __forceinline__ void store16<bf16>(bf16 *dst, const float (&v)[16]) {
     *reinterpret_cast<uint4 *>(dst + 8) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-template <int CIN, int COUT, typename OutT>
-__global__ void __launch_bounds__(128)
-k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const bf16 *__restrict__ W, const float *__restrict__ bias,
-           OutT *__restrict__ out, int nx, int ny, int nz, int relu) {
-    using C = ConvTc<CIN, COUT>;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    bf16 *brick = reinterpret_cast<bf16 *>(sm);
-    bf16 *wts = reinterpret_cast<bf16 *>(sm + C::kBrickBytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + C::kBrickBytes + C::kWBytes);  // MMA completion
-    uint64_t *bar_in = bar + 1;                                                        // input brick
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kTcX, y0 = blockIdx.y * kTcY, z0 = blockIdx.z * kTcZ;
-    const uint32_t bar_a = smem_u32(bar), bar_b = smem_u32(bar_in);
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
-    if (warp == 0) {  // tensor memory for the two accumulators
+template <int CIN, int COUT, typename OutT>
+__global__ void __launch_bounds__(kConvThreads, 1)
+k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
+           const float *__restrict__ bias, OutT *__restrict__ out, int nx, int ny, int nz, int relu) {
+    using C = ConvTc<CIN, COUT>;
+    constexpr int NB = C::NB, NWS = C::NWS;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const uint32_t sm0 = smem_u32(sm);
+    const uint32_t wts0 = sm0 + (uint32_t)(NB * C::kBrickBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NB * C::kBrickBytes + C::kWBytes);
+    const uint32_t bar0 = smem_u32(bars);
+    // barrier addresses: brick full / empty, weight full / empty, accumulator full / empty
+    auto b_full = [&](int b) { return bar0 + 8u * (uint32_t)b; };
+    auto b_empty = [&](int b) { return bar0 + 8u * (uint32_t)(NB + b); };
+    auto w_full = [&](int s) { return bar0 + 8u * (uint32_t)(2 * NB + s); };
+    auto w_empty = [&](int s) { return bar0 + 8u * (uint32_t)(2 * NB + NWS + s); };
+    auto a_full = [&](int a) { return bar0 + 8u * (uint32_t)(2 * NB + 2 * NWS + a); };
+    auto a_empty = [&](int a) { return bar0 + 8u * (uint32_t)(2 * NB + 2 * NWS + 2 + a); };
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + C::kBars);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (nx + kTcX - 1) / kTcX, nty = (ny + kTcY - 1) / kTcY, ntz = (nz + kTcZ - 1) / kTcZ;
+    const int ntiles = ntx * nty * ntz;
+    const int my_tiles = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto tile_origin = [&](int i, int &x0, int &y0, int &z0) {
+        const int t = (int)blockIdx.x + i * (int)gridDim.x;
+        x0 = (t % ntx) * kTcX;
+        y0 = ((t / ntx) % nty) * kTcY;
+        z0 = (t / (ntx * nty)) * kTcZ;
+    };
+
+    if (warp == 0) {  // tensor memory for the two accumulator sets
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                      "r"(C::kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(bar_a, 1);
-        mbar_init(bar_b, 1);
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(b_full(b), 1);
+            mbar_init(b_empty(b), 1);
+        }
+        for (int q = 0; q < NWS; ++q) {
+            mbar_init(w_full(q), 1);
+            mbar_init(w_empty(q), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(a_full(a), 1);
+            mbar_init(a_empty(a), 128);
+        }
+        *abort_flag = 0;
         mbar_init_fence();
-        // the input brick, channel-chunked [cc][z][y][x][8], by one 5D TMA box
-        // (zero fill outside the grid); the weights are staged meanwhile
-        mbar_expect_tx(bar_b, (uint32_t)C::kBrickBytes);
-        tma_load_5d(smem_u32(brick), &tm_in, 0, x0 - 1, y0 - 1, z0 - 1, 0, bar_b);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t brick_a = smem_u32(brick), wts_a = smem_u32(wts);
-    constexpr uint32_t idesc = umma_idesc_bf16(128, COUT);
-    bool ok = true;
-    uint32_t phase = 0;
-    for (int g = 0; g < 3; ++g) {  // the nine taps with dz = g
-        if (g > 0) {               // the previous group's MMAs have read the weight buffer
-            ok &= mbar_wait_bounded(bar_a, phase);
-            phase ^= 1;
-        }
-        // one 16-byte row (8 input channels of one output channel) per item;
-        // consecutive threads read consecutive output channels
-        for (int i = tid; i < 9 * (CIN / 8) * COUT; i += 128) {
-            const int co = i % COUT, r = i / COUT, cc = r % (CIN / 8), tt = r / (CIN / 8);
-            const bf16 *src = W + ((size_t)(g * 9 + tt) * CIN + cc * 8) * COUT + co;
-            uint32_t w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t lo = __bfloat16_as_ushort(src[(2 * j) * COUT]);
-                const uint32_t hi = __bfloat16_as_ushort(src[(2 * j + 1) * COUT]);
-                w[j] = lo | (hi << 16);
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        atomicExch(&g_conv_timeout, 1);
+    };
+
+    if (warp == 4) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0 && my_tiles > 0) {
+            int issued_b = 0, issued_w = 0;  // bricks and weight groups whose copies were issued
+            if (C::kResident) {
+                mbar_expect_tx(w_full(0), (uint32_t)C::kAllW);
+                tma_load_4d(wts0, &tm_w, 0, 0, 0, 0, w_full(0));
             }
-            *reinterpret_cast<uint4 *>(wts + ((size_t)(tt * (CIN / 8) + cc) * COUT + co) * 8) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        fence_proxy_async();  // generic-proxy writes of the operands -> tensor-core reads
-        if (g == 0) ok &= mbar_wait_bounded(bar_b, 0);  // the brick has landed
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll 1
-            for (int tt = 0; tt < 9; ++tt) {
-                const int dy = tt / 3, dx = tt % 3;
-#pragma unroll
-                for (int kk = 0; kk < CIN / 16; ++kk) {
-                    const uint64_t bd = umma_desc(wts_a + (uint32_t)(tt * C::kTapBytes + 2 * kk * COUT * 16),
-                                                  COUT * 16, 128);
-#pragma unroll
-                    for (int zt = 0; zt < kTcZ; ++zt) {
-                        const uint32_t vox = ((zt + g) * kTcBY + dy) * kTcBX + dx;
-                        const uint64_t ad =
-                            umma_desc(brick_a + (uint32_t)((2 * kk * kTcBrick + vox) * 16), kTcBrick * 16, kTcBX * 16);
-                        umma_bf16(tmem + zt * COUT, ad, bd, idesc, (g | tt | kk) != 0);
+            for (int i = 0; i < my_tiles && !*abort_flag; ++i) {
+                const int b = i % NB, use = i / NB;
+                if (use > 0 && !mbar_wait_bounded(b_empty(b), (uint32_t)((use - 1) & 1))) {
+                    give_up();
+                    break;
+                }
+                int x0, y0, z0;
+                tile_origin(i, x0, y0, z0);
+                mbar_expect_tx(b_full(b), (uint32_t)C::kBrickBytes);
+                tma_load_5d(sm0 + (uint32_t)(b * C::kBrickBytes), &tm_in, 0, x0 - 1, y0 - 1, z0 - 1, 0, b_full(b));
+                issued_b = i + 1;
+                if (!C::kResident) {
+                    for (int g = 0; g < 9; ++g) {
+                        const int q = issued_w % NWS, u = issued_w / NWS;
+                        if (u > 0 && !mbar_wait_bounded(w_empty(q), (uint32_t)((u - 1) & 1))) {
+                            give_up();
+                            break;
+                        }
+                        mbar_expect_tx(w_full(q), (uint32_t)C::kGroupBytes);
+                        tma_load_4d(wts0 + (uint32_t)(q * C::kGroupBytes), &tm_w, 0, 0, 0, 3 * g, w_full(q));
+                        ++issued_w;
                     }
                 }
             }
-            umma_commit(bar_a);
-        }
-    }
-    ok &= mbar_wait_bounded(bar_a, phase);
-    if (!ok) {
-        if (tid == 0) atomicExch(&g_conv_timeout, 1);
-        mbar_wait_bounded(bar_b, 0);      // the brick copy and in-flight MMAs get a second
-        mbar_wait_bounded(bar_a, phase);  // chance before TMEM and shared memory are freed
-    }
-    tc_fence_after();
-    // epilogue: TMEM lane 32w + lane = tile row m = y * 8 + x
-    const int m = 32 * warp + lane;
-    const int gx = x0 + (m % kTcX), gy = y0 + (m / kTcX);
-#pragma unroll
-    for (int zt = 0; zt < kTcZ; ++zt) {
-        const int gz = z0 + zt;
-        const bool inside = gx < nx && gy < ny && gz < nz;
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(zt * COUT + c0), v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float q = v[i] + (bias ? bias[c0 + i] : 0.f);
-                if (relu) q = fmaxf(q, 0.f);
-                v[i] = ok ? q : __int_as_float(0x7fc00000);  // a timed-out block writes NaN
+            if (*abort_flag) {  // the copies in flight land before the block exits
+                for (int b = 0; b < NB && b < issued_b; ++b) {
+                    const int last = issued_b - 1 - ((issued_b - 1 - b) % NB);
+                    mbar_wait_bounded(b_full(b), (uint32_t)((last / NB) & 1));
+                }
+                if (C::kResident) {
+                    mbar_wait_bounded(w_full(0), 0);
+                } else {
+                    for (int q = 0; q < NWS && q < issued_w; ++q) {
+                        const int last = issued_w - 1 - ((issued_w - 1 - q) % NWS);
+                        mbar_wait_bounded(w_full(q), (uint32_t)((last / NWS) & 1));
+                    }
+                }
             }
-            if (inside) store16<OutT>(out + (((size_t)gz * ny + gy) * nx + gx) * COUT + c0, v);
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0 && my_tiles > 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16(128, COUT) | (1u << 16);  // B MN-major
+            int used_w = 0, committed = 0;
+            bool ok = !C::kResident || mbar_wait_bounded(w_full(0), 0);
+            if (!ok) give_up();
+            for (int i = 0; ok && i < my_tiles && !*abort_flag; ++i) {
+                const int b = i % NB, a = i & 1;
+                if (!mbar_wait_bounded(b_full(b), (uint32_t)((i / NB) & 1)) ||
+                    (i >= 2 && !mbar_wait_bounded(a_empty(a), (uint32_t)(((i >> 1) - 1) & 1)))) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t brick = sm0 + (uint32_t)(b * C::kBrickBytes);
+                const uint32_t acc = tmem + (uint32_t)a * C::kAccCols;
+                for (int g = 0; g < 9; ++g) {
+                    const int dz = g / 3, dy = g % 3;
+                    uint32_t wg;
+                    int q = 0;
+                    if (C::kResident) {
+                        wg = wts0 + (uint32_t)(g * C::kGroupBytes);
+                    } else {
+                        q = used_w % NWS;
+                        if (!mbar_wait_bounded(w_full(q), (uint32_t)((used_w / NWS) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        wg = wts0 + (uint32_t)(q * C::kGroupBytes);
+                    }
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t bd = umma_desc(wg + (uint32_t)(dx * C::kTapBytes + kk * 256), 128, CIN * 16);
+#pragma unroll
+                            for (int zt = 0; zt < kTcZ; ++zt) {
+                                const uint32_t vox = ((zt + dz) * kTcBY + dy) * kTcBX + dx;
+                                const uint64_t ad = umma_desc(brick + (uint32_t)((2 * kk * kTcBrick + vox) * 16),
+                                                              kTcBrick * 16, kTcBX * 16);
+                                umma_bf16(acc + (uint32_t)(zt * COUT), ad, bd, idesc, (g | dx | kk) != 0);
+                            }
+                        }
+                    }
+                    if (!C::kResident) {
+                        umma_commit(w_empty(q));  // the slot refills once these MMAs are done
+                        ++used_w;
+                    }
+                }
+                if (!ok) {
+                    give_up();
+                    break;
+                }
+                umma_commit(b_empty(b));
+                umma_commit(a_full(a));
+                committed = i + 1;
+            }
+            if (*abort_flag && committed > 0) {  // the MMAs in flight finish before the block exits
+                const int i = committed - 1;
+                mbar_wait_bounded(a_full(i & 1), (uint32_t)((i >> 1) & 1));
+            }
+        }
+    } else {
+        // ---------------- epilogue (warps 0-3) ----------------
+        const int m = 32 * warp + lane;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int a = i & 1;
+            if (*abort_flag || !mbar_wait_bounded(a_full(a), (uint32_t)((i >> 1) & 1))) {
+                give_up();
+                break;
+            }
+            tc_fence_after();
+            int x0, y0, z0;
+            tile_origin(i, x0, y0, z0);
+            const int gx = x0 + (m % kTcX), gy = y0 + (m / kTcX);
+#pragma unroll
+            for (int zt = 0; zt < kTcZ; ++zt) {
+                const int gz = z0 + zt;
+                const bool inside = gx < nx && gy < ny && gz < nz;
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * C::kAccCols + zt * COUT + c0), v);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float q = v[e] + (bias ? bias[c0 + e] : 0.f);
+                        v[e] = relu ? fmaxf(q, 0.f) : q;
+                    }
+                    if (inside) store16<OutT>(out + (((size_t)gz * ny + gy) * nx + gx) * COUT + c0, v);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(a_empty(a));
         }
     }
     tc_fence_before();
@@ -451,28 +582,57 @@ __global__ void k_flip_weights(const bf16 *__restrict__ W, bf16 *__restrict__ Wt
 template <int CIN, int COUT, typename OutT>
 static kv_status launch_fwd_t(int nx, int ny, int nz, const bf16 *in, const bf16 *W, const float *bias,
                               OutT *out, int relu, cudaStream_t s) {
-    const size_t smem = ConvTc<CIN, COUT>::kSmem;
-    static bool attr = false;
-    if (!attr) {
+    using C = ConvTc<CIN, COUT>;
+    const size_t smem = C::kSmem;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm <= 0) {
         if (cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return KV_ERR_CUDA;
-        attr = true;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_conv_fwd<CIN, COUT, OutT>, kConvThreads, smem) !=
+                cudaSuccess ||
+            b <= 0)
+            return KV_ERR_CUDA;
+        // tensor memory: blocks on one SM must fit its 512 columns together
+        blocks_per_sm = std::min(b, (int)(512 / C::kCols));
     }
-    // 5D view of the channel-last input: (8 channels, x, y, z, channel chunk)
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 148;
+    }
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder(nullptr));
-    if (!enc || (reinterpret_cast<uintptr_t>(in) & 15)) return KV_ERR_ARG;
-    CUtensorMap tm;
-    cuuint64_t dims[5] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(CIN / 8)};
-    cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)nx * CIN * 2, (cuuint64_t)nx * ny * CIN * 2, 16};
-    cuuint32_t box[5] = {8, kTcBX, kTcBY, kTcBZ, CIN / 8};
-    cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(in), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return KV_ERR_CUDA;
-    dim3 grid((nx + kTcX - 1) / kTcX, (ny + kTcY - 1) / kTcY, (nz + kTcZ - 1) / kTcZ);
-    k_conv_fwd<CIN, COUT, OutT><<<grid, 128, smem, s>>>(tm, W, bias, out, nx, ny, nz, relu);
+    if (!enc || (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(W) & 15)) return KV_ERR_ARG;
+    // 5D view of the channel-last input: (8 channels, x, y, z, channel chunk)
+    CUtensorMap tm, tw;
+    {
+        cuuint64_t dims[5] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(CIN / 8)};
+        cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)nx * CIN * 2, (cuuint64_t)nx * ny * CIN * 2, 16};
+        cuuint32_t box[5] = {8, kTcBX, kTcBY, kTcBZ, CIN / 8};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(in), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return KV_ERR_CUDA;
+    }
+    // 4D view of the weights W[t][ci][co]: (8 co, ci, co chunk, tap), a box lands as
+    // [tap][co chunk][ci][8], the MN-major core matrices of the B operand
+    {
+        cuuint64_t dims[4] = {8, (cuuint64_t)CIN, (cuuint64_t)(COUT / 8), 27};
+        cuuint64_t strides[3] = {(cuuint64_t)COUT * 2, 16, (cuuint64_t)CIN * COUT * 2};
+        cuuint32_t box[4] = {8, CIN, COUT / 8, C::kResident ? 27u : 3u};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(W), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return KV_ERR_CUDA;
+    }
+    const long long ntiles = (long long)((nx + kTcX - 1) / kTcX) * ((ny + kTcY - 1) / kTcY) * ((nz + kTcZ - 1) / kTcZ);
+    const int grid = (int)std::min<long long>(ntiles, (long long)sms * blocks_per_sm);
+    k_conv_fwd<CIN, COUT, OutT><<<grid, kConvThreads, smem, s>>>(tm, tw, bias, out, nx, ny, nz, relu);
     return cudaGetLastError() == cudaSuccess ? KV_OK : KV_ERR_CUDA;
 }
 

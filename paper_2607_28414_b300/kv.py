@@ -130,6 +130,7 @@ def lib():
         L.kv_net_num_params.argtypes = [vp]
         L.kv_net_num_params.restype = ctypes.c_longlong
         L.kv_net_init.argtypes = [vp, ctypes.c_ulonglong]
+        L.kv_net_set_loss.argtypes = [vp, i]
         L.kv_net_get_params.argtypes = [vp, vp]
         L.kv_net_set_params.argtypes = [vp, vp]
         L.kv_net_train_step.argtypes = [vp, i, i, i, d, vp, vp, d, ctypes.POINTER(d)]
@@ -145,7 +146,7 @@ def lib():
                      "kv_destroy", "kv_project_force_noalloc", "kv_batch_create",
                      "kv_batch_set_config", "kv_batch_get_config", "kv_batch_autotune",
                      "kv_batch_step", "kv_batch_destroy", "kv_share_force", "kv_net_create",
-                     "kv_net_destroy", "kv_net_init", "kv_net_get_params", "kv_net_set_params",
+                     "kv_net_destroy", "kv_net_init", "kv_net_set_loss", "kv_net_get_params", "kv_net_set_params",
                      "kv_net_train_step", "kv_net_predict", "kv_attach_net", "kv_nn_conv3d_fwd",
                      "kv_nn_conv3d_flip", "kv_nn_conv3d_bwd_weight"):
             getattr(L, name).restype = ctypes.c_int
@@ -524,6 +525,15 @@ def kv_net_num_params(n):
 
 def kv_net_init(n, seed=0):
     _check(lib().kv_net_init(n, ctypes.c_ulonglong(seed)))
+
+
+KV_LOSS_MSE, KV_LOSS_RESIDUAL = 0, 1
+
+
+def kv_net_set_loss(n, kind):
+    """Training loss of the net: KV_LOSS_MSE (potential) or KV_LOSS_RESIDUAL
+    (squared residual of the prediction)."""
+    _check(lib().kv_net_set_loss(n, int(kind)))
 
 
 def kv_net_get_params(n):

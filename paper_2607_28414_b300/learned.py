@@ -156,6 +156,9 @@ def main():
     ap.add_argument("--channels", default="16,32,64,64")
     ap.add_argument("--seed", type=int, default=104)
     ap.add_argument("--out", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--loss", default="mse", choices=["mse", "residual"],
+                    help="mse: squared error of the potential; residual: squared residual "
+                         "|b - A phi_hat|^2 of the prediction")
     args = ap.parse_args()
     if args.conv_bench:
         cin, cout, n = (int(v) for v in args.conv_bench.split(","))
@@ -170,13 +173,14 @@ def main():
     t_data = time.perf_counter() - t0
     net = kv.kv_net_create(ch, tuple(max(a, b) for a, b in zip(tshape, eshape)))
     kv.kv_net_init(net, args.seed)
+    kv.kv_net_set_loss(net, kv.KV_LOSS_RESIDUAL if args.loss == "residual" else kv.KV_LOSS_MSE)
     t0 = time.perf_counter()
     losses = train(net, B, P, tshape, args.epochs, args.lr, log=print)
     t_train = time.perf_counter() - t0
     del B, P
     res = evaluate(net, eshape, inputs.random_gaussian_forces_torch(args.eval, eshape, DX,
                                                                     args.seed + 1_000_000, device))
-    res.update({"train_fields": args.train, "train_shape": tshape, "eval_shape": eshape,
+    res.update({"loss": args.loss, "train_fields": args.train, "train_shape": tshape, "eval_shape": eshape,
                 "channels": ch, "epochs": args.epochs, "data_s": t_data, "train_s": t_train,
                 "train_cg_iters_mean": float(np.mean(it)), "final_loss": float(np.mean(losses[-50:])),
                 "first_loss": float(np.mean(losses[:50])), "params": kv.kv_net_num_params(net)})

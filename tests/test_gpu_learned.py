@@ -87,6 +87,32 @@ def test_training_lowers_the_loss(device):
     assert np.mean(losses[-6:]) < 0.5 * np.mean(losses[:6])
 
 
+def test_residual_loss_training_lowers_the_residual(device):
+    """Training on the squared residual |b - A phi_hat|^2 lowers it; the loss
+    the net reports equals the oracle's residual of the net's own prediction
+    (in the net's unit-RMS scaling of b)."""
+    shape = (24, 24, 24)
+    B, P, _ = small_pairs(6, shape, 4, device)
+    net = kv.kv_net_create([16, 16], shape)
+    kv.kv_net_init(net, 3)
+    kv.kv_net_set_loss(net, kv.KV_LOSS_RESIDUAL)
+    losses = learned.train(net, B, P, shape, epochs=12, lr=2e-3)
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-6:]) < 0.5 * np.mean(losses[:6])
+    phi = torch.empty_like(B[0])
+    kv.kv_net_predict(net, shape, learned.DX, B[0], phi)
+    b = B[0].double().cpu().numpy()
+    r = b - orc.apply_A(phi.double().cpu().numpy(), learned.DX)
+    r[0], r[-1], r[:, 0], r[:, -1], r[:, :, 0], r[:, :, -1] = 0, 0, 0, 0, 0, 0
+    s2 = b.size / (b ** 2).sum()  # the net's scale s = 1/rms(b), squared
+    expect = (r ** 2).sum() * s2 / b.size
+    # a train step reports the loss of the forward pass before its update: compare
+    # with a step at learning rate 0, whose weights stay those of the prediction
+    got = kv.kv_net_train_step(net, shape, learned.DX, B[0], P[0], 0.0)
+    kv.kv_net_destroy(net)
+    assert got == pytest.approx(expect, rel=2e-2)
+
+
 def test_warm_start_reaches_the_same_residual_and_saves_iterations(device):
     """Zero start and learned start stop on the same true residual (checked by
     the oracle on the learned-start potential); after a short training the
