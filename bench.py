@@ -434,8 +434,11 @@ def main():
     step_cfg = kv.kv_get_step_config(h)
     classes = kv.kv_medium_classes(h) if step_cfg["variant"] == 0 else 0
     medium_enc = "classes" if classes > 0 else "fields"
+    two_step = step_cfg["variant"] in (2, 3)  # temporal blocking: one sweep advances two steps
     bytes_per_cell = (CLASS_STEP_BYTES_PER_CELL if classes > 0 else
                       DIV_STEP_BYTES_PER_CELL if div else STEP_BYTES_PER_CELL)
+    if two_step:
+        bytes_per_cell = STEP_BYTES_PER_CELL / 2  # (u, d) and the fields once per two steps
     if args.cg_config is not None:
         kv.kv_set_cg_config(h, args.cg_config)
         cg_tune_ms = None
@@ -581,16 +584,20 @@ def main():
                                             "profiles/kv_step_traffic.json; not measured in "
                                             "this run" if traffic is not None else
                                             "no stored capture for this configuration"),
-                         "kernel": "k_step_tma", "peak_kind": peak_kind,
+                         "kernel": {0: "k_step_tma", 1: "k_step_plain", 2: "k_step2_tma",
+                                    3: "k_step2c_tma"}[step_cfg["variant"]],
+                         "steps_per_launch": 2 if two_step else 1, "peak_kind": peak_kind,
                          "bytes_model": (f"algorithmic {ALG_BYTES_HETEROG} B/cell (heterogeneous, "
                                          f"3-level recurrence) + {FORCE_BYTES_PER_CELL} B/cell "
                                          "on force steps"),
                          "launch_us": launch_s * 1e6,
                          "achieved_storage_form": achieved_storage,
                          "frac_storage_form": achieved_storage / peak,
-                         "storage_bytes_model": (f"{bytes_per_cell} B/cell ((u, d) read + write "
-                                                 f"48 B + medium) + {FORCE_BYTES_PER_CELL} B/cell "
-                                                 "on force steps")},
+                         "storage_bytes_model": (f"{bytes_per_cell:g} B/cell per step ((u, d) read "
+                                                 "+ write 48 B + medium"
+                                                 + (", once per two steps" if two_step else "")
+                                                 + f") + {FORCE_BYTES_PER_CELL} B/cell on force "
+                                                 "steps")},
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": e2e,

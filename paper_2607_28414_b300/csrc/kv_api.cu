@@ -414,7 +414,7 @@ kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_fie
     const int het = (G.where != KV_SCALAR) || (rho.where != KV_SCALAR) || (eta.where != KV_SCALAR);
     if (het != h->het)
         return set_error(h, KV_ERR_ARG, "kv_set_operator: homogeneous/heterogeneous kind differs from kv_create");
-    if (op == KV_OP_DIVERGENCE && h->het && h->precision == KV_FP32 && h->variant == 2)
+    if (op == KV_OP_DIVERGENCE && h->het && h->precision == KV_FP32 && h->variant >= 2)
         return set_error(h, KV_ERR_UNSUPPORTED, "kv_set_operator: the two-step kernel supports only the pointwise operator");
     double dt_max;
     kv_status st = cuda_check(h, cudaStreamSynchronize(h->stream), "kv_set_operator");
@@ -682,7 +682,7 @@ namespace {
 // Direct launches of n steps in the handle's current variant (no graph).
 kv_status launch_steps_direct(kv_handle *h, int n) {
     kv_status st;
-    if (h->precision == KV_FP32 && h->variant == 2) {
+    if (h->precision == KV_FP32 && h->variant >= 2) {
         for (; n >= 2; n -= 2) {
             if ((st = step2_launch(h, h->cur)) != KV_OK) return st;
             h->cur = 1 - h->cur;
@@ -702,7 +702,7 @@ kv_status kv_step(kv_handle *h, int n) {
     if (!h || n < 0) return set_error(h, KV_ERR_ARG, "kv_step: invalid arguments");
     if (h->sticky) return KV_ERR_STATE;
     kv_status st;
-    const bool two = h->precision == KV_FP32 && h->variant == 2;
+    const bool two = h->precision == KV_FP32 && h->variant >= 2;
     const int G = h->graph_steps;  // steps per graph; buffer swaps per graph stay even
     if (n >= G && G > 0 && G % 4 == 0) {
         if (!h->graph[h->cur]) {
@@ -794,12 +794,12 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
 
 kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, int ns) {
     if (!h) return KV_ERR_ARG;
-    if (variant > 2 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
+    if (variant > 3 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
         (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 16) || (ns > 0 && ns != 4 && ns != 6 && ns != 8))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant, tile or stage count");
     const int ntx = tx > 0 ? tx : h->tx, nty = ty > 0 ? ty : h->ty;
     const int nvar = variant >= 0 ? variant : h->variant;
-    if (nvar != 2 && (ntx * nty / 4 < 64 || ntx * nty / 4 > 512))
+    if (nvar < 2 && (ntx * nty / 4 < 64 || ntx * nty / 4 > 512))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: tile %dx%d out of range", ntx, nty);
     cudaStreamSynchronize(h->stream);
     const int old[5] = {h->variant, h->tx, h->ty, h->zc, h->ns_stages};
@@ -845,6 +845,7 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
     struct Cand { int variant, tx, ty, ns, zc; };
     static const int tiles[][2] = {{32, 8}, {32, 16}, {64, 4}, {64, 8}, {64, 16}, {128, 2}, {128, 4}, {128, 8}};
     static const int tiles2[][2] = {{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}};
+    static const int tiles3[][2] = {{32, 8}, {32, 16}, {64, 4}, {64, 8}, {64, 16}, {128, 4}, {128, 8}};
     static const int zcs[] = {16, 32, 64};
     std::vector<Cand> cands;
     for (auto &t : tiles)
@@ -853,6 +854,9 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
     for (auto &t : tiles2)
         for (int ns : {4, 6})
             for (int zc : zcs) cands.push_back({2, t[0], t[1], ns, zc});
+    for (auto &t : tiles3)
+        for (int ns : {4, 6})
+            for (int zc : zcs) cands.push_back({3, t[0], t[1], ns, zc});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(h, KV_ERR_CUDA, "kv_autotune_step: cudaEventCreate failed");

@@ -882,6 +882,286 @@ k_step2_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------------------
+// Two steps per sweep, one displacement component per block (variant 3).
+//
+// The pointwise operator couples the three components of u only through the
+// shared coefficients, so a block can advance a single component c: it stages
+// only (u_c, d_c) (two TMA boxes per plane, fields c and 3 + c of the state
+// tensor) and the coefficient tile, a third of the state bytes of the
+// three-component kernel. The smaller stages let two or three blocks share an
+// SM, which is what the three-component two-step kernel lacks (one block of
+// four warps per SM, bound by latency). Block b of the x dimension is tile
+// b / 3, component b % 3, so the three component blocks of a tile run side by
+// side and two of them read the tile's coefficients from L2. Per node and two
+// steps the DRAM traffic is (u, d) read + write once (48 B) plus the
+// coefficients once (8 B): 28 B per node and step instead of 56 B.
+// The z march, the intermediate ring and the update order are those of
+// k_step2_tma, so the result is bit for bit that of two single steps.
+// ---------------------------------------------------------------------------
+template <int TX, int TY, bool HET>
+struct Tile2C {
+    static constexpr int BX = TX + 8;
+    static constexpr int BYI = TY + 4;
+    static constexpr int BYM = TY + 2;
+    static constexpr int IN_F = BX * BYI;
+    static constexpr int MID_F = BX * BYM;
+    static constexpr int IN_STATE = 2 * IN_F;                 // u_c, d_c
+    static constexpr int IN_COEF = HET ? 2 * MID_F : 0;       // A', B' with a one-node ring
+    static constexpr int IN_STAGE = (IN_STATE + IN_COEF + 31) / 32 * 32;
+    static constexpr int MID_STAGE = (2 * MID_F + 31) / 32 * 32;
+    static constexpr int GXI = BX / 4;
+    static constexpr int MID_GROUPS = GXI * BYM;
+    static constexpr int GX = TX / 4;
+    static constexpr int OUT_GROUPS = GX * TY;
+    static constexpr int NT = OUT_GROUPS;                     // one output group per thread
+    static constexpr int RM = (MID_GROUPS + NT - 1) / NT;     // intermediate groups per thread
+    static constexpr size_t smem(int ns) { return (size_t)(ns * IN_STAGE + 2 * MID_STAGE) * 4 + ns * 8; }
+};
+
+template <int TX, int TY, int NS, bool HET>
+__global__ void __launch_bounds__(TX *TY / 4)
+k_step2c_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
+             const float *__restrict__ F, float *__restrict__ out, StepParams p) {
+    using T2 = Tile2C<TX, TY, HET>;
+    constexpr int RM = T2::RM, NT = T2::NT;
+    extern __shared__ __align__(128) float smem[];
+    float *inr = smem;                                 // NS input stages
+    float *mid = smem + NS * T2::IN_STAGE;             // 2 intermediate planes
+    uint64_t *bars = reinterpret_cast<uint64_t *>(mid + 2 * T2::MID_STAGE);
+    const uint32_t bar0 = smem_u32(bars);
+    const int tid = threadIdx.x;
+    const int comp = (int)(blockIdx.x % 3);
+    const int x0 = (int)(blockIdx.x / 3) * TX, y0 = 1 + blockIdx.y * TY;
+    const int k0 = 1 + blockIdx.z * p.zc;
+    const int k1 = min(k0 + p.zc, p.nz - 1);  // output planes k0..k1-1
+    const int qb = k0 - 2;                     // first staged input plane (may be -1)
+    const long long step = __ldcg(&p.ctrl[kStep]);
+    const float g0 = p.g_const_on ? p.g_const : (step < p.n_g) ? p.g[step] : 0.f;
+    const float g1 = p.g_const_on ? p.g_const : (step + 1 < p.n_g) ? p.g[step + 1] : 0.f;
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const float *Fc = F + comp * p.Np;
+    float *out_u = out + comp * p.Np, *out_d = out + (3 + comp) * p.Np;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto slot = [&](int q) { return (q - qb) % NS; };
+    auto par = [&](int q) { return (uint32_t)(((q - qb) / NS) & 1); };
+    auto midp = [&](int j) { return mid + ((j - (k0 - 1)) & 1) * T2::MID_STAGE; };
+    auto issue = [&](int q) {
+        const uint32_t bar = bar0 + 8 * slot(q);
+        float *st = inr + slot(q) * T2::IN_STAGE;
+        mbar_expect_tx(bar, (T2::IN_STATE + T2::IN_COEF) * 4);
+        tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 2, q, comp, bar);
+        tma_load_4d(smem_u32(st + T2::IN_F), &tm_in, x0 - 4, y0 - 2, q, 3 + comp, bar);
+        if (HET) tma_load_4d(smem_u32(st + T2::IN_STATE), &tm_coef, x0 - 4, y0 - 1, q, 0, bar);
+    };
+    int next_issue = qb;
+    auto refill = [&](int upto) {  // thread 0, after a barrier: stage planes up to `upto`
+        if (tid == 0) {
+            fence_proxy_async();
+            for (; next_issue <= min(k1 + 1, upto); ++next_issue) issue(next_issue);
+        }
+    };
+    if (tid == 0)
+        for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue(next_issue);
+    bool ok = true;
+
+    // z-1 neighbours in registers: input plane j-1 of this thread's
+    // intermediate groups, intermediate plane k-1 of its output group.
+    float4 prev_in[RM][2], prev_mid[2], coef_cur[2], coef_next[2] = {};
+    const int ro_r = tid / T2::GX, ro_gx = tid % T2::GX;      // this thread's output group
+    const int om_out = (ro_r + 1) * T2::BX + 4 + 4 * ro_gx;   // its offset in an intermediate plane
+
+    auto load_prev_in = [&](int j) {
+        const float *sc = inr + slot(j) * T2::IN_STAGE;
+#pragma unroll
+        for (int rr = 0; rr < RM; ++rr) {
+            const int gi = tid + rr * NT;
+            if (gi >= T2::MID_GROUPS) continue;
+            const int r = gi / T2::GXI, cg = gi % T2::GXI;
+            const int oi = (r + 1) * T2::BX + 4 * cg;
+#pragma unroll
+            for (int f = 0; f < 2; ++f) prev_in[rr][f] = *reinterpret_cast<const float4 *>(sc + f * T2::IN_F + oi);
+        }
+    };
+    auto load_out_coef = [&](int k, float4 (&dst)[2]) {
+        if (HET) {
+            const float *cs = inr + slot(k) * T2::IN_STAGE + T2::IN_STATE;
+            dst[0] = *reinterpret_cast<const float4 *>(cs + om_out);
+            dst[1] = *reinterpret_cast<const float4 *>(cs + T2::MID_F + om_out);
+        } else {
+            dst[0] = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+            dst[1] = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+        }
+    };
+    auto load_prev_mid = [&](int j) {
+        const float *mj = midp(j);
+#pragma unroll
+        for (int f = 0; f < 2; ++f) prev_mid[f] = *reinterpret_cast<const float4 *>(mj + f * T2::MID_F + om_out);
+    };
+
+    // intermediate plane j of component comp (input plane j centre and j+1
+    // staged, j-1 in prev_in)
+    auto compute_mid = [&](int j) {
+        float *mj = midp(j);
+        const bool plane_in = (j >= 1 && j <= p.nz - 2);
+        const float *sc = inr + slot(j) * T2::IN_STAGE;
+        const float *sp = inr + slot(j + 1) * T2::IN_STAGE;
+#pragma unroll
+        for (int rr = 0; rr < RM; ++rr) {
+            const int gi = tid + rr * NT;
+            if (gi >= T2::MID_GROUPS) continue;
+            const int r = gi / T2::GXI, cg = gi % T2::GXI;
+            const int y = y0 - 1 + r, x = x0 - 4 + 4 * cg;
+            const int oi = (r + 1) * T2::BX + 4 * cg;
+            const int om = r * T2::BX + 4 * cg;
+            const bool row_in = plane_in && y >= 1 && y <= p.ny - 2;
+            bool m[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) m[e] = row_in && (x + e >= 1) && (x + e <= p.nx - 2);
+            float4 A4, B4;
+            if (HET) {
+                A4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + om);
+                B4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + T2::MID_F + om);
+            } else {
+                A4 = make_float4((float)p.A, (float)p.A, (float)p.A, (float)p.A);
+                B4 = make_float4((float)p.B, (float)p.B, (float)p.B, (float)p.B);
+            }
+            float4 ctr[2], sum[2];
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const float *fc = sc + f * T2::IN_F + oi;
+                const float4 c = *reinterpret_cast<const float4 *>(fc);
+                const float4 ym = *reinterpret_cast<const float4 *>(fc - T2::BX);
+                const float4 yp = *reinterpret_cast<const float4 *>(fc + T2::BX);
+                const float4 zm = prev_in[rr][f];
+                const float4 zp = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
+                const float left = (cg == 0) ? 0.f : fc[-1];
+                const float right = (cg == T2::GXI - 1) ? 0.f : fc[4];
+                float4 s4;
+                s4.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+                s4.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+                s4.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+                s4.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+                ctr[f] = c;
+                sum[f] = s4;
+                prev_in[rr][f] = c;
+            }
+            float Fv[4] = {0.f, 0.f, 0.f, 0.f};
+            if (g0 != 0.f) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (m[e]) Fv[e] = Fc[(long long)j * sz + (long long)y * sy + x + e];
+            }
+            const float4 u = ctr[0], su = sum[0], d = ctr[1], sd = sum[1];
+            float4 uo, dn;
+            kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g0, Fv[0], uo.x, dn.x);
+            kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g0, Fv[1], uo.y, dn.y);
+            kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g0, Fv[2], uo.z, dn.z);
+            kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g0, Fv[3], uo.w, dn.w);
+            if (!m[0]) uo.x = dn.x = 0.f;
+            if (!m[1]) uo.y = dn.y = 0.f;
+            if (!m[2]) uo.z = dn.z = 0.f;
+            if (!m[3]) uo.w = dn.w = 0.f;
+            *reinterpret_cast<float4 *>(mj + om) = uo;
+            *reinterpret_cast<float4 *>(mj + T2::MID_F + om) = dn;
+        }
+    };
+
+    // Prologue, as in k_step2_tma.
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(qb), par(qb));
+    load_prev_in(qb);
+    __syncthreads();
+    refill(qb + NS);
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 - 1), par(k0 - 1));
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0), par(k0));
+    compute_mid(k0 - 1);
+    __syncthreads();
+    refill(k0 - 1 + NS);
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 + 1), par(k0 + 1));
+    compute_mid(k0);
+    load_out_coef(k0, coef_cur);
+    __syncthreads();  // intermediate planes k0-1 and k0 complete
+    load_prev_mid(k0 - 1);
+    refill(k0 + NS);
+    __syncthreads();  // plane k0-1's slot is read: the loop's first intermediate plane overwrites it
+
+    const int y_out = y0 + ro_r, x_out = x0 + 4 * ro_gx;
+    const bool row_ok = (y_out <= p.ny - 2) && (x_out < p.px);
+    const bool m0 = (x_out >= 1) && (x_out <= p.nx - 2), m1 = (x_out + 1 <= p.nx - 2);
+    const bool m2 = (x_out + 2 <= p.nx - 2), m3 = (x_out + 3 <= p.nx - 2);
+    for (int k = k0; k < k1; ++k) {
+        ok &= mbar_wait_bounded(bar0 + 8 * slot(k + 2), par(k + 2));
+        compute_mid(k + 1);  // into the slot of intermediate plane k-1 (now in prev_mid)
+        if (k + 1 < k1) load_out_coef(k + 1, coef_next);
+        __syncthreads();     // intermediate plane k+1 complete; input plane k+1 consumed
+        refill(k + 1 + NS);
+        // sensors of the intermediate step owned by this block (plane k, component comp)
+        if (p.ns > 0 && step < p.cap) {
+            const float *mk = midp(k);
+            float *tr = reinterpret_cast<float *>(p.traces) + (size_t)step * p.ns * 3;
+            for (int q = p.sens_off[k] + tid; q < p.sens_off[k + 1]; q += NT) {
+                const int s = p.sens_ord[q];
+                const int i = p.sensors[3 * s], jj = p.sensors[3 * s + 1];
+                if (i >= x0 && i < x0 + TX && jj >= y0 && jj < y0 + TY && jj <= p.ny - 2)
+                    tr[3 * s + comp] = mk[(jj - y0 + 1) * T2::BX + (i - x0 + 4)];
+            }
+        }
+        // final step of plane k from intermediate planes k-1 (registers), k, k+1
+        const float *mc = midp(k);
+        const float *mp = midp(k + 1);
+        float4 ctr[2], sum[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const float *fc = mc + f * T2::MID_F + om_out;
+            const float4 c = *reinterpret_cast<const float4 *>(fc);
+            const float4 ym = *reinterpret_cast<const float4 *>(fc - T2::BX);
+            const float4 yp = *reinterpret_cast<const float4 *>(fc + T2::BX);
+            const float4 zm = prev_mid[f];
+            const float4 zp = *reinterpret_cast<const float4 *>(mp + f * T2::MID_F + om_out);
+            const float left = fc[-1], right = fc[4];
+            float4 s4;
+            s4.x = kv_add(kv_add(kv_add(left, c.y), kv_add(ym.x, yp.x)), kv_add(zm.x, zp.x));
+            s4.y = kv_add(kv_add(kv_add(c.x, c.z), kv_add(ym.y, yp.y)), kv_add(zm.y, zp.y));
+            s4.z = kv_add(kv_add(kv_add(c.y, c.w), kv_add(ym.z, yp.z)), kv_add(zm.z, zp.z));
+            s4.w = kv_add(kv_add(kv_add(c.z, right), kv_add(ym.w, yp.w)), kv_add(zm.w, zp.w));
+            ctr[f] = c;
+            sum[f] = s4;
+            prev_mid[f] = c;
+        }
+        if (row_ok) {
+            const long long gbase = k * sz + (long long)y_out * sy + x_out;
+            float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g1 != 0.f) F4 = __ldg(reinterpret_cast<const float4 *>(Fc + gbase));
+            const float4 A4 = coef_cur[0], B4 = coef_cur[1];
+            const float4 u = ctr[0], su = sum[0], d = ctr[1], sd = sum[1];
+            float4 uo, dn;
+            kv_update(u.x, su.x, d.x, sd.x, A4.x, B4.x, g1, F4.x, uo.x, dn.x);
+            kv_update(u.y, su.y, d.y, sd.y, A4.y, B4.y, g1, F4.y, uo.y, dn.y);
+            kv_update(u.z, su.z, d.z, sd.z, A4.z, B4.z, g1, F4.z, uo.z, dn.z);
+            kv_update(u.w, su.w, d.w, sd.w, A4.w, B4.w, g1, F4.w, uo.w, dn.w);
+            if (!m0) uo.x = dn.x = 0.f;
+            if (!m1) uo.y = dn.y = 0.f;
+            if (!m2) uo.z = dn.z = 0.f;
+            if (!m3) uo.w = dn.w = 0.f;
+            *reinterpret_cast<float4 *>(out_u + gbase) = uo;
+            *reinterpret_cast<float4 *>(out_d + gbase) = dn;
+        }
+        coef_cur[0] = coef_next[0];
+        coef_cur[1] = coef_next[1];
+        __syncthreads();  // intermediate plane k is no longer read: its slot takes plane k+2
+    }
+    if (__syncthreads_or(!ok) && tid == 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
+        for (int q = qb; q < next_issue; ++q) mbar_wait_bounded(bar0 + 8 * slot(q), par(q));
+    }
+    step_epilogue_n<float>(out, p, step, 2);
+}
+
+// ---------------------------------------------------------------------------
 // Small kernels: medium fold, initial velocity
 // ---------------------------------------------------------------------------
 // Grid: (ceil(px/128), ny, nz), block 128.
@@ -1074,7 +1354,37 @@ static bool pick2_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int
            pick2<128, 4, NS>(tx, ty, NS, het, k, smem, nt);
 }
 
-static bool tma2_kernel_for(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+template <int TX, int TY, int NS>
+static bool pick2c(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (tx != TX || ty != TY || ns != NS) return false;
+    if (het) {
+        *k = k_step2c_tma<TX, TY, NS, true>;
+        *smem = Tile2C<TX, TY, true>::smem(NS);
+    } else {
+        *k = k_step2c_tma<TX, TY, NS, false>;
+        *smem = Tile2C<TX, TY, false>::smem(NS);
+    }
+    *nt = TX * TY / 4;
+    return true;
+}
+
+template <int NS>
+static bool pick2c_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    return pick2c<32, 8, NS>(tx, ty, NS, het, k, smem, nt) || pick2c<32, 16, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick2c<64, 4, NS>(tx, ty, NS, het, k, smem, nt) || pick2c<64, 8, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick2c<64, 16, NS>(tx, ty, NS, het, k, smem, nt) || pick2c<128, 4, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick2c<128, 8, NS>(tx, ty, NS, het, k, smem, nt);
+}
+
+// variant 2: three components per block; variant 3: one component per block
+static bool tma2_kernel_for(int variant, int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (variant == 3) {
+        switch (ns) {
+            case 4: return pick2c_tile<4>(tx, ty, het, k, smem, nt);
+            case 6: return pick2c_tile<6>(tx, ty, het, k, smem, nt);
+            default: return false;
+        }
+    }
     switch (ns) {
         case 4: return pick2_tile<4>(tx, ty, het, k, smem, nt);
         case 6: return pick2_tile<6>(tx, ty, het, k, smem, nt);
@@ -1130,18 +1440,20 @@ kv_status step_prepare(kv_handle *h) {
     TmaKernel k;
     size_t smem;
     int nt;
-    if (h->variant == 2) {
+    if (h->variant == 2 || h->variant == 3) {
         if (step_kind(h) == kKindDiv)
-            return set_error(h, KV_ERR_UNSUPPORTED, "the two-step kernel supports only the pointwise operator");
-        if (!tma2_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
-            return set_error(h, KV_ERR_ARG, "no two-step kernel for tile %dx%d with %d stages", h->tx, h->ty,
-                             h->ns_stages);
+            return set_error(h, KV_ERR_UNSUPPORTED, "the two-step kernels support only the pointwise operator");
+        if (!tma2_kernel_for(h->variant, h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
+            return set_error(h, KV_ERR_ARG, "no two-step kernel (variant %d) for tile %dx%d with %d stages",
+                             h->variant, h->tx, h->ty, h->ns_stages);
         if (smem > 227 * 1024)
             return set_error(h, KV_ERR_ARG, "two-step tile %dx%d with %d stages needs %zu bytes of shared memory",
                              h->tx, h->ty, h->ns_stages, smem);
         kv_status st;
+        // variant 3 stages one field per box (u_c and d_c are fields c and 3 + c)
+        const int fbox = h->variant == 3 ? 1 : 6;
         for (int b = 0; b < 2; ++b)
-            if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 4, 6)) != KV_OK)
+            if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 4, fbox)) != KV_OK)
                 return st;
         if (h->het && (st = encode_tensor_4d(h, &h->tm_coef, h->coef, 2, h->tx + 8, h->ty + 2, 2)) != KV_OK)
             return st;
@@ -1199,7 +1511,7 @@ static StepParams make_params(kv_handle *h, int nblocks) {
     return p;
 }
 
-// Two steps from state[from] into state[1 - from] (variant 2).
+// Two steps from state[from] into state[1 - from] (variants 2 and 3).
 kv_status step2_launch(kv_handle *h, int from) {
     if (!h->tma_ready) {
         kv_status st = step_prepare(h);
@@ -1208,8 +1520,10 @@ kv_status step2_launch(kv_handle *h, int from) {
     TmaKernel k;
     size_t smem;
     int nt;
-    tma2_kernel_for(h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt);
-    dim3 grid((h->px + h->tx - 1) / h->tx, (h->ny - 2 + h->ty - 1) / h->ty, (h->nz - 2 + h->zc - 1) / h->zc);
+    tma2_kernel_for(h->variant, h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt);
+    const int ncomp_blocks = h->variant == 3 ? 3 : 1;  // variant 3: the three components of a tile side by side
+    dim3 grid(ncomp_blocks * ((h->px + h->tx - 1) / h->tx), (h->ny - 2 + h->ty - 1) / h->ty,
+              (h->nz - 2 + h->zc - 1) / h->zc);
     StepParams p = make_params(h, grid.x * grid.y * grid.z);
     k<<<grid, nt, smem, h->stream>>>(h->tm_state[from], h->tm_coef, (const float *)h->F,
                                      (float *)h->state[1 - from], p);
