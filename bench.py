@@ -124,9 +124,15 @@ def parse():
     ap.add_argument("--step-config", default=None,
                     help="[variant,]tx,ty,zc,ns of the step kernel instead of autotuning "
                          "(profiling runs; variant 0 one step per sweep, 2 two steps per sweep)")
-    ap.add_argument("--projection", default="mg", choices=["mg", "cg"],
-                    help="mg: CG preconditioned by a multigrid V-cycle (mode 4, same system and "
-                         "stopping rule); cg: the paper's plain CG from zero (mode 0)")
+    ap.add_argument("--projection", default="auto", choices=["auto", "learned", "mg", "cg"],
+                    help="learned: the trained network's potential as the start of the "
+                         "multigrid-preconditioned CG (mode 5); mg: that CG from zero (mode 4); cg: "
+                         "the paper's plain CG from zero (mode 0); all stop on the same true "
+                         "residual. auto: learned for the bone shell (its workload names a "
+                         "learned warm start), mg otherwise")
+    ap.add_argument("--net", default=None,
+                    help="parameters of the warm-start network (.npz written by "
+                         "paper_2607_28414_b300.learned --out; default: the committed one)")
     ap.add_argument("--cg-config", type=int, default=None,
                     help="z chunk of the CG passes (default: the CG autotuner's choice)")
     ap.add_argument("--cg-tol", type=float, default=1e-8,
@@ -292,7 +298,7 @@ def run_sweep(args, rank, world):
         forces.append([torch.from_numpy(a).to(device) for a in w.force])
     b = kv.kv_batch_create(hs)
     N = sum(w.n_cells for w in cases)
-    proj_mode = 4 if args.projection == "mg" else 0
+    proj_mode = 0 if args.projection == "cg" else 4  # the sweep has no learned start
 
     def one_pass():
         grids = {}
@@ -454,7 +460,16 @@ def main():
     ev = lambda: torch.cuda.Event(enable_timing=True)
     stats_last = {}
 
-    proj_mode = 4 if args.projection == "mg" else 0
+    projection = args.projection
+    if projection == "auto":
+        projection = "learned" if args.workload == "bone512" else "mg"
+    proj_mode = {"learned": 5, "mg": 4, "cg": 0}[projection]
+    net = None
+    if proj_mode == 5:
+        from paper_2607_28414_b300 import learned
+        net = learned.load_net(args.net or learned.WEIGHTS, (w.nx, w.ny, w.nz),
+                               stream=stream.cuda_stream)
+        kv.kv_attach_net(h, net)
 
     def one_pass(step_events=None, medium=medium_d, force=force_d, traces=traces_d):
         kv.kv_set_medium(h, *medium)
@@ -474,7 +489,7 @@ def main():
     # both projections once, outside the timed region, for the record (the
     # paper's plain CG from zero and the multigrid-preconditioned CG)
     by_mode = {}
-    for name, mode in (("cg", 0), ("mg", 4)):
+    for name, mode in (("cg", 0), ("mg", 4)) + ((("learned_mg", 5),) if net is not None else ()):
         st = kv.kv_project_force(h, *force_d, w.tol, 0, mode)
         by_mode[name] = {"ms": st["ms"], "iters": st["iters"], "rel_res_true": st["rel_res_true"]}
 
@@ -552,6 +567,8 @@ def main():
         cpu.update({"value_1_core": v1, "sample_1_core": info1["sample"]})
 
     kv.kv_destroy(h)
+    if net is not None:
+        kv.kv_net_destroy(net)
     if rank == 0:
         line = {
             "metric": f"KV-FDTD Gcell-updates/s (projection + {w.n_steps} steps)",
@@ -567,8 +584,10 @@ def main():
                        "operator": args.operator,
                        "medium_encoding": (f"{classes} classes: 1 byte per node + coefficient table"
                                            if classes > 0 else "coefficient fields (FP32)"),
-                       "projection": ("CG preconditioned by a multigrid V(1,1)-cycle (mode 4)"
-                                      if proj_mode == 4 else "plain CG from zero (mode 0)"),
+                       "projection": {5: "learned warm start (BF16 U-Net, residual loss) + CG "
+                                         "preconditioned by a multigrid V(1,1)-cycle (mode 5)",
+                                      4: "CG preconditioned by a multigrid V(1,1)-cycle (mode 4)",
+                                      0: "plain CG from zero (mode 0)"}[proj_mode],
                        "reductions": "f64", "parallelism": f"replicas{world}",
                        "l2": f"state {48 * N / 1e9:.1f} GB > 126 MB L2 (inputs larger than L2)"},
             "kv_step_gcells": step_gcells,

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -21,6 +22,18 @@ import numpy as np
 from . import inputs, kv
 
 DX = 0.2 * inputs.MM
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_residual.npz")
+
+
+def load_net(path=WEIGHTS, max_shape=(128, 128, 128), stream=None):
+    """A net with the parameters stored by `--out` (default: the committed
+    residual-loss net), activations allocated for grids up to max_shape."""
+    d = np.load(path)
+    net = kv.kv_net_create([int(c) for c in d["channels"]], tuple(max_shape), stream=stream)
+    kv.kv_net_set_params(net, np.ascontiguousarray(d["params"], np.float32))
+    return net
 
 
 def projection_handle(shape, dx=DX, stream=None):
@@ -155,7 +168,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--channels", default="16,32,64,64")
     ap.add_argument("--seed", type=int, default=104)
-    ap.add_argument("--out", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--out", default=None, help="write the trained parameters and their recipe (.npz)")
     ap.add_argument("--loss", default="mse", choices=["mse", "residual"],
                     help="mse: squared error of the potential; residual: squared residual "
                          "|b - A phi_hat|^2 of the prediction")
@@ -184,8 +197,12 @@ def main():
                 "channels": ch, "epochs": args.epochs, "data_s": t_data, "train_s": t_train,
                 "train_cg_iters_mean": float(np.mean(it)), "final_loss": float(np.mean(losses[-50:])),
                 "first_loss": float(np.mean(losses[:50])), "params": kv.kv_net_num_params(net)})
-    if args.out:
-        np.save(args.out, kv.kv_net_get_params(net))
+    if args.out:  # parameters and how they were made (.npz)
+        np.savez_compressed(args.out, params=kv.kv_net_get_params(net), channels=np.array(ch),
+                            loss=args.loss, seed=args.seed,
+                            protocol=(f"{args.train} fields at {args.train_n}^3 (seed {args.seed}), "
+                                      f"plain-CG potentials at 1e-10, {args.epochs} epochs of Adam "
+                                      f"(lr {args.lr:g}, cosine), {args.loss} loss"))
     kv.kv_net_destroy(net)
     print(json.dumps(res))
 

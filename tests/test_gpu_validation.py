@@ -6,7 +6,8 @@ Four homogeneous phantoms (G = 1, 2, 5, 10 kPa, rho = 1000, eta = 0) on
 0.62 / 1.1 mm, focus 30 mm deep, 167 us), solenoidal projection to 1e-8,
 dt = 0.5 x the stability limit. The group speed from cross-correlating the
 axial velocity traces at lateral offsets 4-14 mm must match sqrt(G/rho); the
-paper reports ~1 % for all four, the gate here is 2 %.
+paper reports ~1 % for all four (Sec. 4.4), the gate here is 1.2 % (the runs
+measure -0.94 ... -1.15 %).
 """
 import numpy as np
 import pytest
@@ -36,7 +37,7 @@ def test_qiba_phantom_group_speed(device, G):
     c = np.sqrt(G / 1000.0)
     print(f"QIBA G = {G / 1e3:.0f} kPa: group speed {c_est:.4f} m/s vs {c:.4f} "
           f"({100 * (c_est - c) / c:+.2f} %), {n_steps} steps, CG {st['iters']}")
-    assert abs(c_est - c) / c < 0.02
+    assert abs(c_est - c) / c < 0.012
 
 
 # ---------------------------------------------------------------------------
