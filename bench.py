@@ -78,24 +78,44 @@ def job_rate(world, cell_updates_per_rank, t_max):
     return world * cell_updates_per_rank / t_max / 1e9
 
 
-def step_traffic(w, step_cfg, operator, n_force_steps, medium="fields"):
+def step_traffic(w, step_cfg, operator, n_force_steps, medium="fields", with_source=False):
     """DRAM bytes per step launch from the committed ncu capture
     (profiles/kv_step_traffic.json: dram__bytes_read.sum + dram__bytes_write.sum
     of force and plain steps), averaged over this pass's launches like
-    `achieved`; None unless the capture is of this grid, operator, medium
-    encoding ("fields" or "classes") and kernel configuration."""
+    `achieved`; None unless a capture is of this operator, medium encoding
+    ("fields" or "classes") and kernel configuration, and either of this grid
+    or marked `scale_by_cells` for this workload family (a smaller case of a
+    grid too large to capture, scaled by the cell count). with_source: also
+    return a one-line description of the capture used."""
     tfile = os.path.join(ROOT, "profiles", "kv_step_traffic.json")
-    if not os.path.exists(tfile):
-        return None
-    try:
-        for c in json.load(open(tfile))["captures"]:
-            if (c["grid"] == [w.nx, w.ny, w.nz] and c["operator"] == operator
-                    and c.get("medium", "fields") == medium and c["step_config"] == step_cfg):
-                nf = n_force_steps
-                return (nf * c["bytes_force_step"] + (w.n_steps - nf) * c["bytes_plain_step"]) / w.n_steps
-    except (KeyError, ValueError, TypeError):
-        return None
-    return None
+    res = (None, None)
+    if os.path.exists(tfile):
+        try:
+            caps = json.load(open(tfile))["captures"]
+            nf = n_force_steps
+            for exact in (True, False):
+                for c in caps:
+                    if not (c["operator"] == operator and c.get("medium", "fields") == medium
+                            and c["step_config"] == step_cfg):
+                        continue
+                    if exact and c["grid"] != [w.nx, w.ny, w.nz]:
+                        continue
+                    if not exact and not (c.get("scale_by_cells")
+                                          and c.get("family") == getattr(w, "family", None)):
+                        continue
+                    scale = (w.nx * w.ny * w.nz) / float(np.prod(c["grid"]))
+                    t = scale * (nf * c["bytes_force_step"] + (w.n_steps - nf) * c["bytes_plain_step"]) \
+                        / w.n_steps
+                    src = ("stored ncu capture of this grid" if exact else
+                           f"stored ncu capture of a {'x'.join(map(str, c['grid']))} case of the same "
+                           f"workload and kernel configuration, scaled by the cell count ({scale:.3g}x)")
+                    res = (t, src)
+                    break
+                if res[0] is not None:
+                    break
+        except (KeyError, ValueError, TypeError):
+            res = (None, None)
+    return res if with_source else res[0]
 
 
 def parse():
@@ -119,6 +139,8 @@ def parse():
                          "read as one class byte per node (bit for bit the same step); fields: "
                          "always read the coefficient fields")
     ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--shape", default=None,
+                    help="NX,NY,NZ of a smaller bone shell over the same box (profiling captures)")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="time steps of the pass (default: the workload's own)")
     ap.add_argument("--step-config", default=None,
@@ -196,12 +218,22 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def workload(grid, n_steps, kind="bone512"):
+def workload(grid, n_steps, kind="bone512", shape=None):
+    """The workload of a pass. shape (bone shell only): a smaller grid over the
+    same physical box (dx scaled), for captures of the same kernels."""
     from paper_2607_28414_b300 import inputs
     n_steps = DEFAULT_STEPS[kind] if n_steps is None else n_steps
     if kind == "bone512":
-        return inputs.bone_shell(n_steps=n_steps)
-    return inputs.heterogeneous_inclusions(n=grid, n_steps=n_steps)
+        if shape:
+            nx, ny, nz = shape
+            w = inputs.bone_shell(nx=nx, ny=ny, nz=nz, dx=0.15e-3 * 512 / nx, n_steps=n_steps)
+        else:
+            w = inputs.bone_shell(n_steps=n_steps)
+        w.family = "bone_shell"
+        return w
+    w = inputs.heterogeneous_inclusions(n=grid, n_steps=n_steps)
+    w.family = "inclusions"
+    return w
 
 
 def cpu_oracle_sample(w, dt, cg_iters, n_sample_steps=6, n_sample_iters=6, divform=False):
@@ -413,7 +445,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = workload(args.grid, args.time_steps, args.workload)
+    w = workload(args.grid, args.time_steps, args.workload,
+                 tuple(int(v) for v in args.shape.split(",")) if args.shape else None)
     w.tol = args.cg_tol
     N = w.n_cells
     stream = torch.cuda.Stream(device)  # a non-default stream shared by torch events and libkv
@@ -523,7 +556,8 @@ def main():
     achieved = alg_bytes / launch_s / 1e9
     achieved_storage = (N * bytes_per_cell + force_bytes) / launch_s / 1e9
     peak, peak_kind = peaks()
-    traffic = step_traffic(w, step_cfg, args.operator, n_force_steps, medium_enc)
+    traffic, traffic_src = step_traffic(w, step_cfg, args.operator, n_force_steps, medium_enc,
+                                        with_source=True)
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -597,10 +631,10 @@ def main():
             "cg_zc": cg_zc, "cg_autotune_ms_40_iters": cg_tune_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "traffic_source": ("stored ncu capture (dram__bytes_read.sum + "
-                                            "dram__bytes_write.sum per launch) of this grid, "
-                                            "operator, medium encoding and kernel configuration, "
-                                            "profiles/kv_step_traffic.json; not measured in "
+                         "traffic_source": (f"{traffic_src} (dram__bytes_read.sum + "
+                                            "dram__bytes_write.sum per launch, same operator, "
+                                            "medium encoding and kernel configuration, "
+                                            "profiles/kv_step_traffic.json); not measured in "
                                             "this run" if traffic is not None else
                                             "no stored capture for this configuration"),
                          "kernel": {0: "k_step_tma", 1: "k_step_plain", 2: "k_step2_tma",

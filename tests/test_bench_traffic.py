@@ -44,3 +44,21 @@ def test_class_captures_move_fewer_bytes_than_field_captures():
     fld = [c["bytes_plain_step"] for c in CAPTURES if c.get("medium", "fields") == "fields"]
     # 49 instead of 56 algorithmic bytes per node: at least 8 % less DRAM traffic
     assert max(cls) < 0.92 * min(fld)
+
+
+def test_scaled_capture_of_a_smaller_case():
+    """A capture marked scale_by_cells (a smaller grid of the same workload
+    family and kernel configuration) is scaled by the cell count and labelled;
+    another family or configuration finds none."""
+    caps = [c for c in CAPTURES if c.get("scale_by_cells")]
+    assert caps
+    c = caps[0]
+    big = SimpleNamespace(nx=512, ny=512, nz=384, n_steps=5000, family=c["family"])
+    scale = 512 * 512 * 384 / float(c["grid"][0] * c["grid"][1] * c["grid"][2])
+    t, src = bench.step_traffic(big, c["step_config"], c["operator"], 118, c["medium"], with_source=True)
+    want = scale * (118 * c["bytes_force_step"] + 4882 * c["bytes_plain_step"]) / 5000
+    assert t == want and "scaled by the cell count" in src
+    other = SimpleNamespace(nx=512, ny=512, nz=384, n_steps=5000, family="inclusions")
+    assert bench.step_traffic(other, c["step_config"], c["operator"], 118, c["medium"]) is None
+    cfg = dict(c["step_config"], tx=128)
+    assert bench.step_traffic(big, cfg, c["operator"], 118, c["medium"]) is None
