@@ -216,7 +216,12 @@ kv_status kv_set_initial_velocity(kv_handle *h, kv_field vx, kv_field vy, kv_fie
  * same stopping rule, far fewer iterations; FP32 handles only, and the first
  * mode-4 call allocates the level arrays, about 2.3 floats per node);
  * 5 = the learned initial guess of mode 1, then the preconditioned CG of
- * mode 4; other values KV_ERR_UNSUPPORTED. fs_out: NULL, or a device
+ * mode 4; 2 = flexible CG with the attached net as preconditioner (z = Net(r)
+ * each iteration, Polak-Ribiere beta; FP64 vectors, allocated on the first
+ * mode-2 call, 5 doubles per node; not in the paper: same system and stopping
+ * rule, checked on the true residual); modes 1, 2 and 5 without an attached
+ * net that fits the grid: KV_ERR_STATE; other values KV_ERR_UNSUPPORTED.
+ * fs_out: NULL, or a device
  * pointer to 3*nx*ny*nz floats (component-major) that receives f_S0.
  * stats: NULL or filled. Returns KV_OK, KV_CG_MAXITER, KV_CG_BREAKDOWN or
  * KV_ERR_NONFINITE (the stats say which). A zero right-hand side gives

@@ -253,7 +253,7 @@ kv_status kv_destroy(kv_handle *h) {
     medium_labels_free(h);
     void *dev[] = {h->state[0], h->state[1], h->F, h->coef, h->S, h->g_dev, h->sens_dev,
                    h->traces, h->ctrl, h->cgv, h->phi, h->b, h->scal,
-                   h->partials, h->fstage, h->dtmin, h->mg_pool};
+                   h->partials, h->fstage, h->dtmin, h->mg_pool, h->fcg_pool};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (h->ctrl_host) cudaFreeHost(h->ctrl_host);
@@ -563,12 +563,12 @@ kv_status kv_project_force(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, 
                            int max_iter, int mode, float *fs_out, kv_cg_stats *stats) {
     if (!h) return KV_ERR_ARG;
     if (h->sticky) return KV_ERR_STATE;
-    if (mode != 0 && mode != 1 && mode != 3 && mode != 4 && mode != 5)
+    if (mode < 0 || mode > 5)
         return set_error(h, KV_ERR_UNSUPPORTED, "projection mode %d is not available", mode);
     if ((mode == 4 || mode == 5) && h->precision != KV_FP32)
         return set_error(h, KV_ERR_UNSUPPORTED, "projection modes 4 and 5 (multigrid-preconditioned CG) need an FP32 handle");
-    if ((mode == 1 || mode == 5) && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
-        return set_error(h, KV_ERR_STATE, "modes 1 and 5 need a network attached with kv_attach_net that fits the grid");
+    if ((mode == 1 || mode == 2 || mode == 5) && (!h->net || !kv_net_fits(h->net, h->nx, h->ny, h->nz)))
+        return set_error(h, KV_ERR_STATE, "modes 1, 2 and 5 need a network attached with kv_attach_net that fits the grid");
     if (!(tol > 0.0)) return set_error(h, KV_ERR_ARG, "tol must be > 0");
     const kv_field *f[3] = {&fx, &fy, &fz};
     for (auto *q : f)

@@ -863,8 +863,13 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
         if ((e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s)) != cudaSuccess)
             return cuda_check(h, e, "projection memset");
     }
+    int fcg_iters = 0;
+    double fcg_true2 = 0.0;
     if (!isfinite(bb)) {
         status = KV_ERR_NONFINITE;
+    } else if (bb > 0.0 && mode == 2) {  // flexible CG with the network as preconditioner
+        kv_status fs = project_fcg(h, tol, max_iter, &status, &fcg_iters, &fcg_true2, bb);
+        if (fs != KV_OK) return fs;
     } else if (bb > 0.0) {
         const int chunk = pcg ? 4 : 32;  // iterations queued between polls of the control word
         while (true) {
@@ -912,11 +917,12 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
         return set_error(h, KV_ERR_TIMEOUT, "a bounded device wait timed out in a CG kernel");
     }
     if (st) {
-        st->iters = (int)h->ctrl_host[kCgIters];
-        st->refinements = (int)std::max(0ll, h->ctrl_host[kCgRefine] - 1);
+        st->iters = mode == 2 ? fcg_iters : (int)h->ctrl_host[kCgIters];
+        st->refinements = mode == 2 ? 0 : (int)std::max(0ll, h->ctrl_host[kCgRefine] - 1);
         st->status = status;
-        st->rel_res_true = bb > 0.0 ? sqrt(h->scal_host[kTrue2] / bb) : 0.0;
-        st->rel_res_recursive = bb > 0.0 ? sqrt(h->scal_host[kRRLast] / bb) : 0.0;
+        const double t2 = mode == 2 ? fcg_true2 : h->scal_host[kTrue2];
+        st->rel_res_true = bb > 0.0 ? sqrt(t2 / bb) : 0.0;
+        st->rel_res_recursive = bb > 0.0 ? sqrt((mode == 2 ? fcg_true2 : h->scal_host[kRRLast]) / bb) : 0.0;
         st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                      .count();
     }
@@ -924,7 +930,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     if (status == KV_CG_BREAKDOWN) return set_error(h, KV_CG_BREAKDOWN, "CG breakdown (p.Ap <= 0)");
     if (status == KV_CG_MAXITER) {
         snprintf(h->err, sizeof(h->err), "CG reached max_iter=%d, true rel. residual %.3e", max_iter,
-                 bb > 0.0 ? sqrt(h->scal_host[kTrue2] / bb) : 0.0);
+                 bb > 0.0 ? sqrt((mode == 2 ? fcg_true2 : h->scal_host[kTrue2]) / bb) : 0.0);
         return KV_CG_MAXITER;
     }
     return KV_OK;

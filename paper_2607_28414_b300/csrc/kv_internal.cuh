@@ -172,6 +172,7 @@ struct kv_handle {
     int mg_levels;
     kv::MgLevel mg[kv::kMgMaxLevels];
     float *mg_pool;        // all level arrays in one allocation
+    double *fcg_pool;      // flexible CG (mode 2) vectors, allocated on first use
     CUtensorMap tm_mg_r;   // TMA view of the fine residual (mg[0].r)
     double *phi;           // [Np]
     double *b;             // [Np] right-hand side
@@ -262,6 +263,9 @@ void medium_labels_free(kv_handle *h);
 
 // Projection kernels (kv_cg.cu)
 kv_status project(kv_handle *h, double tol, int max_iter, int mode, float *fs_out, kv_cg_stats *st);
+// Flexible CG with the attached network as preconditioner (projection mode 2, kv_fcg.cu)
+kv_status project_fcg(kv_handle *h, double tol, int max_iter, int *status, int *iters, double *true2,
+                      double bb);
 
 // Multigrid preconditioner (kv_mg.cu): level setup and one application
 // z = M r from mg[0].r into cgv field 1, with r.z reduced into scal[kRR].

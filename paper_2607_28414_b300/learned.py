@@ -83,13 +83,14 @@ def train(net, B, P, shape, epochs=3, lr=1e-3, dx=DX, seed=0, log=None):
     return losses
 
 
-MODES = {0: "plain", 1: "learned", 4: "mg", 5: "learned_mg"}
+MODES = {0: "plain", 1: "learned", 2: "fcg", 4: "mg", 5: "learned_mg"}
 
 
 def evaluate(net, shape, forces, tol=1e-8, dx=DX, device="cuda:0", modes=(0, 1, 4, 5)):
     """Projection of each field at the same tolerance with each mode: 0 the
-    paper's CG from zero, 1 the learned start, 4 multigrid-preconditioned CG
-    from zero, 5 the learned start with the multigrid-preconditioned CG.
+    paper's CG from zero, 1 the learned start, 2 flexible CG with the net as
+    preconditioner, 4 multigrid-preconditioned CG from zero, 5 the learned
+    start with the multigrid-preconditioned CG.
     Returns mean iterations and milliseconds per mode (keys <name>_iters,
     <name>_ms, max_rel_res_<name>) and the wall-time ratios to mode 0."""
     h = projection_handle(shape, dx)
@@ -169,6 +170,10 @@ def main():
     ap.add_argument("--channels", default="16,32,64,64")
     ap.add_argument("--seed", type=int, default=104)
     ap.add_argument("--out", default=None, help="write the trained parameters and their recipe (.npz)")
+    ap.add_argument("--modes", default="0,1,4,5",
+                    help="projection modes compared on the held-out fields (2: flexible CG)")
+    ap.add_argument("--load", default=None,
+                    help="evaluate the parameters of this .npz (from --out) instead of training")
     ap.add_argument("--loss", default="mse", choices=["mse", "residual"],
                     help="mse: squared error of the potential; residual: squared residual "
                          "|b - A phi_hat|^2 of the prediction")
@@ -180,6 +185,17 @@ def main():
     device = torch.device("cuda:0")
     tshape = (args.train_n,) * 3
     eshape = (args.eval_n,) * 3
+    modes = tuple(int(m) for m in args.modes.split(","))
+    held = lambda: inputs.random_gaussian_forces_torch(args.eval, eshape, DX, args.seed + 1_000_000, device)
+    if args.load:  # evaluation of stored parameters only
+        net = load_net(args.load, eshape)
+        res = evaluate(net, eshape, held(), modes=modes)
+        d = np.load(args.load)
+        res.update({"params_file": os.path.basename(args.load), "loss": str(d["loss"]),
+                    "protocol": str(d["protocol"]), "eval_shape": eshape})
+        kv.kv_net_destroy(net)
+        print(json.dumps(res))
+        return
     ch = [int(c) for c in args.channels.split(",")]
     t0 = time.perf_counter()
     B, P, it = make_pairs(tshape, inputs.random_gaussian_forces_torch(args.train, tshape, DX, args.seed, device))
@@ -191,8 +207,7 @@ def main():
     losses = train(net, B, P, tshape, args.epochs, args.lr, log=print)
     t_train = time.perf_counter() - t0
     del B, P
-    res = evaluate(net, eshape, inputs.random_gaussian_forces_torch(args.eval, eshape, DX,
-                                                                    args.seed + 1_000_000, device))
+    res = evaluate(net, eshape, held(), modes=modes)
     res.update({"loss": args.loss, "train_fields": args.train, "train_shape": tshape, "eval_shape": eshape,
                 "channels": ch, "epochs": args.epochs, "data_s": t_data, "train_s": t_train,
                 "train_cg_iters_mean": float(np.mean(it)), "final_loss": float(np.mean(losses[-50:])),

@@ -139,3 +139,33 @@ def test_warm_start_reaches_the_same_residual_and_saves_iterations(device):
     assert r < 1e-8 and r == pytest.approx(st["rel_res_true"], rel=1e-3)
     kv.kv_destroy(h)
     kv.kv_net_destroy(net)
+
+
+def test_flexible_cg_with_the_net_meets_the_same_residual(device):
+    """Mode 2 (flexible CG, the net as preconditioner) stops on the same true
+    residual as the zero-start CG, checked by the oracle on its potential, and
+    its projected force matches mode 0's node by node."""
+    shape = (40, 40, 40)
+    net = learned.load_net(learned.WEIGHTS, shape)
+    held = list(inputs.random_gaussian_forces_torch(3, shape, learned.DX, 10_009, device))
+    h = learned.projection_handle(shape)
+    kv.kv_attach_net(h, net)
+    try:
+        for f in held:
+            fs0 = torch.zeros((3,) + shape[::-1], dtype=torch.float32, device=device)
+            fs2 = torch.zeros_like(fs0)
+            st0 = kv.kv_project_force(h, *f, 1e-8, 0, 0, fs0)
+            st2 = kv.kv_project_force(h, *f, 1e-8, 0, 2, fs2)
+            phi = np.empty(shape[::-1], np.float64)
+            kv.kv_read_field(h, kv.FIELD_PHI, 0, phi)
+            b = -orc.div_minus(*[c.cpu().numpy() for c in f], learned.DX)
+            r = np.linalg.norm(b - orc.apply_A(phi, learned.DX)) / np.linalg.norm(b)
+            print(f"flexible CG 40^3: {st2['iters']} iterations (plain CG {st0['iters']}), "
+                  f"true residual {st2['rel_res_true']:.2e}, oracle {r:.2e}")
+            assert st2["status"] == kv.KV_OK and st2["rel_res_true"] < 1e-8
+            assert r < 1e-8 and r == pytest.approx(st2["rel_res_true"], rel=1e-3)
+            a, c = fs0.cpu().numpy(), fs2.cpu().numpy()
+            assert np.abs(a - c).max() <= 1e-6 * np.abs(a).max()
+    finally:
+        kv.kv_destroy(h)
+        kv.kv_net_destroy(net)

@@ -388,11 +388,12 @@ def test_cg_status_paths(device):
     st = kv.kv_project_force(s.h, *bad, 1e-8, 0, 0, None, check=False)
     assert st["rc"] == kv.KV_ERR_NONFINITE
     with pytest.raises(kv.KvError) as e:
-        kv.kv_project_force(s.h, *s.force, 1e-8, 0, 2)
+        kv.kv_project_force(s.h, *s.force, 1e-8, 0, 6)
     assert e.value.status == kv.KV_ERR_UNSUPPORTED
-    with pytest.raises(kv.KvError) as e:  # learned start without an attached net
-        kv.kv_project_force(s.h, *s.force, 1e-8, 0, 1)
-    assert e.value.status == kv.KV_ERR_STATE
+    for mode in (1, 2, 5):  # the learned start and preconditioner need an attached net
+        with pytest.raises(kv.KvError) as e:
+            kv.kv_project_force(s.h, *s.force, 1e-8, 0, mode)
+        assert e.value.status == kv.KV_ERR_STATE
     # the handle is still usable after these statuses
     st = s.project()
     assert st["status"] == kv.KV_OK and st["rel_res_true"] < 1e-8
