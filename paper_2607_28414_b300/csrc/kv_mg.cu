@@ -45,8 +45,16 @@ __device__ __forceinline__ bool mg_running(const CgParams &p) {
     return __ldcg(&p.ctrl[kCgStatus]) == kCgRunning;
 }
 
+// Cells k = k0 .. k1 of this block's contiguous z chunk (gridDim.z chunks).
+__device__ __forceinline__ void mg_chunk(int nz, int &k0, int &k1) {
+    const int zc = (nz + (int)gridDim.z - 1) / (int)gridDim.z;
+    k0 = 1 + (int)blockIdx.z * zc;
+    k1 = min(nz, k0 + zc - 1);
+}
+
 // t = r - A (S r) = (1 - omega) r + (omega / 6) (sum of the six neighbours of r)
-// on interior cells (r is 0 on the ghost layer).
+// on interior cells (r is 0 on the ghost layer). Each thread marches its z
+// chunk with the z-1, z and z+1 values of r in registers.
 __global__ void __launch_bounds__(kMgBX *kMgBY)
 k_mg_pre(MgLevel L, CgParams p) {
     if (!mg_running(p)) return;
@@ -54,11 +62,17 @@ k_mg_pre(MgLevel L, CgParams p) {
     const int j = 1 + blockIdx.y * kMgBY + (threadIdx.x / kMgBX);
     if (i > L.nx || j > L.ny) return;
     const long long sy = L.px, sz = (long long)L.px * (L.ny + 2);
-    for (int k = 1 + blockIdx.z; k <= L.nz; k += gridDim.z) {
-        const long long c = mg_idx(L, i, j, k);
-        const float s = ((L.r[c - 1] + L.r[c + 1]) + (L.r[c - sy] + L.r[c + sy])) +
-                        (L.r[c - sz] + L.r[c + sz]);
-        L.t[c] = (1.f - kMgOmega) * L.r[c] + (kMgOmega / 6.f) * s;
+    int k0, k1;
+    mg_chunk(L.nz, k0, k1);
+    if (k0 > k1) return;
+    long long c = mg_idx(L, i, j, k0);
+    float rm = L.r[c - sz], rc = L.r[c];
+    for (int k = k0; k <= k1; ++k, c += sz) {
+        const float rp = L.r[c + sz];
+        const float s = ((L.r[c - 1] + L.r[c + 1]) + (L.r[c - sy] + L.r[c + sy])) + (rm + rp);
+        L.t[c] = (1.f - kMgOmega) * rc + (kMgOmega / 6.f) * s;
+        rm = rc;
+        rc = rp;
     }
 }
 
@@ -73,7 +87,9 @@ k_mg_restrict(MgLevel F, MgLevel C, CgParams p) {
     const int I = 1 + blockIdx.x * kMgBX + (threadIdx.x % kMgBX);
     const int J = 1 + blockIdx.y * kMgBY + (threadIdx.x / kMgBX);
     if (I > C.nx || J > C.ny) return;
-    for (int K = 1 + blockIdx.z; K <= C.nz; K += gridDim.z) {
+    int K0, K1;
+    mg_chunk(C.nz, K0, K1);
+    for (int K = K0; K <= K1; ++K) {
         float acc = 0.f;
         for (int c = 0; c < 4; ++c) {
             const int k = 2 * K - 2 + c;
@@ -120,7 +136,9 @@ k_mg_prolong(MgLevel F, MgLevel C, CgParams p) {
     const int j = 1 + blockIdx.y * kMgBY + (threadIdx.x / kMgBX);
     if (i > F.nx || j > F.ny) return;
     const float sh = kMgOmega * (float)F.h2 / 6.f;
-    for (int k = 1 + blockIdx.z; k <= F.nz; k += gridDim.z) {
+    int k0, k1;
+    mg_chunk(F.nz, k0, k1);
+    for (int k = k0; k <= k1; ++k) {
         const long long c = mg_idx(F, i, j, k);
         F.t[c] = sh * F.r[c] + mg_prolong(C, i, j, k);
     }
@@ -137,12 +155,16 @@ k_mg_smooth(MgLevel F, float *__restrict__ out_z, CgParams p) {
     const long long sy = F.px, sz = (long long)F.px * (F.ny + 2);
     const float h2 = (float)F.h2;
     AccFF acc;
-    if (i <= F.nx && j <= F.ny) {
-        for (int k = 1 + blockIdx.z; k <= F.nz; k += gridDim.z) {
-            const long long c = mg_idx(F, i, j, k);
-            const float *t = F.t;
-            const float zc = t[c];
-            const float s = ((t[c - 1] + t[c + 1]) + (t[c - sy] + t[c + sy])) + (t[c - sz] + t[c + sz]);
+    int k0, k1;
+    mg_chunk(F.nz, k0, k1);
+    if (i <= F.nx && j <= F.ny && k0 <= k1) {
+        // z march with the z-1, z and z+1 values of z2 in registers
+        const float *t = F.t;
+        long long c = mg_idx(F, i, j, k0);
+        float tm = t[c - sz], zc = t[c];
+        for (int k = k0; k <= k1; ++k, c += sz) {
+            const float tp = t[c + sz];
+            const float s = ((t[c - 1] + t[c + 1]) + (t[c - sy] + t[c + sy])) + (tm + tp);
             const float rv = F.r[c];
             // S (r - A z2) = (omega / 6) (h^2 r - 6 z2 + sum of neighbours)
             const float z = zc + (kMgOmega / 6.f) * (h2 * rv - 6.f * zc + s);
@@ -152,6 +174,8 @@ k_mg_smooth(MgLevel F, float *__restrict__ out_z, CgParams p) {
             } else {
                 F.e[c] = z;
             }
+            tm = zc;
+            zc = tp;
         }
     }
     if (!out_z) return;
