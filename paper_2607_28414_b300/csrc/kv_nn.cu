@@ -33,12 +33,21 @@ namespace kv {
 // of K step by one channel chunk (LBO = 1080 x 16 bytes). So the 27 taps need no
 // gather: each is a descriptor with a different start address.
 //
-// The weights W[t][ci][co] arrive by TMA straight from their own layout: a 4D
-// view (8 co, ci, co chunk, tap) lands as [tap][co chunk][ci][8], the MN-major
-// core matrices of the B operand (8 ci rows x 8 co, 128 contiguous bytes; LBO =
-// 128 bytes along K, SBO = CIN x 16 bytes along N). All 27 taps stay resident
-// when they fit beside the bricks; otherwise the nine (dz, dy) groups of three
-// taps stream through a 3-slot ring, refilled while the tensor cores work.
+// The three z taps of one (dx, dy) share the A operand: the brick plane p seen
+// from (dx, dy) is the input of tap dz for output plane p - dz. So the weights
+// of a (dy, dx) group are stacked along N in the order dz = 2, 1, 0 and one MMA
+// of N = (number of valid dz) x COUT accumulates into the adjacent accumulator
+// columns of output planes p - dz_hi .. p - dz_lo: per tile six planes x nine
+// (dx, dy) groups of MMAs instead of 27 taps x four planes, with half the A
+// reads from shared memory. Each tap's weights W[t][ci][co] arrive by TMA
+// straight from their own layout: a 4D view (8 co, ci, co chunk, tap) lands as
+// [co chunk][ci][8], the MN-major core matrices of the B operand (8 ci rows x
+// 8 co, 128 contiguous bytes; LBO = 128 bytes along K, SBO = CIN x 16 bytes
+// along N, uniform across the stacked taps). All 27 taps stay resident when
+// they fit beside the bricks; otherwise the nine (dy, dx) groups of three taps
+// stream through a 3-slot ring, refilled while the tensor cores work. An MMA
+// covers a varying set of output planes, so the accumulators are zeroed by the
+// epilogue (tcgen05.st) and every MMA accumulates.
 //
 // Persistent, warp-specialised blocks walk the tiles (tile = first + i x grid):
 //   warp 4  (one thread) issues the TMA copies: bricks into a ring of NB
@@ -50,8 +59,8 @@ namespace kv {
 //           the weight slot and hand the accumulators to the epilogue;
 //   warps 0-3 read the accumulators with tcgen05.ld (warp w owns TMEM lanes
 //           32w .. 32w + 31 = tile rows m = y x 8 + x), add the bias, apply
-//           ReLU, store, and free the accumulator set, so the epilogue of
-//           tile i overlaps the MMAs of tile i + 1.
+//           ReLU, store, zero the accumulator set and free it, so the
+//           epilogue of tile i overlaps the MMAs of tile i + 1.
 // Every wait is bounded (~1 s of SM clocks); a wait that gives up sets a
 // shared abort flag and the device timeout flag, every role stops issuing,
 // the copies and MMAs in flight are awaited (bounded) and the tensor memory
@@ -68,7 +77,7 @@ struct ConvTc {
     static constexpr size_t kBrickBytes = (size_t)(CIN / 8) * kTcBrick * 16;
     static constexpr size_t kTapBytes = (size_t)CIN * COUT * 2;
     static constexpr size_t kAllW = 27 * kTapBytes;
-    static constexpr size_t kGroupBytes = 3 * kTapBytes;          // one (dz, dy) group of taps
+    static constexpr size_t kGroupBytes = 3 * kTapBytes;          // one (dy, dx) group: dz = 2, 1, 0
     static constexpr int NB = 2 * kBrickBytes + 3 * kGroupBytes <= kBudget ? 2 : 1;
     static constexpr bool kResident = NB * kBrickBytes + kAllW <= kBudget;
     static constexpr int NWS = kResident ? 1 : 3;                 // weight slots
@@ -132,6 +141,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// Zero 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ int g_conv_timeout;  // set when a bounded wait of a convolution gave up
 
@@ -225,6 +245,13 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    if (warp < 4) {  // both accumulator sets start at zero (every MMA accumulates)
+        for (uint32_t c = 0; c < 2 * C::kAccCols; c += 16) tmem_zero16(tmem + ((uint32_t)(32 * warp) << 16) + c);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     auto give_up = [&]() {
         *abort_flag = 1;
         atomicExch(&g_conv_timeout, 1);
@@ -234,9 +261,16 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
         // ---------------- TMA producer ----------------
         if (lane == 0 && my_tiles > 0) {
             int issued_b = 0, issued_w = 0;  // bricks and weight groups whose copies were issued
+            // the three taps of group g = (dy, dx) in the order dz = 2, 1, 0
+            auto load_group = [&](uint32_t dst, int g, uint32_t bar) {
+                const int dy = g / 3, dx = g % 3;
+                for (int dz = 2; dz >= 0; --dz)
+                    tma_load_4d(dst + (uint32_t)((2 - dz) * C::kTapBytes), &tm_w, 0, 0, 0, dz * 9 + dy * 3 + dx,
+                                bar);
+            };
             if (C::kResident) {
                 mbar_expect_tx(w_full(0), (uint32_t)C::kAllW);
-                tma_load_4d(wts0, &tm_w, 0, 0, 0, 0, w_full(0));
+                for (int g = 0; g < 9; ++g) load_group(wts0 + (uint32_t)(g * C::kGroupBytes), g, w_full(0));
             }
             for (int i = 0; i < my_tiles && !*abort_flag; ++i) {
                 const int b = i % NB, use = i / NB;
@@ -257,7 +291,7 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
                             break;
                         }
                         mbar_expect_tx(w_full(q), (uint32_t)C::kGroupBytes);
-                        tma_load_4d(wts0 + (uint32_t)(q * C::kGroupBytes), &tm_w, 0, 0, 0, 3 * g, w_full(q));
+                        load_group(wts0 + (uint32_t)(q * C::kGroupBytes), g, w_full(q));
                         ++issued_w;
                     }
                 }
@@ -280,7 +314,10 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
     } else if (warp == 5) {
         // ---------------- MMA issuer ----------------
         if (lane == 0 && my_tiles > 0) {
-            constexpr uint32_t idesc = umma_idesc_bf16(128, COUT) | (1u << 16);  // B MN-major
+            // N = 1, 2 or 3 stacked taps of COUT channels; B MN-major
+            constexpr uint32_t idesc_n[3] = {umma_idesc_bf16(128, COUT) | (1u << 16),
+                                             umma_idesc_bf16(128, 2 * COUT) | (1u << 16),
+                                             umma_idesc_bf16(128, 3 * COUT) | (1u << 16)};
             int used_w = 0, committed = 0;
             bool ok = !C::kResident || mbar_wait_bounded(w_full(0), 0);
             if (!ok) give_up();
@@ -295,7 +332,7 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
                 const uint32_t brick = sm0 + (uint32_t)(b * C::kBrickBytes);
                 const uint32_t acc = tmem + (uint32_t)a * C::kAccCols;
                 for (int g = 0; g < 9; ++g) {
-                    const int dz = g / 3, dy = g % 3;
+                    const int dy = g / 3, dx = g % 3;
                     uint32_t wg;
                     int q = 0;
                     if (C::kResident) {
@@ -310,17 +347,18 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
                         wg = wts0 + (uint32_t)(q * C::kGroupBytes);
                     }
 #pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
+                    for (int kk = 0; kk < CIN / 16; ++kk) {
 #pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t bd = umma_desc(wg + (uint32_t)(dx * C::kTapBytes + kk * 256), 128, CIN * 16);
-#pragma unroll
-                            for (int zt = 0; zt < kTcZ; ++zt) {
-                                const uint32_t vox = ((zt + dz) * kTcBY + dy) * kTcBX + dx;
-                                const uint64_t ad = umma_desc(brick + (uint32_t)((2 * kk * kTcBrick + vox) * 16),
-                                                              kTcBrick * 16, kTcBX * 16);
-                                umma_bf16(acc + (uint32_t)(zt * COUT), ad, bd, idesc, (g | dx | kk) != 0);
-                            }
+                        for (int pz = 0; pz < kTcBZ; ++pz) {
+                            // brick plane pz feeds output planes pz - dz for the dz with
+                            // 0 <= pz - dz < kTcZ; their weights sit at stack rows 2 - dz
+                            const int dz_hi = pz < 2 ? pz : 2, dz_lo = pz > kTcZ - 1 ? pz - (kTcZ - 1) : 0;
+                            const uint64_t bd =
+                                umma_desc(wg + (uint32_t)((2 - dz_hi) * C::kTapBytes + kk * 256), 128, CIN * 16);
+                            const uint32_t vox = (pz * kTcBY + dy) * kTcBX + dx;
+                            const uint64_t ad = umma_desc(brick + (uint32_t)((2 * kk * kTcBrick + vox) * 16),
+                                                          kTcBrick * 16, kTcBX * 16);
+                            umma_bf16(acc + (uint32_t)((pz - dz_hi) * COUT), ad, bd, idesc_n[dz_hi - dz_lo], 1u);
                         }
                     }
                     if (!C::kResident) {
@@ -370,6 +408,10 @@ k_conv_fwd(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CU
                     if (inside) store16<OutT>(out + (((size_t)gz * ny + gy) * nx + gx) * COUT + c0, v);
                 }
             }
+            // the next tile on this set accumulates from zero
+            for (uint32_t c = 0; c < C::kAccCols; c += 16)
+                tmem_zero16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)a * C::kAccCols + c);
+            tmem_wait_st();
             tc_fence_before();
             mbar_arrive(a_empty(a));
         }
@@ -623,7 +665,7 @@ static kv_status launch_fwd_t(int nx, int ny, int nz, const bf16 *in, const bf16
     {
         cuuint64_t dims[4] = {8, (cuuint64_t)CIN, (cuuint64_t)(COUT / 8), 27};
         cuuint64_t strides[3] = {(cuuint64_t)COUT * 2, 16, (cuuint64_t)CIN * COUT * 2};
-        cuuint32_t box[4] = {8, CIN, COUT / 8, C::kResident ? 27u : 3u};
+        cuuint32_t box[4] = {8, CIN, COUT / 8, 1};  // one tap per box
         cuuint32_t es[4] = {1, 1, 1, 1};
         if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(W), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
