@@ -383,10 +383,11 @@ kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, 
 /* Current step configuration: cfg[5] = {variant, tx, ty, zc, ns}. */
 kv_status kv_get_step_config(kv_handle *h, int *cfg);
 
-/* Autotuner of the FP32 step: times trial_steps launches of every supported
- * (tile, stage count, z chunk) on this handle's grid with CUDA events on its
- * stream, keeps the fastest, then resets the state (kv_reset). *best_ms: mean
- * milliseconds per step of the choice (NULL allowed). Synchronising. */
+/* Autotuner of the FP32 step: times trial_steps steps of every supported
+ * (variant, tile, stage count, z chunk) on this handle's grid with CUDA events
+ * on its stream, times the four fastest again over 4 x trial_steps steps and
+ * keeps the fastest of those, then resets the state (kv_reset). *best_ms:
+ * mean milliseconds per step of the choice (NULL allowed). Synchronising. */
 kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms);
 
 /* Launch shape of the FP32 CG passes (Sec. 3.2.3 iteration): zc planes per

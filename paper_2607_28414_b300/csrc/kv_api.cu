@@ -865,18 +865,38 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
     Cand pick = {saved[0], saved[1], saved[2], saved[4], saved[3]};
     kv_status st = KV_OK;
     const int trial = trial_steps + (trial_steps & 1);  // even: whole two-step launches
-    for (const Cand &c : cands) {
-        if (kv_set_step_config(h, c.variant, c.tx, c.ty, c.zc, c.ns) != KV_OK) continue;
-        if ((st = launch_steps_direct(h, 2)) != KV_OK) break;
+    // time one candidate over n steps (after two warm-up steps); < 0 if it cannot run
+    auto time_cand = [&](const Cand &c, int n, float *ms) -> kv_status {
+        *ms = -1.f;
+        if (kv_set_step_config(h, c.variant, c.tx, c.ty, c.zc, c.ns) != KV_OK) return KV_OK;
+        kv_status ts;
+        if ((ts = launch_steps_direct(h, 2)) != KV_OK) return ts;
         cudaEventRecord(e0, h->stream);
-        if ((st = launch_steps_direct(h, trial)) != KV_OK) break;
+        if ((ts = launch_steps_direct(h, n)) != KV_OK) return ts;
         cudaEventRecord(e1, h->stream);
-        if ((st = cuda_check(h, cudaEventSynchronize(e1), "kv_autotune_step")) != KV_OK) break;
+        if ((ts = cuda_check(h, cudaEventSynchronize(e1), "kv_autotune_step")) != KV_OK) return ts;
+        cudaEventElapsedTime(ms, e0, e1);
+        return KV_OK;
+    };
+    // round 1: every candidate over `trial` steps; round 2: the four fastest
+    // again over four times as many steps, so that near-ties are decided on a
+    // longer sample
+    std::vector<std::pair<float, Cand>> timed;
+    for (const Cand &c : cands) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms > 0.f && ms < best) {
-            best = ms;
-            pick = c;
+        if ((st = time_cand(c, trial, &ms)) != KV_OK) break;
+        if (ms > 0.f) timed.push_back({ms, c});
+    }
+    if (st == KV_OK) {
+        std::sort(timed.begin(), timed.end(),
+                  [](const std::pair<float, Cand> &a, const std::pair<float, Cand> &b) { return a.first < b.first; });
+        for (size_t q = 0; q < timed.size() && q < 4; ++q) {
+            float ms = 0.f;
+            if ((st = time_cand(timed[q].second, 4 * trial, &ms)) != KV_OK) break;
+            if (ms > 0.f && ms / 4.f < best) {
+                best = ms / 4.f;
+                pick = timed[q].second;
+            }
         }
     }
     cudaEventDestroy(e0);
