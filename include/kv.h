@@ -401,7 +401,8 @@ kv_status kv_get_cg_config(kv_handle *h, int *zc);
 
 /* Autotuner of the FP32 CG passes: runs the projection of (fx, fy, fz) for
  * iters iterations (twice) with each z chunk in {8, 16, 24, 32, 48, 64, 96,
- * 128} that fits the grid, keeps the fastest and reports its wall time in
+ * 128} that fits the grid and each shared-memory stage count of the passes
+ * (8 or 4 planes per block's ring), keeps the fastest and reports its wall time in
  * *best_ms (NULL allowed). The trial projections stop early, so the force
  * must be projected again (kv_project_force) before stepping. No-op for
  * FP64 handles. Synchronising. */

@@ -311,6 +311,7 @@ kv_status kv_create(kv_handle **out, int nx, int ny, int nz, double dx, double d
     h->op = KV_OP_POINTWISE;
     h->medium_encoding = KV_MEDIUM_AUTO;
     h->variant = 0;
+    h->cg_ns = 8;
     h->tx = 64;
     h->ty = 8;
     h->zc = 32;
@@ -611,27 +612,33 @@ kv_status kv_autotune_cg(kv_handle *h, kv_field fx, kv_field fy, kv_field fz, in
         return KV_OK;
     }
     const int cand[] = {8, 16, 24, 32, 48, 64, 96, 128};
-    const int saved = h->cg_zc;
-    int best = -1;
+    const int saved = h->cg_zc, saved_ns = h->cg_ns;
+    int best = -1, best_ns = saved_ns;
     double best_t = INFINITY;
-    for (int zc : cand) {
-        if (zc > std::max(h->nz - 2, 8) || kv_set_cg_config(h, zc) != KV_OK) continue;
-        double t = INFINITY;
-        for (int rep = 0; rep < 2; ++rep) {  // the first run also warms the caches
-            kv_cg_stats stc;
-            kv_status st = kv_project_force(h, fx, fy, fz, 1e-30, iters, 0, nullptr, &stc);
-            if (st != KV_OK && st != KV_CG_MAXITER) {
-                h->cg_zc = saved;
-                return st;
+    for (int ns : {8, 4}) {
+        h->cg_ns = ns;
+        for (int zc : cand) {
+            if (zc > std::max(h->nz - 2, 8) || kv_set_cg_config(h, zc) != KV_OK) continue;
+            double t = INFINITY;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run also warms the caches
+                kv_cg_stats stc;
+                kv_status st = kv_project_force(h, fx, fy, fz, 1e-30, iters, 0, nullptr, &stc);
+                if (st != KV_OK && st != KV_CG_MAXITER) {
+                    h->cg_zc = saved;
+                    h->cg_ns = saved_ns;
+                    return st;
+                }
+                t = std::min(t, stc.ms);
             }
-            t = std::min(t, stc.ms);
-        }
-        if (t < best_t) {
-            best_t = t;
-            best = zc;
+            if (t < best_t) {
+                best_t = t;
+                best = zc;
+                best_ns = ns;
+            }
         }
     }
     h->cg_zc = best > 0 ? best : saved;
+    h->cg_ns = best > 0 ? best_ns : saved_ns;
     h->have_force = 0;  // the trial projections stopped early: project again before stepping
     h->phi_valid = 0;
     if (best_ms) *best_ms = best_t;
@@ -878,9 +885,9 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
         cudaEventElapsedTime(ms, e0, e1);
         return KV_OK;
     };
-    // round 1: every candidate over `trial` steps; round 2: the four fastest
-    // again over four times as many steps, so that near-ties are decided on a
-    // longer sample
+    // first pass: every candidate over `trial` steps; second pass: the four
+    // fastest again over four times as many steps, so that near-ties are
+    // decided on a longer sample
     std::vector<std::pair<float, Cand>> timed;
     for (const Cand &c : cands) {
         float ms = 0.f;

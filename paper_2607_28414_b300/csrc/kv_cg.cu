@@ -246,14 +246,14 @@ k_cg_upd(const T *__restrict__ p0, const T *__restrict__ p1, T *__restrict__ r, 
 // The CG vectors of a handle are one allocation [pA, r, pB, e] (4 x Np floats),
 // seen by TMA as a 4D tensor (x, y, z, field). A block owns a kCgTX x kCgTY
 // column and marches z; every plane it needs arrives by TMA into a ring of
-// kCgNS shared-memory stages, so several planes are in flight per block while
+// NS shared-memory stages, so several planes are in flight per block while
 // one is computed. The z-1 neighbour is the previous plane's centre value,
 // kept in registers, so a stage is refilled as soon as its plane is done. Each thread computes four consecutive x nodes (a float4);
 // x neighbours come from warp shuffles, y and z neighbours from the staged
 // tiles. Per-node arithmetic is the same sequence as the plain kernels above.
 // Reductions: float-float per thread and across the block, double per block.
 // ---------------------------------------------------------------------------
-constexpr int kCgTX = 64, kCgTY = 8, kCgNS = 8;
+constexpr int kCgTX = 64, kCgTY = 8;
 constexpr int kCgNT = kCgTX * kCgTY / 4;
 constexpr int kCgGX = kCgTX / 4;
 constexpr int kCgBXh = kCgTX + 8, kCgBYh = kCgTY + 2;
@@ -263,8 +263,9 @@ constexpr int kCgStageDir = 2 * kCgHalo;                  // (p_old, r) or (r, p
 constexpr int kCgHaloPad = (kCgHalo + 31) / 32 * 32;
 constexpr int kCgStageUpd = kCgHaloPad + 2 * kCgCtr;      // p' halo, r and e centre
 static_assert((kCgStageDir * 4) % 128 == 0 && (kCgStageUpd * 4) % 128 == 0, "stage alignment");
-constexpr size_t kCgSmemDir = kCgNS * kCgStageDir * 4 + kCgNS * 8;
-constexpr size_t kCgSmemUpd = kCgNS * kCgStageUpd * 4 + kCgNS * 8;
+// NS shared-memory stages per block (4 or 8): the CG autotuner picks, with the z chunk
+constexpr size_t cg_smem_dir(int ns) { return (size_t)ns * kCgStageDir * 4 + ns * 8; }
+constexpr size_t cg_smem_upd(int ns) { return (size_t)ns * kCgStageUpd * 4 + ns * 8; }
 
 // Per-block partial (thread 0's value) -> last block sums all partials.
 __device__ __forceinline__ bool finish_blocks(const CgParams &p, double tot, double &sum) {
@@ -314,6 +315,7 @@ __device__ __forceinline__ void upd_finish(const CgParams &p, double rr) {
     }
 }
 
+template <int NS>
 struct CgTile {
     int x0, y0, k0, k1, kb, gx, gy;
     __device__ CgTile(const CgParams &p) {
@@ -325,25 +327,27 @@ struct CgTile {
         gx = threadIdx.x % kCgGX;
         gy = threadIdx.x / kCgGX;
     }
-    __device__ int slot(int q) const { return (q - kb) % kCgNS; }
-    __device__ uint32_t parity(int q) const { return ((q - kb) / kCgNS) & 1; }
+    __device__ int slot(int q) const { return (q - kb) % NS; }
+    __device__ uint32_t parity(int q) const { return ((q - kb) / NS) & 1; }
 };
 
 __device__ __forceinline__ float4 ld4(const float *a) { return *reinterpret_cast<const float4 *>(a); }
 
 // Drain every stage (bounded) after a wait gave up, then flag the timeout.
-__device__ __forceinline__ void ring_drain(const CgParams &p, const CgTile &t, uint32_t bar0,
+template <int NS>
+__device__ __forceinline__ void ring_drain(const CgParams &p, const CgTile<NS> &t, uint32_t bar0,
                                            bool ok) {
     if (__syncthreads_or(!ok) && threadIdx.x == 0) {
         atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
         const int rel_max = t.k1 - t.kb;
-        for (int s = 0; s < kCgNS && s <= rel_max; ++s) {
-            const int rel_last = s + ((rel_max - s) / kCgNS) * kCgNS;
-            mbar_wait_bounded(bar0 + 8 * s, (rel_last / kCgNS) & 1);
+        for (int s = 0; s < NS && s <= rel_max; ++s) {
+            const int rel_last = s + ((rel_max - s) / NS) * NS;
+            mbar_wait_bounded(bar0 + 8 * s, (rel_last / NS) & 1);
         }
     }
 }
 
+template <int NS>
 __global__ void __launch_bounds__(kCgNT)
 k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv, CgParams p) {
     if (__ldcg(&p.ctrl[kCgStatus]) != kCgRunning) return;
@@ -353,10 +357,10 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
     const float beta = (float)__ldcg(&p.scal[kBeta]);
     const float inv = (float)p.inv_dx2;
     extern __shared__ __align__(128) float smem[];
-    const uint32_t bar0 = smem_u32(smem + kCgNS * kCgStageDir);
-    const CgTile t(p);
+    const uint32_t bar0 = smem_u32(smem + NS * kCgStageDir);
+    const CgTile<NS> t(p);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kCgNS; ++s) mbar_init(bar0 + 8 * s, 1);
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -366,7 +370,7 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
         tma_load_4d(smem_u32(smem + t.slot(q) * kCgStageDir), &tm_h2, t.x0 - 4, t.y0 - 1, q, par, bar);
     };
     if (threadIdx.x == 0)
-        for (int q = t.kb; q <= min(t.k1, t.kb + kCgNS - 1); ++q) issue(q);
+        for (int q = t.kb; q <= min(t.k1, t.kb + NS - 1); ++q) issue(q);
 
     AccFF acc;
     bool ok = true;
@@ -386,9 +390,9 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
     ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.kb), t.parity(t.kb));
     float4 prev = pn4(smem + t.slot(t.kb) * kCgStageDir, o);
     __syncthreads();
-    if (threadIdx.x == 0 && t.kb + kCgNS <= t.k1) {
+    if (threadIdx.x == 0 && t.kb + NS <= t.k1) {
         fence_proxy_async();
-        issue(t.kb + kCgNS);
+        issue(t.kb + NS);
     }
     ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.k0), t.parity(t.k0));
     for (int k = t.k0; k < t.k1; ++k) {
@@ -422,7 +426,7 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int q = k + kCgNS;
+            const int q = k + NS;
             if (q <= t.k1) {
                 fence_proxy_async();
                 issue(q);
@@ -435,6 +439,7 @@ k_cg_dir_tma(const __grid_constant__ CUtensorMap tm_h2, float *__restrict__ cgv,
     if (finish_blocks(p, tot, sum) && threadIdx.x == 0) dir_finish(p, sum);
 }
 
+template <int NS>
 __global__ void __launch_bounds__(kCgNT)
 k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ CUtensorMap tm_c1,
              const __grid_constant__ CUtensorMap tm_r, float *__restrict__ cgv, CgParams p) {
@@ -446,10 +451,10 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
     float *__restrict__ rg = p.rbuf;
     float *__restrict__ eg = cgv + 3 * p.Np;
     extern __shared__ __align__(128) float smem[];
-    const uint32_t bar0 = smem_u32(smem + kCgNS * kCgStageUpd);
-    const CgTile t(p);
+    const uint32_t bar0 = smem_u32(smem + NS * kCgStageUpd);
+    const CgTile<NS> t(p);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kCgNS; ++s) mbar_init(bar0 + 8 * s, 1);
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -465,7 +470,7 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
         }
     };
     if (threadIdx.x == 0)
-        for (int q = t.kb; q <= min(t.k1, t.kb + kCgNS - 1); ++q) issue(q);
+        for (int q = t.kb; q <= min(t.k1, t.kb + NS - 1); ++q) issue(q);
 
     AccFF acc;
     bool ok = true;
@@ -480,9 +485,9 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
     ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.kb), t.parity(t.kb));
     float4 prev = ld4(smem + t.slot(t.kb) * kCgStageUpd + o);
     __syncthreads();
-    if (threadIdx.x == 0 && t.kb + kCgNS <= t.k1) {
+    if (threadIdx.x == 0 && t.kb + NS <= t.k1) {
         fence_proxy_async();
-        issue(t.kb + kCgNS);
+        issue(t.kb + NS);
     }
     ok &= mbar_wait_bounded(bar0 + 8 * t.slot(t.k0), t.parity(t.k0));
     for (int k = t.k0; k < t.k1; ++k) {
@@ -521,7 +526,7 @@ k_cg_upd_tma(const __grid_constant__ CUtensorMap tm_h1, const __grid_constant__ 
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int q = k + kCgNS;
+            const int q = k + NS;
             if (q <= t.k1) {
                 fence_proxy_async();
                 issue(q);
@@ -761,11 +766,17 @@ static kv_status cg_tma_prepare(kv_handle *h) {
     if ((st = encode_tensor_4d(h, &h->tm_cg_h2, h->cgv, 4, kCgBXh, kCgBYh, 2)) != KV_OK) return st;
     if ((st = encode_tensor_4d(h, &h->tm_cg_h1, h->cgv, 4, kCgBXh, kCgBYh, 1)) != KV_OK) return st;
     if ((st = encode_tensor_4d(h, &h->tm_cg_c1, h->cgv, 4, kCgTX, kCgTY, 1)) != KV_OK) return st;
-    cudaError_t e = cudaFuncSetAttribute(k_cg_dir_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kCgSmemDir);
+    cudaError_t e = cudaFuncSetAttribute(k_cg_dir_tma<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)cg_smem_dir(8));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_cg_upd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kCgSmemUpd);
+        e = cudaFuncSetAttribute(k_cg_upd_tma<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cg_smem_upd(8));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cg_dir_tma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cg_smem_dir(4));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cg_upd_tma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)cg_smem_upd(4));
     if (e != cudaSuccess) return cuda_check(h, e, "cudaFuncSetAttribute(CG)");
     h->cg_tma_ready = 1;
     return KV_OK;
@@ -883,10 +894,15 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
                 for (int it = 0; it < chunk; ++it) {
                     if (use_tma) {
                         if (pcg) mg_apply(h, pt);
-                        k_cg_dir_tma<<<tgrid, kCgNT, kCgSmemDir, s>>>(h->tm_cg_h2, (float *)h->cgv, pt);
-                        k_cg_upd_tma<<<tgrid, kCgNT, kCgSmemUpd, s>>>(h->tm_cg_h1, h->tm_cg_c1,
-                                                                      pcg ? h->tm_mg_r : h->tm_cg_c1,
-                                                                      (float *)h->cgv, pt);
+                        if (h->cg_ns == 4) {
+                            k_cg_dir_tma<4><<<tgrid, kCgNT, cg_smem_dir(4), s>>>(h->tm_cg_h2, (float *)h->cgv, pt);
+                            k_cg_upd_tma<4><<<tgrid, kCgNT, cg_smem_upd(4), s>>>(
+                                h->tm_cg_h1, h->tm_cg_c1, pcg ? h->tm_mg_r : h->tm_cg_c1, (float *)h->cgv, pt);
+                        } else {
+                            k_cg_dir_tma<8><<<tgrid, kCgNT, cg_smem_dir(8), s>>>(h->tm_cg_h2, (float *)h->cgv, pt);
+                            k_cg_upd_tma<8><<<tgrid, kCgNT, cg_smem_upd(8), s>>>(
+                                h->tm_cg_h1, h->tm_cg_c1, pcg ? h->tm_mg_r : h->tm_cg_c1, (float *)h->cgv, pt);
+                        }
                     } else {
                         k_cg_dir<T><<<grid, nt, 0, s>>>((const T *)h->r, p0, p1, p);
                         k_cg_upd<T><<<grid, nt, 0, s>>>(p0, p1, (T *)h->r, (T *)h->e, p);

@@ -167,6 +167,7 @@ struct kv_handle {
     CUtensorMap tm_cg_h2, tm_cg_h1, tm_cg_c1;  // TMA views of cgv (FP32)
     int cg_tma_ready;
     int cg_zc;             // planes per block of the TMA CG passes (0: default)
+    int cg_ns;             // shared-memory stages of the TMA CG passes (4 or 8)
 
     // multigrid preconditioner (projection mode 4), allocated on first use
     int mg_levels;
