@@ -385,8 +385,10 @@ kv_status kv_get_step_config(kv_handle *h, int *cfg);
 
 /* Autotuner of the FP32 step: times trial_steps steps of every supported
  * (variant, tile, stage count, z chunk) on this handle's grid with CUDA events
- * on its stream, times the four fastest again over 4 x trial_steps steps and
- * keeps the fastest of those, then resets the state (kv_reset). *best_ms:
+ * on its stream, times the four fastest (and the fastest one-step candidate)
+ * again over 4 x trial_steps steps and keeps the fastest of those, a two-step
+ * variant only if it is more than 3 % faster than the best one-step kernel,
+ * then resets the state (kv_reset). *best_ms:
  * mean milliseconds per step of the choice (NULL allowed). Synchronising. */
 kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms);
 
