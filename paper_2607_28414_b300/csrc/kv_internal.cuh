@@ -114,7 +114,10 @@ struct MgLevel {
     int nx, ny, nz, px;
     long long n;         // elements of one array (px * (ny + 2) * (nz + 2))
     double h2;           // grid spacing squared
-    float *r, *e, *t;    // right-hand side, solution, residual after pre-smoothing
+    float h2f, sh;       // h^2 and the smoother S = omega h^2 / 6 in FP32
+    float *r, *e;        // right-hand side, solution (level 0: r only, z goes to the CG)
+    int dn_zc, up_zc;    // planes per block: restriction to the next level (coarse
+                         // planes), prolongation and post-smoothing (this level's)
 };
 
 }  // namespace kv
@@ -175,6 +178,8 @@ struct kv_handle {
     float *mg_pool;        // all level arrays in one allocation
     double *fcg_pool;      // flexible CG (mode 2) vectors, allocated on first use
     CUtensorMap tm_mg_r;   // TMA view of the fine residual (mg[0].r)
+    CUtensorMap tm_mg[kv::kMgMaxLevels][3];  // per level: r (restriction box), r (prolongation box),
+                                             // next level's e (prolongation box)
     double *phi;           // [Np]
     double *b;             // [Np] right-hand side
     double *scal;          // kv::kCgScalars

@@ -24,6 +24,15 @@ struct AccFF {
         hi = __fadd_rn(s, t);
         lo = __fsub_rn(t, __fsub_rn(hi, s));
     }
+    // acc += v with the sum formed exactly (TwoSum), then renormalised.
+    __device__ __forceinline__ void add(float v) {
+        const float s = __fadd_rn(hi, v);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+        const float t = __fadd_rn(e, lo);
+        hi = __fadd_rn(s, t);
+        lo = __fsub_rn(t, __fsub_rn(hi, s));
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 struct AccD {
