@@ -135,7 +135,7 @@ kv_status kv_set_medium(kv_handle *h, kv_field G, kv_field rho, kv_field eta);
  * handle's dt must not exceed kv_stable_dt_op for that operator (else
  * KV_ERR_UNSTABLE_DT and nothing changes). The divergence form stores three
  * coefficient fields (dt^2 G/dx^2, dt eta/dx^2, 1/rho) instead of two; the
- * two-step kernels (kv_set_step_config variants 2 and 3) support only the pointwise
+ * two-step kernels (kv_set_step_config variants 2 to 4) support only the pointwise
  * operator (KV_ERR_UNSUPPORTED). The state and traces are kept. A kv_create
  * handle starts with KV_OP_POINTWISE. Synchronising. */
 kv_status kv_set_operator(kv_handle *h, int op, kv_field G, kv_field rho, kv_field eta);
@@ -370,12 +370,14 @@ kv_status kv_sync(kv_handle *h);
  * 3: two steps per z sweep with one displacement component per block (the
  * pointwise operator couples the components only through the shared
  * coefficients; pointwise operator only; tiles 32x8, 32x16, 64x4, 64x8,
- * 64x16, 128x4, 128x8 with ns in {4, 6}). Variants 2 and 3 read the
- * coefficient fields, never class bytes, and give bit for bit the result of
- * two single steps.
- * tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in [64, 512];
- * zc >= 1 planes per block; ns in {4, 6, 8} shared-memory stages (ns - 3
- * planes in flight per block). Values <= 0 keep the current choice. A shape
+ * 64x16, 128x4, 128x8 with ns in {4, 6});
+ * 4: as 3 with a tx x 14 tile whose intermediate step takes one group of four
+ * nodes per thread plus one warp for the two halo columns (tx in {32, 64, 128},
+ * ty = 14, ns in {3, 4, 6}). Variants 2 to 4 read the coefficient fields,
+ * never class bytes, and give bit for bit the result of two single steps.
+ * Variants 0 and 1: tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in
+ * [64, 512]; zc >= 1 planes per block; ns in {4, 6, 8} shared-memory stages
+ * (ns - 3 planes in flight per block). Values <= 0 keep the current choice. A shape
  * whose stages exceed the shared memory of a block is refused (KV_ERR_ARG)
  * and the previous configuration is kept. */
 kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, int ns);

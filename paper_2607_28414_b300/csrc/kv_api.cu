@@ -801,11 +801,14 @@ kv_status kv_read_field(kv_handle *h, int which, int comp, void *out, int where)
 
 kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, int ns) {
     if (!h) return KV_ERR_ARG;
-    if (variant > 3 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
-        (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 16) || (ns > 0 && ns != 4 && ns != 6 && ns != 8))
+    if (variant > 4 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
+        (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 14 && ty != 16) ||
+        (ns > 0 && ns != 3 && ns != 4 && ns != 6 && ns != 8))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant, tile or stage count");
     const int ntx = tx > 0 ? tx : h->tx, nty = ty > 0 ? ty : h->ty;
     const int nvar = variant >= 0 ? variant : h->variant;
+    if ((nvar == 4) != (nty == 14))
+        return set_error(h, KV_ERR_ARG, "kv_set_step_config: variant 4 takes tiles of 14 rows, the others not");
     if (nvar < 2 && (ntx * nty / 4 < 64 || ntx * nty / 4 > 512))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: tile %dx%d out of range", ntx, nty);
     cudaStreamSynchronize(h->stream);
@@ -864,6 +867,9 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
     for (auto &t : tiles3)
         for (int ns : {4, 6})
             for (int zc : zcs) cands.push_back({3, t[0], t[1], ns, zc});
+    for (int tx : {32, 64, 128})
+        for (int ns : {3, 4, 6})
+            for (int zc : zcs) cands.push_back({4, tx, 14, ns, zc});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(h, KV_ERR_CUDA, "kv_autotune_step: cudaEventCreate failed");

@@ -62,6 +62,7 @@ struct StepParams {
     int nx, ny, nz, px;
     long long Np;        // px * ny * nz (elements per component)
     double A, B;         // homogeneous coefficients (dt^2 G/(rho dx^2), dt eta/(rho dx^2))
+    float Af, Bf;        // the same in FP32
     const float *g;      // envelope table on the device
     int n_g;
     int g_const_on;      // 1: use g_const for every step instead of the table

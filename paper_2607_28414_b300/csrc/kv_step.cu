@@ -1162,6 +1162,322 @@ k_step2c_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
+// Two steps per sweep, one component per block, balanced (variant 4).
+//
+// Variant 3 computes the intermediate step on (TX + 8) x (TY + 2) nodes in
+// groups of four, (TX / 4 + 2) (TY + 2) groups for TX TY / 4 threads, so some
+// warps take two groups and the rest wait at the barrier. Here the tile is
+// TX x 14: the intermediate plane's 16 rows of TX / 4 groups take one group
+// per thread (16 TX / 4 threads) and one more warp computes the two halo
+// columns x0 - 1 and x0 + TX of the 16 rows (one node per lane), the only
+// halo nodes the second step reads. The intermediate planes rotate through
+// three buffers, so one barrier per plane suffices: the buffer written at
+// plane k + 1 was last read by the second step of plane k - 1, before the
+// barrier of plane k. The neighbour sums and the update run on pairs of nodes
+// (packed FP32; each lane rounds as the scalar operation does) in the order
+// of kv_update, so the result is bit for bit that of two single steps.
+// ---------------------------------------------------------------------------
+template <int TX, bool HET>
+struct Tile2B {
+    static constexpr int TY = 14;                              // output rows
+    static constexpr int GX = TX / 4;                          // groups of four nodes per row
+    static constexpr int BX = TX + 8;                          // staged row: x from x0 - 4
+    static constexpr int BYI = TY + 4;                         // input rows: y from y0 - 2
+    static constexpr int BYM = TY + 2;                         // intermediate rows: y from y0 - 1
+    static constexpr int IN_F = (BX * BYI + 31) / 32 * 32;     // field tile, padded: every TMA
+                                                               // destination on a 128-byte boundary
+    static constexpr int MID_F = BX * BYM;                     // (BYM = 16: a 128-byte multiple)
+    static constexpr int IN_STATE = 2 * IN_F;                  // u_c, d_c
+    static constexpr int IN_COEF = HET ? 2 * MID_F : 0;        // A', B'
+    static constexpr int IN_STAGE = (IN_STATE + IN_COEF + 31) / 32 * 32;
+    static constexpr int TX_BYTES = (2 * BX * BYI + IN_COEF) * 4;  // bytes the copies of a stage deliver
+    static constexpr int MID_STAGE = (2 * MID_F + 31) / 32 * 32;
+    static constexpr int NMID = GX * BYM;                      // intermediate groups: one per thread
+    static constexpr int NOUT = GX * TY;                       // output groups
+    static constexpr int NT = NMID + 32;                       // + the halo-column warp
+    static constexpr size_t smem(int ns) { return (size_t)(ns * IN_STAGE + 3 * MID_STAGE) * 4 + ns * 8; }
+    static_assert(2 * BYM == 32, "one lane per halo node of the 16 intermediate rows");
+    static_assert((MID_F * 4) % 128 == 0 && (IN_F * 4) % 128 == 0, "TMA destinations on 128-byte boundaries");
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2lo(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 f2hi(const float4 &v) { return make_float2(v.z, v.w); }
+
+// Neighbour sums ((xm + xp) + (ym + yp)) + (zm + zp) of four consecutive
+// nodes (left / right: the x neighbours beyond the group), as two pairs.
+__device__ __forceinline__ void nbsum4(const float4 &c, float left, float right, const float4 &ym,
+                                       const float4 &yp, const float4 &zm, const float4 &zp, float2 &s01,
+                                       float2 &s23) {
+    const float2 mid = f2(c.y, c.z);
+    s01 = __fadd2_rn(__fadd2_rn(__fadd2_rn(f2(left, c.x), mid), __fadd2_rn(f2lo(ym), f2lo(yp))),
+                     __fadd2_rn(f2lo(zm), f2lo(zp)));
+    s23 = __fadd2_rn(__fadd2_rn(__fadd2_rn(mid, f2(c.w, right)), __fadd2_rn(f2hi(ym), f2hi(yp))),
+                     __fadd2_rn(f2hi(zm), f2hi(zp)));
+}
+
+// kv_update on a pair of nodes.
+__device__ __forceinline__ void kv_update2(float2 u, float2 su, float2 d, float2 sd, float2 A, float2 B, float2 g,
+                                           float2 F, float2 &u_out, float2 &d_out) {
+    const float2 m6 = f2(-6.f, -6.f);
+    const float2 lu = __ffma2_rn(m6, u, su);
+    const float2 ld = __ffma2_rn(m6, d, sd);
+    float2 dn = __ffma2_rn(g, F, d);
+    dn = __ffma2_rn(B, ld, dn);
+    dn = __ffma2_rn(A, lu, dn);
+    d_out = dn;
+    u_out = __fadd2_rn(u, dn);
+}
+
+template <int TX, int NS, bool HET>
+__global__ void __launch_bounds__(Tile2B<TX, HET>::NT)
+k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
+             const float *__restrict__ F, float *__restrict__ out, StepParams p) {
+    using T2 = Tile2B<TX, HET>;
+    constexpr int TY = T2::TY, GX = T2::GX, BX = T2::BX;
+    extern __shared__ __align__(128) float smem[];
+    float *inr = smem;                                 // NS input stages
+    float *mid = smem + NS * T2::IN_STAGE;             // 3 intermediate planes
+    const uint32_t bar0 = smem_u32(mid + 3 * T2::MID_STAGE);
+    const int tid = threadIdx.x;
+    const int comp = (int)(blockIdx.x % 3);
+    const int x0 = (int)(blockIdx.x / 3) * TX, y0 = 1 + blockIdx.y * TY;
+    const int k0 = 1 + blockIdx.z * p.zc;
+    const int k1 = min(k0 + p.zc, p.nz - 1);  // output planes k0..k1-1
+    const int qb = k0 - 2;                     // first staged input plane (may be -1)
+    const long long step = __ldcg(&p.ctrl[kStep]);
+    const float g0 = p.g_const_on ? p.g_const : (step < p.n_g) ? p.g[step] : 0.f;
+    const float g1 = p.g_const_on ? p.g_const : (step + 1 < p.n_g) ? p.g[step + 1] : 0.f;
+    const long long sy = p.px, sz = (long long)p.px * p.ny;
+    const float *Fc = F + comp * p.Np;
+    float *out_u = out + comp * p.Np, *out_d = out + (3 + comp) * p.Np;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(bar0 + 8 * s, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto slot = [&](int q) { return (int)((unsigned)(q - qb) % NS); };
+    auto par = [&](int q) { return ((unsigned)(q - qb) / NS) & 1u; };
+    auto midp = [&](int j) { return mid + ((unsigned)(j - (k0 - 1)) % 3u) * T2::MID_STAGE; };
+    auto issue = [&](int q) {
+        const uint32_t bar = bar0 + 8 * slot(q);
+        float *st = inr + slot(q) * T2::IN_STAGE;
+        mbar_expect_tx(bar, T2::TX_BYTES);
+        tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 2, q, comp, bar);
+        tma_load_4d(smem_u32(st + T2::IN_F), &tm_in, x0 - 4, y0 - 2, q, 3 + comp, bar);
+        if (HET) tma_load_4d(smem_u32(st + T2::IN_STATE), &tm_coef, x0 - 4, y0 - 1, q, 0, bar);
+    };
+    int next_issue = qb;
+    auto refill = [&](int upto) {  // thread 0, after a barrier: stage planes up to `upto`
+        if (tid == 0) {
+            fence_proxy_async();
+            for (; next_issue <= min(k1 + 1, upto); ++next_issue) issue(next_issue);
+        }
+    };
+    if (tid == 0)
+        for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue(next_issue);
+    bool ok = true;
+
+    // intermediate node(s) of this thread: a group of four (x .. x+3) in row
+    // mr, or (halo warp) the node x0 - 1 or x0 + TX of row mr
+    const bool grp = tid < T2::NMID;
+    const int mr = grp ? tid / GX : (tid - T2::NMID) >> 1;
+    const int mc = tid % GX;
+    const int mcol = grp ? 4 + 4 * mc : ((tid & 1) ? 4 + TX : 3);  // staged column
+    const int ym_ = y0 - 1 + mr, xm_ = x0 - 4 + mcol;
+    const int oi = (mr + 1) * BX + mcol;  // in an input field tile
+    const int om = mr * BX + mcol;        // in an intermediate plane (and the coefficient tile)
+    const bool mrow = ym_ >= 1 && ym_ <= p.ny - 2;
+    const bool mm0 = mrow && xm_ >= 1 && xm_ <= p.nx - 2, mm1 = mrow && xm_ + 1 <= p.nx - 2,
+               mm2 = mrow && xm_ + 2 <= p.nx - 2, mm3 = mrow && xm_ + 3 <= p.nx - 2;
+    const bool mload = mrow && xm_ >= 0 && xm_ < p.px;  // force row inside the pitched array
+    const float *Fm = Fc + (long long)ym_ * sy + xm_;
+    // output group of this thread (tid < NOUT): row orr, x .. x+3
+    const bool outer = tid < T2::NOUT;
+    const int orr = outer ? tid / GX : 0, oc = tid % GX;
+    const int oo = (orr + 1) * BX + 4 + 4 * oc;  // in an intermediate plane
+    const int y_out = y0 + orr, x_out = x0 + 4 * oc;
+    const bool row_ok = outer && (y_out <= p.ny - 2) && (x_out < p.px);
+    const bool m0 = (x_out >= 1) && (x_out <= p.nx - 2), m1 = (x_out + 1 <= p.nx - 2);
+    const bool m2 = (x_out + 2 <= p.nx - 2), m3 = (x_out + 3 <= p.nx - 2);
+    const float2 Ah = f2(p.Af, p.Af), Bh = f2(p.Bf, p.Bf);
+
+    float4 prev_in[2], prev_mid[2], coef_cur[2], coef_next[2];
+    auto stage = [&](int q) { return inr + slot(q) * T2::IN_STAGE; };
+    auto load_prev_in = [&](const float *sc) {
+        if (grp) {
+            prev_in[0] = *reinterpret_cast<const float4 *>(sc + oi);
+            prev_in[1] = *reinterpret_cast<const float4 *>(sc + T2::IN_F + oi);
+        } else {
+            prev_in[0].x = sc[oi];
+            prev_in[1].x = sc[T2::IN_F + oi];
+        }
+    };
+    auto load_out_coef = [&](const float *sc, float4 (&dst)[2]) {
+        if (HET && outer) {
+            const float *cs = sc + T2::IN_STATE;
+            dst[0] = *reinterpret_cast<const float4 *>(cs + oo);
+            dst[1] = *reinterpret_cast<const float4 *>(cs + T2::MID_F + oo);
+        }
+    };
+
+    // intermediate plane j into mj: input plane j staged at sc (centre), j+1
+    // at sp (z+), j-1 in prev_in; the x neighbours are read from the staged
+    // rows, which hold them for every group
+    auto compute_mid = [&](const float *sc, const float *sp, float *mj, int j) {
+        const bool pin = j >= 1 && j <= p.nz - 2;
+        if (grp) {
+            float4 c[2];
+            float2 s01[2], s23[2];
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const float *fc = sc + f * T2::IN_F + oi;
+                c[f] = *reinterpret_cast<const float4 *>(fc);
+                const float4 ym = *reinterpret_cast<const float4 *>(fc - BX);
+                const float4 yp = *reinterpret_cast<const float4 *>(fc + BX);
+                const float4 zp = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
+                nbsum4(c[f], fc[-1], fc[4], ym, yp, prev_in[f], zp, s01[f], s23[f]);
+                prev_in[f] = c[f];
+            }
+            float2 A01 = Ah, A23 = Ah, B01 = Bh, B23 = Bh;
+            if (HET) {
+                const float4 A4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + om);
+                const float4 B4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + T2::MID_F + om);
+                A01 = f2lo(A4);
+                A23 = f2hi(A4);
+                B01 = f2lo(B4);
+                B23 = f2hi(B4);
+            }
+            float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g0 != 0.f && pin && mload) F4 = __ldg(reinterpret_cast<const float4 *>(Fm + (long long)j * sz));
+            const float2 g = f2(g0, g0);
+            float2 u01, d01, u23, d23;
+            kv_update2(f2lo(c[0]), s01[0], f2lo(c[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
+            kv_update2(f2hi(c[0]), s23[0], f2hi(c[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
+            const bool q0 = pin && mm0, q1 = pin && mm1, q2 = pin && mm2, q3 = pin && mm3;
+            *reinterpret_cast<float4 *>(mj + om) =
+                make_float4(q0 ? u01.x : 0.f, q1 ? u01.y : 0.f, q2 ? u23.x : 0.f, q3 ? u23.y : 0.f);
+            *reinterpret_cast<float4 *>(mj + T2::MID_F + om) =
+                make_float4(q0 ? d01.x : 0.f, q1 ? d01.y : 0.f, q2 ? d23.x : 0.f, q3 ? d23.y : 0.f);
+        } else {
+            float cv[2], sv[2];
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const float *fc = sc + f * T2::IN_F + oi;
+                cv[f] = fc[0];
+                sv[f] = kv_add(kv_add(kv_add(fc[-1], fc[1]), kv_add(fc[-BX], fc[BX])),
+                               kv_add(prev_in[f].x, sp[f * T2::IN_F + oi]));
+                prev_in[f].x = cv[f];
+            }
+            const float A = HET ? sc[T2::IN_STATE + om] : p.Af;
+            const float B = HET ? sc[T2::IN_STATE + T2::MID_F + om] : p.Bf;
+            const bool q0 = pin && mm0;
+            const float Fv = (g0 != 0.f && q0) ? Fm[(long long)j * sz] : 0.f;
+            float uo, dn;
+            kv_update(cv[0], sv[0], cv[1], sv[1], A, B, g0, Fv, uo, dn);
+            mj[om] = q0 ? uo : 0.f;
+            mj[T2::MID_F + om] = q0 ? dn : 0.f;
+        }
+    };
+
+    // the three intermediate buffers: planes k-2 (free), k-1, k at the top of iteration k
+    float *mfree = mid + 2 * T2::MID_STAGE, *mprev = mid, *mcur = mid + T2::MID_STAGE;
+
+    // Prologue: input plane k0-2 into registers, intermediate planes k0-1, k0.
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(qb), par(qb));
+    load_prev_in(stage(qb));
+    __syncthreads();
+    refill(qb + NS);
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 - 1), par(k0 - 1));
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0), par(k0));
+    compute_mid(stage(k0 - 1), stage(k0), mprev, k0 - 1);
+    __syncthreads();
+    refill(k0 - 1 + NS);
+    ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 + 1), par(k0 + 1));
+    compute_mid(stage(k0), stage(k0 + 1), mcur, k0);
+    load_out_coef(stage(k0), coef_cur);
+    __syncthreads();  // intermediate planes k0-1 and k0 complete, input plane k0 consumed
+    refill(k0 + NS);
+    if (outer) {
+        prev_mid[0] = *reinterpret_cast<const float4 *>(mprev + oo);
+        prev_mid[1] = *reinterpret_cast<const float4 *>(mprev + T2::MID_F + oo);
+    }
+    const bool sens = p.ns > 0 && step < p.cap;
+    int so_k = sens ? __ldg(p.sens_off + k0) : 0;  // sensors of plane k: sens_ord[so_k .. so_k1)
+
+    // input slots of planes k+1 and k+2, parity of k+2's stage
+    int s1 = slot(k0 + 1), s2 = slot(k0 + 2);
+    uint32_t par2 = par(k0 + 2);
+    for (int k = k0; k < k1; ++k) {
+        const int so_k1 = sens ? __ldg(p.sens_off + k + 1) : 0;
+        ok &= mbar_wait_bounded(bar0 + 8 * s2, par2);
+        const float *sc = inr + s1 * T2::IN_STAGE;
+        compute_mid(sc, inr + s2 * T2::IN_STAGE, mfree, k + 1);  // into the buffer of plane k-2
+        if (k + 1 < k1) load_out_coef(sc, coef_next);
+        __syncthreads();  // intermediate plane k+1 complete; input plane k+1 consumed
+        refill(k + 1 + NS);
+        const float *mk = mcur, *mn = mfree;  // planes k and k+1
+        // sensors of the intermediate step owned by this block (plane k, component comp)
+        if (sens) {
+            float *tr = reinterpret_cast<float *>(p.traces) + (size_t)step * p.ns * 3;
+            for (int q = so_k + tid; q < so_k1; q += T2::NT) {
+                const int s = p.sens_ord[q];
+                const int i = p.sensors[3 * s], jj = p.sensors[3 * s + 1];
+                if (i >= x0 && i < x0 + TX && jj >= y0 && jj < y0 + TY && jj <= p.ny - 2)
+                    tr[3 * s + comp] = mk[(jj - y0 + 1) * BX + (i - x0 + 4)];
+            }
+        }
+        // second step of plane k from intermediate planes k-1 (registers), k, k+1
+        float4 c[2];
+        float2 s01[2], s23[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const float *fc = mk + f * T2::MID_F + oo;
+            c[f] = *reinterpret_cast<const float4 *>(fc);
+            const float4 ym = *reinterpret_cast<const float4 *>(fc - BX);
+            const float4 yp = *reinterpret_cast<const float4 *>(fc + BX);
+            const float4 zp = *reinterpret_cast<const float4 *>(mn + f * T2::MID_F + oo);
+            nbsum4(c[f], fc[-1], fc[4], ym, yp, prev_mid[f], zp, s01[f], s23[f]);
+            prev_mid[f] = c[f];
+        }
+        if (row_ok) {
+            const long long gbase = k * sz + (long long)y_out * sy + x_out;
+            float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g1 != 0.f) F4 = __ldg(reinterpret_cast<const float4 *>(Fc + gbase));
+            const float2 A01 = HET ? f2lo(coef_cur[0]) : Ah, A23 = HET ? f2hi(coef_cur[0]) : Ah;
+            const float2 B01 = HET ? f2lo(coef_cur[1]) : Bh, B23 = HET ? f2hi(coef_cur[1]) : Bh;
+            const float2 g = f2(g1, g1);
+            float2 u01, d01, u23, d23;
+            kv_update2(f2lo(c[0]), s01[0], f2lo(c[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
+            kv_update2(f2hi(c[0]), s23[0], f2hi(c[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
+            *reinterpret_cast<float4 *>(out_u + gbase) =
+                make_float4(m0 ? u01.x : 0.f, m1 ? u01.y : 0.f, m2 ? u23.x : 0.f, m3 ? u23.y : 0.f);
+            *reinterpret_cast<float4 *>(out_d + gbase) =
+                make_float4(m0 ? d01.x : 0.f, m1 ? d01.y : 0.f, m2 ? d23.x : 0.f, m3 ? d23.y : 0.f);
+        }
+        coef_cur[0] = coef_next[0];
+        coef_cur[1] = coef_next[1];
+        so_k = so_k1;
+        // rotate: the buffer of plane k-1 is the next free one
+        float *t = mprev;
+        mprev = mcur;
+        mcur = mfree;
+        mfree = t;
+        s1 = s2;
+        if (++s2 == NS) {
+            s2 = 0;
+            par2 ^= 1u;
+        }
+    }
+    if (__syncthreads_or(!ok) && tid == 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
+        for (int q = max(qb, next_issue - NS); q < next_issue; ++q) mbar_wait_bounded(bar0 + 8 * slot(q), par(q));
+    }
+    step_epilogue_n<float>(out, p, step, 2);
+}
+
+// ---------------------------------------------------------------------------
 // Small kernels: medium fold, initial velocity
 // ---------------------------------------------------------------------------
 // Grid: (ceil(px/128), ny, nz), block 128.
@@ -1376,8 +1692,37 @@ static bool pick2c_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, in
            pick2c<128, 8, NS>(tx, ty, NS, het, k, smem, nt);
 }
 
-// variant 2: three components per block; variant 3: one component per block
+template <int TX, int NS>
+static bool pick2b(int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (tx != TX || ty != Tile2B<TX, true>::TY || ns != NS) return false;
+    if (het) {
+        *k = k_step2b_tma<TX, NS, true>;
+        *smem = Tile2B<TX, true>::smem(NS);
+    } else {
+        *k = k_step2b_tma<TX, NS, false>;
+        *smem = Tile2B<TX, false>::smem(NS);
+    }
+    *nt = Tile2B<TX, true>::NT;
+    return true;
+}
+
+template <int NS>
+static bool pick2b_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    return pick2b<32, NS>(tx, ty, NS, het, k, smem, nt) || pick2b<64, NS>(tx, ty, NS, het, k, smem, nt) ||
+           pick2b<128, NS>(tx, ty, NS, het, k, smem, nt);
+}
+
+// variant 2: three components per block; variant 3: one component per block;
+// variant 4: one component per block, balanced TX x 14 tile
 static bool tma2_kernel_for(int variant, int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
+    if (variant == 4) {
+        switch (ns) {
+            case 3: return pick2b_tile<3>(tx, ty, het, k, smem, nt);
+            case 4: return pick2b_tile<4>(tx, ty, het, k, smem, nt);
+            case 6: return pick2b_tile<6>(tx, ty, het, k, smem, nt);
+            default: return false;
+        }
+    }
     if (variant == 3) {
         switch (ns) {
             case 4: return pick2c_tile<4>(tx, ty, het, k, smem, nt);
@@ -1440,7 +1785,7 @@ kv_status step_prepare(kv_handle *h) {
     TmaKernel k;
     size_t smem;
     int nt;
-    if (h->variant == 2 || h->variant == 3) {
+    if (h->variant >= 2) {
         if (step_kind(h) == kKindDiv)
             return set_error(h, KV_ERR_UNSUPPORTED, "the two-step kernels support only the pointwise operator");
         if (!tma2_kernel_for(h->variant, h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt))
@@ -1450,8 +1795,8 @@ kv_status step_prepare(kv_handle *h) {
             return set_error(h, KV_ERR_ARG, "two-step tile %dx%d with %d stages needs %zu bytes of shared memory",
                              h->tx, h->ty, h->ns_stages, smem);
         kv_status st;
-        // variant 3 stages one field per box (u_c and d_c are fields c and 3 + c)
-        const int fbox = h->variant == 3 ? 1 : 6;
+        // variants 3 and 4 stage one field per box (u_c and d_c are fields c and 3 + c)
+        const int fbox = h->variant >= 3 ? 1 : 6;
         for (int b = 0; b < 2; ++b)
             if ((st = encode_tensor_4d(h, &h->tm_state[b], h->state[b], 6, h->tx + 8, h->ty + 4, fbox)) != KV_OK)
                 return st;
@@ -1493,6 +1838,8 @@ static StepParams make_params(kv_handle *h, int nblocks) {
     p.Np = h->Np;
     p.A = h->A_s;
     p.B = h->B_s;
+    p.Af = (float)h->A_s;
+    p.Bf = (float)h->B_s;
     p.g = h->g_dev;
     p.n_g = h->have_force ? h->n_g : 0;
     p.g_const_on = h->have_force && h->g_const_on;
@@ -1521,7 +1868,7 @@ kv_status step2_launch(kv_handle *h, int from) {
     size_t smem;
     int nt;
     tma2_kernel_for(h->variant, h->tx, h->ty, h->ns_stages, h->het != 0, &k, &smem, &nt);
-    const int ncomp_blocks = h->variant == 3 ? 3 : 1;  // variant 3: the three components of a tile side by side
+    const int ncomp_blocks = h->variant >= 3 ? 3 : 1;  // variants 3, 4: the three components of a tile side by side
     dim3 grid(ncomp_blocks * ((h->px + h->tx - 1) / h->tx), (h->ny - 2 + h->ty - 1) / h->ty,
               (h->nz - 2 + h->zc - 1) / h->zc);
     StepParams p = make_params(h, grid.x * grid.y * grid.z);

@@ -122,21 +122,25 @@ def test_tma_tiles_match_plain_kernel_bitwise(device, het):
 
 TILES2 = [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4)]
 TILES3 = [(32, 8), (32, 16), (64, 4), (64, 8), (64, 16), (128, 4), (128, 8)]
+TILES4 = [(32, 14), (64, 14), (128, 14)]
+# tiles and stage counts of the two-step kernels
+TWO_STEP = {2: (TILES2, (4, 6)), 3: (TILES3, (4, 6)), 4: (TILES4, (3, 4, 6))}
 
 
-@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("variant", [2, 3, 4])
 @pytest.mark.parametrize("het", [True, False])
 @pytest.mark.parametrize("n_steps", [60, 61])
 def test_two_step_kernel_matches_plain_kernel_bitwise(device, variant, het, n_steps):
     """Temporal blocking (two steps per sweep; variant 2 all components per
-    block, variant 3 one component per block) reproduces single steps bit for
-    bit, including the intermediate step's sensor records and an odd step
-    count (the last step single)."""
+    block, variants 3 and 4 one component per block) reproduces single steps
+    bit for bit, including the intermediate step's sensor records and an odd
+    step count (the last step single)."""
     w = ragged_workload(het=het)
     v0 = inputs.curl_gaussian_velocity(w.nx, w.ny, w.nz, w.dx, sigma=1e-3, envelope="xyz")
     ref_tr, ref_f = run_variant(w, {"variant": 1}, n_steps, v0)
-    for tx, ty in (TILES2 if variant == 2 else TILES3):
-        for ns in (4, 6):
+    tiles, stages = TWO_STEP[variant]
+    for tx, ty in tiles:
+        for ns in stages:
             for zc in (3, 64):
                 try:
                     tr, f = run_variant(w, {"variant": variant, "tx": tx, "ty": ty, "zc": zc, "ns": ns},
@@ -148,10 +152,11 @@ def test_two_step_kernel_matches_plain_kernel_bitwise(device, variant, het, n_st
                 assert np.array_equal(f, ref_f), (tx, ty, ns, zc)
 
 
-@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("variant", [2, 3, 4])
 def test_two_step_graph_replay_matches_direct(device, variant):
     w = ragged_workload()
-    a = Solver(w, n_steps=75, step_config={"variant": variant, "tx": 64, "ty": 4, "zc": 16, "ns": 4})
+    a = Solver(w, n_steps=75, step_config={"variant": variant, "tx": 64, "ty": 14 if variant == 4 else 4,
+                                           "zc": 16, "ns": 4})
     a.project()
     a.step(75)  # one graph of 32 steps (16 two-step launches) + 21 pairs + 1 single
     ta = a.read_traces().cpu().numpy().copy()
@@ -170,7 +175,7 @@ def test_autotuner_picks_a_valid_config_and_resets(device):
     s.project()
     ms = kv.kv_autotune_step(s.h, 4)
     cfg = kv.kv_get_step_config(s.h)
-    assert ms > 0 and cfg["variant"] in (0, 2, 3) and cfg["ns"] in (4, 6, 8)
+    assert ms > 0 and cfg["variant"] in (0, 2, 3, 4) and cfg["ns"] in (3, 4, 6, 8)
     assert kv.kv_steps_taken(s.h) == 0
     s.step()
     tr = s.read_traces().cpu().numpy().copy()
