@@ -1205,15 +1205,16 @@ __device__ __forceinline__ float2 f2lo(const float4 &v) { return make_float2(v.x
 __device__ __forceinline__ float2 f2hi(const float4 &v) { return make_float2(v.z, v.w); }
 
 // Neighbour sums ((xm + xp) + (ym + yp)) + (zm + zp) of four consecutive
-// nodes (left / right: the x neighbours beyond the group), as two pairs.
+// nodes (left / right: the x neighbours beyond the group), as two pairs. The
+// x sums straddle the pairs of the group, so they are formed one node at a
+// time (into fresh registers that pair up without moves).
 __device__ __forceinline__ void nbsum4(const float4 &c, float left, float right, const float4 &ym,
                                        const float4 &yp, const float4 &zm, const float4 &zp, float2 &s01,
                                        float2 &s23) {
-    const float2 mid = f2(c.y, c.z);
-    s01 = __fadd2_rn(__fadd2_rn(__fadd2_rn(f2(left, c.x), mid), __fadd2_rn(f2lo(ym), f2lo(yp))),
-                     __fadd2_rn(f2lo(zm), f2lo(zp)));
-    s23 = __fadd2_rn(__fadd2_rn(__fadd2_rn(mid, f2(c.w, right)), __fadd2_rn(f2hi(ym), f2hi(yp))),
-                     __fadd2_rn(f2hi(zm), f2hi(zp)));
+    const float2 x01 = f2(__fadd_rn(left, c.y), __fadd_rn(c.x, c.z));
+    const float2 x23 = f2(__fadd_rn(c.y, c.w), __fadd_rn(c.z, right));
+    s01 = __fadd2_rn(__fadd2_rn(x01, __fadd2_rn(f2lo(ym), f2lo(yp))), __fadd2_rn(f2lo(zm), f2lo(zp)));
+    s23 = __fadd2_rn(__fadd2_rn(x23, __fadd2_rn(f2hi(ym), f2hi(yp))), __fadd2_rn(f2hi(zm), f2hi(zp)));
 }
 
 // kv_update on a pair of nodes.
