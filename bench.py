@@ -151,7 +151,7 @@ def parse():
                     help="time steps of the pass (default: the workload's own)")
     ap.add_argument("--step-config", default=None,
                     help="[variant,]tx,ty,zc,ns of the step kernel instead of autotuning "
-                         "(profiling runs; variant 0 one step per sweep, 2 two steps per sweep)")
+                         "(profiling runs; variant 0 one step per sweep, 2 to 4 two steps per sweep)")
     ap.add_argument("--projection", default="auto", choices=["auto", "learned", "mg", "cg"],
                     help="learned: the trained network's potential as the start of the "
                          "multigrid-preconditioned CG (mode 5); mg: that CG from zero (mode 4); cg: "
@@ -484,7 +484,7 @@ def main():
     step_cfg = kv.kv_get_step_config(h)
     classes = kv.kv_medium_classes(h) if step_cfg["variant"] == 0 else 0
     medium_enc = "classes" if classes > 0 else "fields"
-    two_step = step_cfg["variant"] in (2, 3)  # temporal blocking: one sweep advances two steps
+    two_step = step_cfg["variant"] in (2, 3, 4)  # temporal blocking: one sweep advances two steps
     bytes_per_cell = (CLASS_STEP_BYTES_PER_CELL if classes > 0 else
                       DIV_STEP_BYTES_PER_CELL if div else STEP_BYTES_PER_CELL)
     if two_step:
@@ -649,7 +649,7 @@ def main():
                                             "this run" if traffic is not None else
                                             "no stored capture for this configuration"),
                          "kernel": {0: "k_step_tma", 1: "k_step_plain", 2: "k_step2_tma",
-                                    3: "k_step2c_tma"}[step_cfg["variant"]],
+                                    3: "k_step2c_tma", 4: "k_step2b_tma"}[step_cfg["variant"]],
                          "steps_per_launch": 2 if two_step else 1, "peak_kind": peak_kind,
                          "bytes_model": (f"algorithmic {ALG_BYTES_HETEROG} B/cell (heterogeneous, "
                                          f"3-level recurrence) + {FORCE_BYTES_PER_CELL} B/cell "
