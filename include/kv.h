@@ -259,6 +259,29 @@ kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx, const floa
                                    float *fs_out, kv_cg_stats *stats, void *stream);
 
 /*
+ * One application of the preconditioner of projection modes 4 and 5: z = M r
+ * with M the symmetric multigrid V(1,1)-cycle for A = -L (the 7-point
+ * Laplacian of Sec. 3.2.3 with phi = 0 on the outer layer) on the handle's
+ * grid: damped Jacobi smoothing (omega = 6/7), cell-centred coarsening of the
+ * interior nodes (coarse cell I covers fine cells 2I-1 and 2I), trilinear
+ * prolongation P, restriction P^T / 8, 32 damped Jacobi sweeps on the
+ * coarsest level (at most 4096 cells with the ghost layer); a grid too small
+ * to coarsen gets M = omega dx^2 / 6 (diagonal scaling). The paper has no
+ * counterpart (its CG is unpreconditioned); this entry point exposes the
+ * operator the mode-4 CG applies every iteration, for checks and reuse.
+ * nx, ny, nz: the handle's grid (KV_ERR_ARG if they differ). r, z: device
+ * pointers to dense nz*ny*nx floats (x fastest), the caller's; only r's
+ * interior nodes are read, z is written on every node (0 on the outer layer).
+ * rz: NULL or receives r.z over the interior (FP64 sum of float-float
+ * partials; 0 when r is 0). FP32 handles only (KV_ERR_UNSUPPORTED otherwise);
+ * the first call allocates the level arrays (as the first mode-4 projection
+ * does). Uses the handle's CG scratch and control block, so it must not run
+ * while a projection of the same handle is in flight. Synchronising.
+ */
+kv_status kv_apply_preconditioner(kv_handle *h, int nx, int ny, int nz, const float *r, float *z,
+                                  double *rz);
+
+/*
  * Learned warm start of the projection. A small 3D U-Net (BF16 tensor-core
  * convolutions with FP32 accumulation, trained on the GPU by these calls)
  * maps the Poisson right-hand side b = -(D- . f) to an approximation of phi;

@@ -685,4 +685,97 @@ void mg_apply(kv_handle *h, const CgParams &p) {
     }
 }
 
+// Dense (x fastest) <-> pitched level-0 layout; the pitched array gets 0 off
+// the interior (ghost layer and row padding).
+__global__ void k_mg_dense_in(const float *__restrict__ r, float *__restrict__ rp, int nx, int ny, int nz,
+                              int px) {
+    const long long n = (long long)px * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % px);
+        const long long jk = q / px;
+        const int j = (int)(jk % ny), k = (int)(jk / ny);
+        const bool in = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+        rp[q] = in ? r[((long long)k * ny + j) * nx + i] : 0.f;
+    }
+}
+
+__global__ void k_mg_dense_out(const float *__restrict__ zp, float *__restrict__ z, int nx, int ny, int nz,
+                               int px) {
+    const long long n = (long long)nx * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % nx);
+        const long long jk = q / nx;
+        const int j = (int)(jk % ny), k = (int)(jk / ny);
+        const bool in = i >= 1 && i <= nx - 2 && j >= 1 && j <= ny - 2 && k >= 1 && k <= nz - 2;
+        z[q] = in ? zp[((long long)k * ny + j) * px + i] : 0.f;
+    }
+}
+
 }  // namespace kv
+
+using namespace kv;
+
+extern "C" kv_status kv_apply_preconditioner(kv_handle *h, int nx, int ny, int nz, const float *r, float *z,
+                                             double *rz) {
+    if (!h || !r || !z) return set_error(h, KV_ERR_ARG, "kv_apply_preconditioner: null handle or pointer");
+    if (nx != h->nx || ny != h->ny || nz != h->nz)
+        return set_error(h, KV_ERR_ARG, "kv_apply_preconditioner: grid %dx%dx%d is not the handle's %dx%dx%d", nx, ny,
+                         nz, h->nx, h->ny, h->nz);
+    if (h->sticky) return KV_ERR_STATE;
+    if (h->precision != KV_FP32)
+        return set_error(h, KV_ERR_UNSUPPORTED, "kv_apply_preconditioner: the multigrid cycle needs an FP32 handle");
+    kv_status st = mg_prepare(h);
+    if (st != KV_OK) return st;
+    cudaStream_t s = h->stream;
+    // control block: "running" with zero iterations and ticket, r.z slot cleared
+    cudaError_t e = cudaMemcpyAsync(h->ctrl_host, h->ctrl, kCtrlWords * sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(h, e, "kv_apply_preconditioner");
+    if (h->ctrl_host[kErrFlags] & 1)
+        return set_error(h, KV_ERR_STATE, "kv_apply_preconditioner: the handle has an unread device timeout");
+    h->ctrl_host[kCgStatus] = kCgRunning;
+    h->ctrl_host[kCgIters] = 0;
+    h->ctrl_host[kCgTicket] = 0;
+    for (int q = 0; q < kCgScalars; ++q) h->scal_host[q] = 0.0;
+    e = cudaMemcpyAsync(h->ctrl, h->ctrl_host, kCtrlWords * sizeof(long long), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->scal, h->scal_host, kCgScalars * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_check(h, e, "kv_apply_preconditioner");
+    const int blocks = 148 * 8;
+    k_mg_dense_in<<<blocks, 256, 0, s>>>(r, h->mg[0].r, h->nx, h->ny, h->nz, h->px);
+    CgParams p{};
+    p.pcg = 1;
+    p.rbuf = h->mg[0].r;
+    p.rfield = 0;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.nz = h->nz;
+    p.px = h->px;
+    p.Np = h->Np;
+    p.inv_dx2 = 1.0 / (h->dx * h->dx);
+    p.inv_dx = 1.0 / h->dx;
+    p.ctrl = h->ctrl;
+    p.scal = h->scal;
+    p.partials = h->partials;
+    p.zc = 1;
+    p.nblocks = 1;  // mg_apply sets the top level's block count
+    mg_apply(h, p);
+    k_mg_dense_out<<<blocks, 256, 0, s>>>((const float *)h->cgv + h->Np, z, h->nx, h->ny, h->nz, h->px);
+    h->launches += 2;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(h, e, "kv_apply_preconditioner launch");
+    e = cudaMemcpyAsync(h->ctrl_host, h->ctrl, kCtrlWords * sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->scal_host, h->scal, kCgScalars * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(h, e, "kv_apply_preconditioner");
+    if (h->ctrl_host[kErrFlags] & 1)
+        return set_error(h, KV_ERR_TIMEOUT, "kv_apply_preconditioner: a bounded device wait gave up");
+    if (rz) *rz = h->scal_host[kRR];
+    // the top level sets non-finite or breakdown (r.z <= 0, e.g. r = 0) in the
+    // control word; only the non-finite case is an error here
+    if (h->ctrl_host[kCgStatus] == kCgNonfinite)
+        return set_error(h, KV_ERR_NONFINITE, "kv_apply_preconditioner: r.z is not finite");
+    return KV_OK;
+}
+

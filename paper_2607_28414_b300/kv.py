@@ -114,6 +114,7 @@ def lib():
         L.kv_launch_count.argtypes = [H]
         L.kv_launch_count.restype = ctypes.c_longlong
         L.kv_destroy.argtypes = [H]
+        L.kv_apply_preconditioner.argtypes = [H, i, i, i, vp, vp, ctypes.POINTER(d)]
         L.kv_project_force_noalloc.argtypes = [i, i, i, d, vp, vp, vp, d, i, vp,
                                                ctypes.POINTER(KvCgStats), vp]
         L.kv_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
@@ -337,6 +338,26 @@ def kv_project_force(h, fx, fy, fz, tol, max_iter=0, mode=0, fs_out=None, check=
     if check or rc not in (KV_CG_MAXITER, KV_CG_BREAKDOWN, KV_ERR_NONFINITE):
         _check(rc, h)
     return d
+
+
+def kv_apply_preconditioner(h, r, z):
+    """z = M r with the mode-4 multigrid V-cycle (see include/kv.h). r, z:
+    contiguous float32 CUDA tensors of shape (nz, ny, nx), the handle's grid.
+    Returns r.z over the interior."""
+    import torch
+    for name, t in (("r", r), ("z", z)):
+        if not isinstance(t, torch.Tensor) or t.dim() != 3:
+            raise ValueError(f"kv_apply_preconditioner: {name} must be a 3D torch tensor (nz, ny, nx)")
+        _check_f32_buffer("kv_apply_preconditioner", name, t, r.numel())
+        if not t.is_cuda:
+            raise ValueError("kv_apply_preconditioner takes device tensors")
+    if tuple(z.shape) != tuple(r.shape):
+        raise ValueError("kv_apply_preconditioner: r and z differ in shape")
+    nz, ny, nx = (int(v) for v in r.shape)
+    rz = ctypes.c_double()
+    _check(lib().kv_apply_preconditioner(h, nx, ny, nz, ctypes.c_void_p(r.data_ptr()),
+                                         ctypes.c_void_p(z.data_ptr()), ctypes.byref(rz)), h)
+    return rz.value
 
 
 def kv_project_force_noalloc(nx, ny, nz, dx, fx, fy, fz, tol, fs_out, max_iter=0, stream=None):

@@ -85,3 +85,62 @@ def test_multigrid_needs_fp32(device):
         kv.kv_project_force(s.h, *s.force, 1e-9, 0, 4)
     assert e.value.status == kv.KV_ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("shape", [(70, 37, 45), (45, 40, 33), (130, 20, 22), (8, 7, 9), (5, 5, 5), (256, 256, 256)])
+def test_preconditioner_matches_the_oracle_cycle(device, shape):
+    """kv_apply_preconditioner (the V-cycle every mode-4 iteration applies)
+    against the oracle's FP64 cycle (oracle/multigrid.py) on seeded random
+    residuals: every node, and r.z. The 5^3 grid is too small to coarsen
+    (M = S); the others run two to seven levels."""
+    from oracle import multigrid as omg
+    nx, ny, nz = shape
+    dx = 2e-4
+    rng = np.random.default_rng(nx * 7 + ny * 3 + nz)
+    r = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    s = torch.cuda.Stream(device)
+    with torch.cuda.stream(s):
+        dt = 0.5 * kv.kv_stable_dt(nx, ny, nz, dx, 4e3, 1000.0, 0.0)
+        h = kv.kv_create(nx, ny, nz, dx, dt, 4e3, 1000.0, 0.0, stream=s.cuda_stream)
+        try:
+            rd = torch.from_numpy(r).to(device)
+            z = torch.full_like(rd, float("nan"))
+            rz = kv.kv_apply_preconditioner(h, rd, z)
+            z2 = torch.empty_like(rd)
+            rz2 = kv.kv_apply_preconditioner(h, rd, z2)  # a second call: the same bits
+            z0 = torch.full_like(rd, float("nan"))
+            rz0 = kv.kv_apply_preconditioner(h, torch.zeros_like(rd), z0)
+            same = bool(torch.equal(z, z2))
+            zero_out = bool((z0 == 0).all())
+        finally:
+            kv.kv_destroy(h)
+    got = z.cpu().numpy().astype(np.float64)
+    ref = omg.vcycle_grid(r, dx)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    rz_ref = float((r.astype(np.float64)[1:-1, 1:-1, 1:-1] * ref[1:-1, 1:-1, 1:-1]).sum())
+    levels = len(omg.levels((nx - 2, ny - 2, nz - 2), dx * dx))
+    print(f"{shape}: {levels} levels, max |z - z_oracle| / max |z_oracle| = {err:.2e}, "
+          f"r.z rel. error {abs(rz - rz_ref) / rz_ref:.2e}")
+    assert np.all(got[0] == 0) and np.all(got[-1] == 0) and np.all(got[:, 0] == 0) and np.all(got[:, :, -1] == 0)
+    assert err <= 2e-6  # FP32 through up to seven levels: measured 4e-8 ... 3.1e-7
+    assert rz == pytest.approx(rz_ref, rel=1e-6)
+    assert same and rz2 == rz
+    assert zero_out and rz0 == 0.0
+
+
+def test_preconditioner_argument_checks(device):
+    w = ragged_workload()
+    s = Solver(w)
+    r = torch.zeros((w.nz, w.ny, w.nx), dtype=torch.float32, device=device)
+    with pytest.raises(ValueError):
+        kv.kv_apply_preconditioner(s.h, r, torch.zeros((w.nz, w.ny, w.nx + 1), dtype=torch.float32, device=device))
+    with pytest.raises(kv.KvError) as e:
+        bad = torch.zeros((w.nz, w.ny + 1, w.nx), dtype=torch.float32, device=device)
+        kv.kv_apply_preconditioner(s.h, bad, torch.zeros_like(bad))
+    assert e.value.status == kv.KV_ERR_ARG
+    s.close()
+    s64 = Solver(w, precision=kv.KV_FP64)
+    with pytest.raises(kv.KvError) as e:
+        kv.kv_apply_preconditioner(s64.h, r, torch.zeros_like(r))
+    assert e.value.status == kv.KV_ERR_UNSUPPORTED
+    s64.close()
