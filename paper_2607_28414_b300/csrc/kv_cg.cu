@@ -253,7 +253,6 @@ k_cg_upd(const T *__restrict__ p0, const T *__restrict__ p1, T *__restrict__ r, 
 // tiles. Per-node arithmetic is the same sequence as the plain kernels above.
 // Reductions: float-float per thread and across the block, double per block.
 // ---------------------------------------------------------------------------
-constexpr int kCgTX = 64, kCgTY = 8;
 constexpr int kCgNT = kCgTX * kCgTY / 4;
 constexpr int kCgGX = kCgTX / 4;
 constexpr int kCgBXh = kCgTX + 8, kCgBYh = kCgTY + 2;

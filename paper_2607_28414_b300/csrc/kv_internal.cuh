@@ -111,6 +111,9 @@ struct CgParams {
 // of (nx + 2) x (ny + 2) x (nz + 2) with a zero ghost layer and row pitch px
 // (level 0 is the handle's pitched grid).
 constexpr int kMgMaxLevels = 12;
+// Column of one block of the TMA CG passes (x, y nodes); the multigrid's fine
+// residual is staged by the update pass with the same box.
+constexpr int kCgTX = 64, kCgTY = 8;
 struct MgLevel {
     int nx, ny, nz, px;
     long long n;         // elements of one array (px * (ny + 2) * (nz + 2))

@@ -606,7 +606,7 @@ kv_status mg_prepare(kv_handle *h) {
     }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    kv_status st = encode_tensor_4d(h, &h->tm_mg_r, L[0].r, 1, 64, 8, 1);
+    kv_status st = encode_tensor_4d(h, &h->tm_mg_r, L[0].r, 1, kCgTX, kCgTY, 1);
     for (int l = 0; st == KV_OK && l + 1 < nl; ++l) {
         MgLevel &f = L[l];
         const MgLevel &c = L[l + 1];
