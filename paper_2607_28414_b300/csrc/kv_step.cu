@@ -1260,7 +1260,6 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
     __syncthreads();
     auto slot = [&](int q) { return (int)((unsigned)(q - qb) % NS); };
     auto par = [&](int q) { return ((unsigned)(q - qb) / NS) & 1u; };
-    auto midp = [&](int j) { return mid + ((unsigned)(j - (k0 - 1)) % 3u) * T2::MID_STAGE; };
     auto issue = [&](int q) {
         const uint32_t bar = bar0 + 8 * slot(q);
         float *st = inr + slot(q) * T2::IN_STAGE;
