@@ -85,10 +85,10 @@ def job_rate(world, cell_updates_per_rank, t_max):
 
 
 def step_traffic(w, step_cfg, operator, n_force_steps, medium="fields", with_source=False):
-    """DRAM bytes per step launch from the committed ncu capture
+    """DRAM bytes per step from the committed ncu capture
     (profiles/kv_step_traffic.json: dram__bytes_read.sum + dram__bytes_write.sum
-    of force and plain steps), averaged over this pass's launches like
-    `achieved`; None unless a capture is of this operator, medium encoding
+    of force and plain steps; a two-step launch's bytes over two), averaged over
+    this pass's steps (the caller scales it to a launch, like `achieved`); None unless a capture is of this operator, medium encoding
     ("fields" or "classes") and kernel configuration, and either of this grid
     or marked `scale_by_cells` for this workload family (a smaller case of a
     grid too large to capture, scaled by the cell count). with_source: also
@@ -561,14 +561,18 @@ def main():
     t_max = slowest(t_total, world, device)
     value = job_rate(world, N * w.n_steps * args.steps, t_max)
     step_gcells = N * w.n_steps * args.steps / t_steps / 1e9
-    launch_s = t_steps / (w.n_steps * args.steps)
-    force_bytes = N * FORCE_BYTES_PER_CELL * n_force_steps / w.n_steps  # per launch, averaged
-    alg_bytes = N * ALG_BYTES_HETEROG + force_bytes
+    # a launch advances steps_per_launch steps (two for the two-step kernels)
+    spl = 2 if two_step else 1
+    launch_s = spl * t_steps / (w.n_steps * args.steps)
+    force_bytes = N * FORCE_BYTES_PER_CELL * n_force_steps / w.n_steps  # per step, averaged
+    alg_bytes = spl * (N * ALG_BYTES_HETEROG + force_bytes)             # per launch
     achieved = alg_bytes / launch_s / 1e9
-    achieved_storage = (N * bytes_per_cell + force_bytes) / launch_s / 1e9
+    achieved_storage = spl * (N * bytes_per_cell + force_bytes) / launch_s / 1e9
     peak, peak_kind = peaks()
     traffic, traffic_src = step_traffic(w, step_cfg, args.operator, n_force_steps, medium_enc,
                                         with_source=True)
+    if traffic is not None:
+        traffic *= spl  # the capture's bytes per step, per launch
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -650,7 +654,8 @@ def main():
                                             "no stored capture for this configuration"),
                          "kernel": {0: "k_step_tma", 1: "k_step_plain", 2: "k_step2_tma",
                                     3: "k_step2c_tma", 4: "k_step2b_tma"}[step_cfg["variant"]],
-                         "steps_per_launch": 2 if two_step else 1, "peak_kind": peak_kind,
+                         "steps_per_launch": spl, "cell_steps_per_launch": N * spl,
+                         "peak_kind": peak_kind,
                          "bytes_model": (f"algorithmic {ALG_BYTES_HETEROG} B/cell (heterogeneous, "
                                          f"3-level recurrence) + {FORCE_BYTES_PER_CELL} B/cell "
                                          "on force steps"),
