@@ -409,7 +409,9 @@ kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, 
 kv_status kv_get_step_config(kv_handle *h, int *cfg);
 
 /* Autotuner of the FP32 step: times trial_steps steps of every supported
- * (variant, tile, stage count, z chunk) on this handle's grid with CUDA events
+ * (variant, tile, stage count, z chunk; z chunks 16, 32, 64, and for variant 4
+ * 32, 64, 128 and a third, a half and all of the interior depth) on this
+ * handle's grid with CUDA events
  * on its stream, times the four fastest (and the fastest one-step candidate)
  * again over 4 x trial_steps steps and keeps the fastest of those, a two-step
  * variant only if it is more than 3 % faster than the best one-step kernel,

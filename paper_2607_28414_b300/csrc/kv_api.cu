@@ -867,9 +867,16 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
     for (auto &t : tiles3)
         for (int ns : {4, 6})
             for (int zc : zcs) cands.push_back({3, t[0], t[1], ns, zc});
+    // variant 4 marches whole columns best: add z chunks of a third, a half
+    // and all of the interior depth (fewer chunks, less z halo per block)
+    std::vector<int> zcs4 = {32, 64, 128};
+    for (int parts : {3, 2, 1}) {
+        const int zc = (h->nz - 2 + parts - 1) / parts;
+        if (std::find(zcs4.begin(), zcs4.end(), zc) == zcs4.end()) zcs4.push_back(zc);
+    }
     for (int tx : {32, 64, 128})
-        for (int ns : {3, 4, 6})
-            for (int zc : zcs) cands.push_back({4, tx, 14, ns, zc});
+        for (int ns : {3, 4})
+            for (int zc : zcs4) cands.push_back({4, tx, 14, ns, zc});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(h, KV_ERR_CUDA, "kv_autotune_step: cudaEventCreate failed");
