@@ -158,7 +158,10 @@ k_mg_down(const __grid_constant__ CUtensorMap tm_r, MgLevel F, MgLevel C, int zc
         for (int q = qb; q <= min(qe, qb + kDnNS - 1); ++q) issue(q);
 
     // t cells: main threads (x .. x+3, y), the extra warp (x, y) at column 64 or 65
-    const bool is_main = tid < kDnMain;
+    // warp index through a shuffle: the compiler then treats the role tests
+    // below as uniform over a warp (they are: the roles are whole warps)
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const bool is_main = warp < kDnMain / 32;
     const int g = tid % 16, row = is_main ? tid / 16 : (tid - kDnMain) >> 1;
     const int col = is_main ? 4 * g : 64 + (tid & 1);  // t column
     const int x = xb + 4 + col, y = yb + 1 + row;
@@ -170,7 +173,7 @@ k_mg_down(const __grid_constant__ CUtensorMap tm_r, MgLevel F, MgLevel C, int zc
     // the coarse column: rows 2cj .. 2cj+3 and columns 2ci .. 2ci+3 of the t plane
     const int ci = tid % kDnCX, cj = tid / kDnCX;
     const int I = 1 + kDnCX * (int)blockIdx.x + ci, J = 1 + kDnCY * (int)blockIdx.y + cj;
-    const bool cthread = tid < kDnCX * kDnCY, cstore = cthread && I <= C.nx && J <= C.ny;
+    const bool cthread = warp < kDnCX * kDnCY / 32, cstore = cthread && I <= C.nx && J <= C.ny;
     const long long csz = (long long)C.px * (C.ny + 2);
     float *cr = C.r + (long long)J * C.px + I + (long long)K0 * csz;  // coarse plane K0
     const int oc = 2 * cj * kDnTP + 2 * ci;
@@ -321,7 +324,8 @@ k_mg_up(const __grid_constant__ CUtensorMap tm_r, const __grid_constant__ CUtens
 
     // main threads: cells (x .. x+3, y); halo warp: the cell (x, y) at staged
     // column 3 (x = kUpTX bx - 1) or 68 (x = kUpTX bx + kUpTX)
-    const bool is_main = tid < kUpMain;
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);  // role tests uniform over a warp
+    const bool is_main = warp < kUpMain / 32;
     const int g = tid % 16, row = is_main ? tid / 16 : (tid - kUpMain) >> 1;
     const int col = is_main ? 4 + 4 * g : ((tid & 1) ? 4 + kUpTX : 3);  // staged column
     const int x = xb + col, y = yb + row;
