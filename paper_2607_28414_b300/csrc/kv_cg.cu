@@ -52,7 +52,26 @@ __device__ __forceinline__ void node_of(int &i, int &j) {
     j = blockIdx.y * kCgBY + (threadIdx.x / kCgBX);
 }
 
-// b = -(D- . f) on interior nodes, ||b||^2.
+// Error-free float operations (Knuth's TwoSum; the exact difference a - b of
+// two floats as hi + lo), so that sums of float differences are formed on the
+// FP32 pipes (B300's FP64 rate is a small fraction of its FP32 rate).
+__device__ __forceinline__ void two_sum(float a, float b, float &hi, float &lo) {
+    hi = __fadd_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += (bh, bl), renormalised
+__device__ __forceinline__ void ff_acc(float &hi, float &lo, float bh, float bl) {
+    float s, e;
+    two_sum(hi, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// b = -(D- . f) on interior nodes, ||b||^2. The three differences of float
+// neighbours are exact as float pairs and summed in float-float; b is that sum
+// (to about 1e-14) times -1/dx in double.
 __global__ void __launch_bounds__(kCgBX *kCgBY)
 k_rhs(const float *__restrict__ f, double *__restrict__ b, CgParams p) {
     int i, j;
@@ -66,13 +85,16 @@ k_rhs(const float *__restrict__ f, double *__restrict__ b, CgParams p) {
             double v = 0.0;
             if (is_interior(i, j, k, p.nx, p.ny, p.nz)) {
                 const float *fx = f, *fy = f + p.Np, *fz = f + 2 * p.Np;
-                const double d = ((double)fx[c] - (double)fx[c - 1]) +
-                                 ((double)fy[c] - (double)fy[c - sy]) +
-                                 ((double)fz[c] - (double)fz[c - sz]);
-                v = -(d * p.inv_dx);
+                float hi, lo, h2, l2;
+                two_sum(fx[c], -fx[c - 1], hi, lo);
+                two_sum(fy[c], -fy[c - sy], h2, l2);
+                ff_acc(hi, lo, h2, l2);
+                two_sum(fz[c], -fz[c - sz], h2, l2);
+                ff_acc(hi, lo, h2, l2);
+                v = -(((double)hi + (double)lo) * p.inv_dx);
             }
             b[c] = v;
-            acc += v * v;
+            acc = __fma_rn(v, v, acc);
         }
     }
     double v1[1] = {acc}, s[1];
@@ -104,7 +126,10 @@ k_true_res(const double *__restrict__ b, const double *__restrict__ phi, T *__re
     node_of(i, j);
     const long long sy = p.px, sz = (long long)p.px * p.ny;
     const int k0 = blockIdx.z * p.zc, k1 = min(k0 + p.zc, p.nz);
-    double acc_t = 0.0, acc_r = 0.0;
+    // FP32 handles: both norms from the stored (rounded) residual, accumulated
+    // in float-float (a relative 1e-7 on the true norm; the FP64 pipe keeps
+    // only the residual itself); FP64 handles: in double
+    typename AccOf<T>::type acc_t, acc_r;
     if (i < p.nx && j < p.ny) {
         for (int k = k0; k < k1; ++k) {
             if (!is_interior(i, j, k, p.nx, p.ny, p.nz)) continue;
@@ -115,11 +140,12 @@ k_true_res(const double *__restrict__ b, const double *__restrict__ phi, T *__re
             const double rt = b[c] + lap;  // b - A phi, A = -L
             const T rs = T(rt);
             r[c] = rs;
-            acc_t += rt * rt;
-            acc_r += (double)rs * (double)rs;
+            if constexpr (sizeof(T) == 8) acc_t.add_prod(rt, rt);
+            else acc_t.add_prod(rs, rs);
+            acc_r.add_prod(rs, rs);
         }
     }
-    double v[2] = {acc_t, acc_r}, s[2];
+    double v[2] = {acc_t.value(), acc_r.value()}, s[2];
     if (last_block_sums<2>(p, v, s) && threadIdx.x == 0) {
         const double bb = p.scal[kBB];
         p.scal[kTrue2] = s[0];
