@@ -582,12 +582,23 @@ k_grad(const float *__restrict__ f, const double *__restrict__ phi, const T *__r
         const double py_ = (j + 1 < p.ny) ? phi[c + sy] : 0.0;
         const double pz_ = (k + 1 < p.nz) ? phi[c + sz] : 0.0;
         const double g[3] = {(px_ - ph) * p.inv_dx, (py_ - ph) * p.inv_dx, (pz_ - ph) * p.inv_dx};
-        const double s = S ? (double)S[c] : S_s;
         const long long cd = ((long long)k * p.ny + j) * p.nx + i;
-        for (int comp = 0; comp < 3; ++comp) {
-            const double fsv = (double)f[comp * p.Np + c] - g[comp];
-            F[comp * p.Np + c] = T(s * fsv);
-            if (fs_out) fs_out[comp * Nd + cd] = (float)fsv;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 handles: f_S0 rounded to float once, the scaling by S in FP32
+            // (the FP64 pipe keeps only the gradient and the subtraction)
+            const float s = S ? (float)S[c] : (float)S_s;
+            for (int comp = 0; comp < 3; ++comp) {
+                const float fsv = (float)((double)f[comp * p.Np + c] - g[comp]);
+                F[comp * p.Np + c] = __fmul_rn(s, fsv);
+                if (fs_out) fs_out[comp * Nd + cd] = fsv;
+            }
+        } else {
+            const double s = S ? (double)S[c] : S_s;
+            for (int comp = 0; comp < 3; ++comp) {
+                const double fsv = (double)f[comp * p.Np + c] - g[comp];
+                F[comp * p.Np + c] = T(s * fsv);
+                if (fs_out) fs_out[comp * Nd + cd] = (float)fsv;
+            }
         }
     }
 }
