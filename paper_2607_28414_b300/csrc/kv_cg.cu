@@ -122,6 +122,8 @@ __global__ void __launch_bounds__(kCgBX *kCgBY)
 k_true_res(const double *__restrict__ b, const double *__restrict__ phi, T *__restrict__ r,
            CgParams p) {
     if (__ldcg(&p.ctrl[kCgStatus]) != kCgNeedTrue) return;
+    // the first evaluation of a start from zero is r = b (no FP64 stencil)
+    const bool phi0 = p.zero_start && __ldcg(&p.ctrl[kCgRefine]) == 0;
     int i, j;
     node_of(i, j);
     const long long sy = p.px, sz = (long long)p.px * p.ny;
@@ -134,10 +136,12 @@ k_true_res(const double *__restrict__ b, const double *__restrict__ phi, T *__re
         for (int k = k0; k < k1; ++k) {
             if (!is_interior(i, j, k, p.nx, p.ny, p.nz)) continue;
             const long long c = k * sz + j * sy + i;
-            const double s = ((phi[c - 1] + phi[c + 1]) + (phi[c - sy] + phi[c + sy])) +
-                             (phi[c - sz] + phi[c + sz]);
-            const double lap = (s - 6.0 * phi[c]) * p.inv_dx2;
-            const double rt = b[c] + lap;  // b - A phi, A = -L
+            double rt = b[c];  // b - A phi, A = -L
+            if (!phi0) {
+                const double s = ((phi[c - 1] + phi[c + 1]) + (phi[c - sy] + phi[c + sy])) +
+                                 (phi[c - sz] + phi[c + sz]);
+                rt += (s - 6.0 * phi[c]) * p.inv_dx2;
+            }
             const T rs = T(rt);
             r[c] = rs;
             if constexpr (sizeof(T) == 8) acc_t.add_prod(rt, rt);
@@ -697,8 +701,9 @@ kv_status stable_dt_device(cudaStream_t stream, double *scratch, int nx, int ny,
 // Host driver
 // ---------------------------------------------------------------------------
 static CgParams cg_params(kv_handle *h, dim3 grid, int zc) {
-    CgParams p;
+    CgParams p{};
     p.pcg = 0;
+    p.zero_start = 0;
     p.rbuf = (float *)h->cgv + h->Np;  // r in field 1 of the CG vectors
     p.rfield = 1;
     p.nx = h->nx;
@@ -857,8 +862,8 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p[0], 0, h->Np * sizeof(T), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p[1], 0, h->Np * sizeof(T), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->e, 0, h->Np * sizeof(T), s);
-    if (e == cudaSuccess && !(mode == 3 && h->phi_valid))  // mode 3 starts from the previous phi
-        e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s);
+    bool phi_zero = !(mode == 3 && h->phi_valid);  // mode 3 starts from the previous phi
+    if (e == cudaSuccess && phi_zero) e = cudaMemsetAsync(h->phi, 0, h->Np * sizeof(double), s);
     if (e != cudaSuccess) return cuda_check(h, e, "projection memset");
     long long *ci = h->ctrl_host;
     double *si = h->scal_host;
@@ -903,6 +908,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
         const double wa = h->scal_host[kWarmA], wc = h->scal_host[kWarmC];
         const double alpha = (isfinite(wa) && isfinite(wc) && wc > 0.0) ? wa / wc : 0.0;
         k_scale<<<fold_blocks, 256, 0, s>>>(h->phi, h->Np, alpha);
+        phi_zero = false;
         h->launches++;
         h->warm_alpha = alpha;
     }
@@ -918,6 +924,7 @@ static kv_status project_t(kv_handle *h, double tol, int max_iter, int mode, flo
         kv_status fs = project_fcg(h, tol, max_iter, &status, &fcg_iters, &fcg_true2, bb);
         if (fs != KV_OK) return fs;
     } else if (bb > 0.0) {
+        p.zero_start = phi_zero ? 1 : 0;
         const int chunk = pcg ? 4 : 32;  // iterations queued between polls of the control word
         while (true) {
             const long long c = h->ctrl_host[kCgStatus];
@@ -1111,6 +1118,7 @@ extern "C" kv_status kv_project_force_noalloc(int nx, int ny, int nz, double dx,
     p.partials = (double *)(sb + kNaPart);
     p.zc = kCgZc;
     p.nblocks = (int)nblocks;
+    p.zero_start = 1;  // phi is cleared below
 
     long long ch[kCtrlWords];
     double sh[kCgScalars];

@@ -105,6 +105,7 @@ struct CgParams {
     int pcg;             // 1: preconditioned CG (z in the CG vector slot of r, r in rbuf)
     float *rbuf;         // residual of the TMA update pass (FP32)
     int rfield;          // field of rbuf's tensor map holding r
+    int zero_start;      // 1: phi is 0 at the first residual evaluation (r = b, no stencil)
 };
 
 // One level of the multigrid preconditioner: nx, ny, nz interior cells, arrays
