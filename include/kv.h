@@ -396,7 +396,9 @@ kv_status kv_sync(kv_handle *h);
  * 64x16, 128x4, 128x8 with ns in {4, 6});
  * 4: as 3 with a tx x 14 tile whose intermediate step takes one group of four
  * nodes per thread plus one warp for the two halo columns (tx in {32, 64, 128},
- * ty = 14, ns in {3, 4, 6}). Variants 2 to 4 read the coefficient fields,
+ * ty = 14, ns in {2, 3, 4, 6}; with 2 stages the copy of plane k + 3 is
+ * issued once plane k + 1 is consumed and three 64 x 14 blocks share an SM).
+ * Variants 2 to 4 read the coefficient fields,
  * never class bytes, and give bit for bit the result of two single steps.
  * Variants 0 and 1: tx in {32, 64, 128}, ty in {2, 4, 8, 16} with tx*ty/4 in
  * [64, 512]; zc >= 1 planes per block; ns in {4, 6, 8} shared-memory stages

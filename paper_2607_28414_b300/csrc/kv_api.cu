@@ -803,7 +803,7 @@ kv_status kv_set_step_config(kv_handle *h, int variant, int tx, int ty, int zc, 
     if (!h) return KV_ERR_ARG;
     if (variant > 4 || (tx > 0 && tx != 32 && tx != 64 && tx != 128) ||
         (ty > 0 && ty != 2 && ty != 4 && ty != 8 && ty != 14 && ty != 16) ||
-        (ns > 0 && ns != 3 && ns != 4 && ns != 6 && ns != 8))
+        (ns > 0 && ns != 2 && ns != 3 && ns != 4 && ns != 6 && ns != 8))
         return set_error(h, KV_ERR_ARG, "kv_set_step_config: invalid variant, tile or stage count");
     const int ntx = tx > 0 ? tx : h->tx, nty = ty > 0 ? ty : h->ty;
     const int nvar = variant >= 0 ? variant : h->variant;
@@ -875,7 +875,7 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
         if (std::find(zcs4.begin(), zcs4.end(), zc) == zcs4.end()) zcs4.push_back(zc);
     }
     for (int tx : {32, 64, 128})
-        for (int ns : {3, 4})
+        for (int ns : {2, 3, 4})
             for (int zc : zcs4) cands.push_back({4, tx, 14, ns, zc});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

@@ -1173,7 +1173,9 @@ k_step2c_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
 // halo nodes the second step reads. The intermediate planes rotate through
 // three buffers, so one barrier per plane suffices: the buffer written at
 // plane k + 1 was last read by the second step of plane k - 1, before the
-// barrier of plane k. The neighbour sums and the update run on pairs of nodes
+// barrier of plane k. The input ring needs two stages at least (planes k + 1
+// and k + 2 are read at plane k; plane k + 3 is copied into the slot of k + 1
+// after the barrier). The neighbour sums and the update run on pairs of nodes
 // (packed FP32; each lane rounds as the scalar operation does) in the order
 // of kv_update, so the result is bit for bit that of two single steps.
 // ---------------------------------------------------------------------------
@@ -1231,7 +1233,7 @@ __device__ __forceinline__ void kv_update2(float2 u, float2 su, float2 d, float2
 }
 
 template <int TX, int NS, bool HET>
-__global__ void __launch_bounds__(Tile2B<TX, HET>::NT)
+__global__ void __launch_bounds__(Tile2B<TX, HET>::NT, TX == 128 ? 1 : 2)
 k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_coef,
              const float *__restrict__ F, float *__restrict__ out, StepParams p) {
     using T2 = Tile2B<TX, HET>;
@@ -1279,75 +1281,79 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
         for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue(next_issue);
     bool ok = true;
 
-    // intermediate node(s) of this thread: a group of four (x .. x+3) in row
-    // mr, or (halo warp) the node x0 - 1 or x0 + TX of row mr
-    const bool grp = tid < T2::NMID;
+    // Roles. A thread of the group warps owns four intermediate nodes x ..
+    // x+3 of row mr and, for 1 <= mr <= TY, the second step of the same four
+    // nodes (they lie in output row mr - 1). The last warp owns the
+    // intermediate halo nodes x0 - 1 and x0 + TX of the 16 rows (one a lane).
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const bool grp = warp < T2::NMID / 32;
     const int mr = grp ? tid / GX : (tid - T2::NMID) >> 1;
     const int mc = tid % GX;
     const int mcol = grp ? 4 + 4 * mc : ((tid & 1) ? 4 + TX : 3);  // staged column
-    const int ym_ = y0 - 1 + mr, xm_ = x0 - 4 + mcol;
+    const int yr = y0 - 1 + mr, xr = x0 - 4 + mcol;                 // global row, first column
     const int oi = (mr + 1) * BX + mcol;  // in an input field tile
     const int om = mr * BX + mcol;        // in an intermediate plane (and the coefficient tile)
-    const bool mrow = ym_ >= 1 && ym_ <= p.ny - 2;
-    const bool mm0 = mrow && xm_ >= 1 && xm_ <= p.nx - 2, mm1 = mrow && xm_ + 1 <= p.nx - 2,
-               mm2 = mrow && xm_ + 2 <= p.nx - 2, mm3 = mrow && xm_ + 3 <= p.nx - 2;
-    const bool mload = mrow && xm_ >= 0 && xm_ < p.px;  // force row inside the pitched array
-    const float *Fm = Fc + (long long)ym_ * sy + xm_;
-    // output group of this thread (tid < NOUT): row orr, x .. x+3
-    const bool outer = tid < T2::NOUT;
-    const int orr = outer ? tid / GX : 0, oc = tid % GX;
-    const int oo = (orr + 1) * BX + 4 + 4 * oc;  // in an intermediate plane
-    const int y_out = y0 + orr, x_out = x0 + 4 * oc;
-    const bool row_ok = outer && (y_out <= p.ny - 2) && (x_out < p.px);
-    const bool m0 = (x_out >= 1) && (x_out <= p.nx - 2), m1 = (x_out + 1 <= p.nx - 2);
-    const bool m2 = (x_out + 2 <= p.nx - 2), m3 = (x_out + 3 <= p.nx - 2);
+    const bool mrow = yr >= 1 && yr <= p.ny - 2;
+    const bool mm0 = mrow && xr >= 1 && xr <= p.nx - 2, mm1 = mrow && xr + 1 <= p.nx - 2,
+               mm2 = mrow && xr + 2 <= p.nx - 2, mm3 = mrow && xr + 3 <= p.nx - 2;
+    const bool mload = mrow && xr >= 0 && xr < p.px;  // force row inside the pitched array
+    const float *Fm = Fc + (long long)yr * sy + xr;
+    const bool row_ok = grp && mr >= 1 && mr <= TY && yr <= p.ny - 2 && xr < p.px;  // output written
     const float2 Ah = f2(p.Af, p.Af), Bh = f2(p.Bf, p.Bf);
+    // Edge words read without branches: the first group of a row reads its
+    // left neighbour, the last group its right one (a lane is at most one of
+    // them), every other lane word 0 of the tile (one broadcast word on bank
+    // 0, which no edge word shares), so each such load is one shared-memory
+    // wavefront. Second step: lanes without an output row take row 1 as
+    // their centre, inside the plane.
+    const int e1 = mc == 0 ? oi - 1 : mc == GX - 1 ? oi + 4 : 0;
+    const int e2 = !row_ok ? 0 : mc == 0 ? om - 1 : mc == GX - 1 ? om + 4 : 0;
+    const int oc2 = row_ok ? om : BX;
 
-    float4 prev_in[2], prev_mid[2], coef_cur[2], coef_next[2];
     auto stage = [&](int q) { return inr + slot(q) * T2::IN_STAGE; };
-    auto load_prev_in = [&](const float *sc) {
+    // own centre value(s) of the input plane staged at sc
+    auto load_in = [&](const float *sc, float4 (&v)[2]) {
         if (grp) {
-            prev_in[0] = *reinterpret_cast<const float4 *>(sc + oi);
-            prev_in[1] = *reinterpret_cast<const float4 *>(sc + T2::IN_F + oi);
+            v[0] = *reinterpret_cast<const float4 *>(sc + oi);
+            v[1] = *reinterpret_cast<const float4 *>(sc + T2::IN_F + oi);
         } else {
-            prev_in[0].x = sc[oi];
-            prev_in[1].x = sc[T2::IN_F + oi];
-        }
-    };
-    auto load_out_coef = [&](const float *sc, float4 (&dst)[2]) {
-        if (HET && outer) {
-            const float *cs = sc + T2::IN_STATE;
-            dst[0] = *reinterpret_cast<const float4 *>(cs + oo);
-            dst[1] = *reinterpret_cast<const float4 *>(cs + T2::MID_F + oo);
+            v[0].x = sc[oi];
+            v[1].x = sc[T2::IN_F + oi];
         }
     };
 
-    // intermediate plane j into mj: input plane j staged at sc (centre), j+1
-    // at sp (z+), j-1 in prev_in; the x neighbours are read from the staged
-    // rows, which hold them for every group
-    auto compute_mid = [&](const float *sc, const float *sp, float *mj, int j) {
+    // Intermediate plane j into mj. The own nodes of input planes j-1 (zm)
+    // and j (c) are in registers, plane j+1 (zn) is read here from the stage
+    // sp; the y neighbours come from the stage sc of plane j, the x
+    // neighbours beyond the group from the neighbouring lanes (at the tile's
+    // halo columns, from sc). Own results, as stored, into r; own
+    // coefficients into cf.
+    auto compute_mid = [&](const float *sc, const float *sp, float *mj, int j, const float4 (&zm)[2],
+                           const float4 (&c)[2], float4 (&zn)[2], float4 (&r)[2], float4 (&cf)[2]) {
         const bool pin = j >= 1 && j <= p.nz - 2;
         if (grp) {
-            float4 c[2];
             float2 s01[2], s23[2];
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
-                const float *fc = sc + f * T2::IN_F + oi;
-                c[f] = *reinterpret_cast<const float4 *>(fc);
+                const float *sf = sc + f * T2::IN_F, *fc = sf + oi;
+                const float ew = sf[e1];
+                float left = __shfl_up_sync(0xffffffffu, c[f].w, 1);
+                float right = __shfl_down_sync(0xffffffffu, c[f].x, 1);
+                left = mc == 0 ? ew : left;
+                right = mc == GX - 1 ? ew : right;
                 const float4 ym = *reinterpret_cast<const float4 *>(fc - BX);
                 const float4 yp = *reinterpret_cast<const float4 *>(fc + BX);
-                const float4 zp = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
-                nbsum4(c[f], fc[-1], fc[4], ym, yp, prev_in[f], zp, s01[f], s23[f]);
-                prev_in[f] = c[f];
+                zn[f] = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
+                nbsum4(c[f], left, right, ym, yp, zm[f], zn[f], s01[f], s23[f]);
             }
             float2 A01 = Ah, A23 = Ah, B01 = Bh, B23 = Bh;
             if (HET) {
-                const float4 A4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + om);
-                const float4 B4 = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + T2::MID_F + om);
-                A01 = f2lo(A4);
-                A23 = f2hi(A4);
-                B01 = f2lo(B4);
-                B23 = f2hi(B4);
+                cf[0] = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + om);
+                cf[1] = *reinterpret_cast<const float4 *>(sc + T2::IN_STATE + T2::MID_F + om);
+                A01 = f2lo(cf[0]);
+                A23 = f2hi(cf[0]);
+                B01 = f2lo(cf[1]);
+                B23 = f2hi(cf[1]);
             }
             float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (g0 != 0.f && pin && mload) F4 = __ldg(reinterpret_cast<const float4 *>(Fm + (long long)j * sz));
@@ -1356,68 +1362,105 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
             kv_update2(f2lo(c[0]), s01[0], f2lo(c[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
             kv_update2(f2hi(c[0]), s23[0], f2hi(c[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
             const bool q0 = pin && mm0, q1 = pin && mm1, q2 = pin && mm2, q3 = pin && mm3;
-            *reinterpret_cast<float4 *>(mj + om) =
-                make_float4(q0 ? u01.x : 0.f, q1 ? u01.y : 0.f, q2 ? u23.x : 0.f, q3 ? u23.y : 0.f);
-            *reinterpret_cast<float4 *>(mj + T2::MID_F + om) =
-                make_float4(q0 ? d01.x : 0.f, q1 ? d01.y : 0.f, q2 ? d23.x : 0.f, q3 ? d23.y : 0.f);
+            r[0] = make_float4(q0 ? u01.x : 0.f, q1 ? u01.y : 0.f, q2 ? u23.x : 0.f, q3 ? u23.y : 0.f);
+            r[1] = make_float4(q0 ? d01.x : 0.f, q1 ? d01.y : 0.f, q2 ? d23.x : 0.f, q3 ? d23.y : 0.f);
+            *reinterpret_cast<float4 *>(mj + om) = r[0];
+            *reinterpret_cast<float4 *>(mj + T2::MID_F + om) = r[1];
         } else {
-            float cv[2], sv[2];
+            float sv[2];
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const float *fc = sc + f * T2::IN_F + oi;
-                cv[f] = fc[0];
-                sv[f] = kv_add(kv_add(kv_add(fc[-1], fc[1]), kv_add(fc[-BX], fc[BX])),
-                               kv_add(prev_in[f].x, sp[f * T2::IN_F + oi]));
-                prev_in[f].x = cv[f];
+                zn[f].x = sp[f * T2::IN_F + oi];
+                sv[f] = kv_add(kv_add(kv_add(fc[-1], fc[1]), kv_add(fc[-BX], fc[BX])), kv_add(zm[f].x, zn[f].x));
             }
             const float A = HET ? sc[T2::IN_STATE + om] : p.Af;
             const float B = HET ? sc[T2::IN_STATE + T2::MID_F + om] : p.Bf;
             const bool q0 = pin && mm0;
             const float Fv = (g0 != 0.f && q0) ? Fm[(long long)j * sz] : 0.f;
             float uo, dn;
-            kv_update(cv[0], sv[0], cv[1], sv[1], A, B, g0, Fv, uo, dn);
+            kv_update(c[0].x, sv[0], c[1].x, sv[1], A, B, g0, Fv, uo, dn);
             mj[om] = q0 ? uo : 0.f;
             mj[T2::MID_F + om] = q0 ? dn : 0.f;
         }
     };
 
-    // the three intermediate buffers: planes k-2 (free), k-1, k at the top of iteration k
-    float *mfree = mid + 2 * T2::MID_STAGE, *mprev = mid, *mcur = mid + T2::MID_STAGE;
+    // Second step of plane k on the own nodes of a group thread with an
+    // output row: intermediate planes k-1 (mz), k (mcen) and k+1 (mn) of these
+    // nodes are in registers; the y neighbours and the halo columns come from
+    // plane k's buffer mk, the x neighbours beyond the group from the
+    // neighbouring lanes.
+    auto second = [&](int k, const float *mk, const float4 (&mz)[2], const float4 (&mcen)[2],
+                      const float4 (&mn)[2], const float4 (&cf)[2]) {
+        if (!grp) return;  // warp-uniform
+        float2 s01[2], s23[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const float *sf = mk + f * T2::MID_F;
+            const float ew = sf[e2];
+            float left = __shfl_up_sync(0xffffffffu, mcen[f].w, 1);
+            float right = __shfl_down_sync(0xffffffffu, mcen[f].x, 1);
+            left = mc == 0 ? ew : left;
+            right = mc == GX - 1 ? ew : right;
+            const float4 ym = *reinterpret_cast<const float4 *>(sf + oc2 - BX);
+            const float4 yp = *reinterpret_cast<const float4 *>(sf + oc2 + BX);
+            nbsum4(mcen[f], left, right, ym, yp, mz[f], mn[f], s01[f], s23[f]);
+        }
+        const long long gbase = k * sz + (long long)yr * sy + xr;
+        float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g1 != 0.f && row_ok) F4 = __ldg(reinterpret_cast<const float4 *>(Fc + gbase));
+        const float2 A01 = HET ? f2lo(cf[0]) : Ah, A23 = HET ? f2hi(cf[0]) : Ah;
+        const float2 B01 = HET ? f2lo(cf[1]) : Bh, B23 = HET ? f2hi(cf[1]) : Bh;
+        const float2 g = f2(g1, g1);
+        float2 u01, d01, u23, d23;
+        kv_update2(f2lo(mcen[0]), s01[0], f2lo(mcen[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
+        kv_update2(f2hi(mcen[0]), s23[0], f2hi(mcen[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
+        if (!row_ok) return;
+        *reinterpret_cast<float4 *>(out_u + gbase) =
+            make_float4(mm0 ? u01.x : 0.f, mm1 ? u01.y : 0.f, mm2 ? u23.x : 0.f, mm3 ? u23.y : 0.f);
+        *reinterpret_cast<float4 *>(out_d + gbase) =
+            make_float4(mm0 ? d01.x : 0.f, mm1 ? d01.y : 0.f, mm2 ? d23.x : 0.f, mm3 ? d23.y : 0.f);
+    };
 
-    // Prologue: input plane k0-2 into registers, intermediate planes k0-1, k0.
+    // Own nodes in registers: input planes (I*), intermediate planes as
+    // stored (M*), coefficients of planes k (Ccur) and k+1 (Cnext). The
+    // planes rotate through the three sets, unrolled by three below.
+    float4 I0[2] = {}, I1[2] = {}, I2[2] = {}, M0[2] = {}, M1[2] = {}, M2[2] = {}, Ccur[2] = {}, Cnext[2] = {};
+    float *const mb0 = mid, *const mb1 = mid + T2::MID_STAGE, *const mb2 = mid + 2 * T2::MID_STAGE;
+
+    // Prologue: input planes k0-2, k0-1 into registers, intermediate planes
+    // k0-1 and k0 (buffers mb0, mb1).
     ok &= mbar_wait_bounded(bar0 + 8 * slot(qb), par(qb));
-    load_prev_in(stage(qb));
+    load_in(stage(qb), I1);
     __syncthreads();
     refill(qb + NS);
     ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 - 1), par(k0 - 1));
     ok &= mbar_wait_bounded(bar0 + 8 * slot(k0), par(k0));
-    compute_mid(stage(k0 - 1), stage(k0), mprev, k0 - 1);
+    load_in(stage(k0 - 1), I2);
+    compute_mid(stage(k0 - 1), stage(k0), mb0, k0 - 1, I1, I2, I0, M0, Cnext);
     __syncthreads();
     refill(k0 - 1 + NS);
     ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 + 1), par(k0 + 1));
-    compute_mid(stage(k0), stage(k0 + 1), mcur, k0);
-    load_out_coef(stage(k0), coef_cur);
+    compute_mid(stage(k0), stage(k0 + 1), mb1, k0, I2, I0, I1, M1, Ccur);
     __syncthreads();  // intermediate planes k0-1 and k0 complete, input plane k0 consumed
     refill(k0 + NS);
-    if (outer) {
-        prev_mid[0] = *reinterpret_cast<const float4 *>(mprev + oo);
-        prev_mid[1] = *reinterpret_cast<const float4 *>(mprev + T2::MID_F + oo);
-    }
     const bool sens = p.ns > 0 && step < p.cap;
     int so_k = sens ? __ldg(p.sens_off + k0) : 0;  // sensors of plane k: sens_ord[so_k .. so_k1)
 
     // input slots of planes k+1 and k+2, parity of k+2's stage
     int s1 = slot(k0 + 1), s2 = slot(k0 + 2);
     uint32_t par2 = par(k0 + 2);
-    for (int k = k0; k < k1; ++k) {
+    // one plane k: input planes k (iz), k+1 (ic) in registers, k+2 into inx;
+    // intermediate planes k-1 (mz), k (mcn) in registers, k+1 into mnx and
+    // its buffer mnb; plane k's buffer mk
+    auto body = [&](int k, const float4 (&iz)[2], const float4 (&ic)[2], float4 (&inx)[2],
+                    const float4 (&mz)[2], const float4 (&mcn)[2], float4 (&mnx)[2], const float *mk,
+                    float *mnb) {
         const int so_k1 = sens ? __ldg(p.sens_off + k + 1) : 0;
         ok &= mbar_wait_bounded(bar0 + 8 * s2, par2);
-        const float *sc = inr + s1 * T2::IN_STAGE;
-        compute_mid(sc, inr + s2 * T2::IN_STAGE, mfree, k + 1);  // into the buffer of plane k-2
-        if (k + 1 < k1) load_out_coef(sc, coef_next);
+        compute_mid(inr + s1 * T2::IN_STAGE, inr + s2 * T2::IN_STAGE, mnb, k + 1, iz, ic, inx, mnx, Cnext);
         __syncthreads();  // intermediate plane k+1 complete; input plane k+1 consumed
         refill(k + 1 + NS);
-        const float *mk = mcur, *mn = mfree;  // planes k and k+1
         // sensors of the intermediate step owned by this block (plane k, component comp)
         if (sens) {
             float *tr = reinterpret_cast<float *>(p.traces) + (size_t)step * p.ns * 3;
@@ -1428,47 +1471,21 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
                     tr[3 * s + comp] = mk[(jj - y0 + 1) * BX + (i - x0 + 4)];
             }
         }
-        // second step of plane k from intermediate planes k-1 (registers), k, k+1
-        float4 c[2];
-        float2 s01[2], s23[2];
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            const float *fc = mk + f * T2::MID_F + oo;
-            c[f] = *reinterpret_cast<const float4 *>(fc);
-            const float4 ym = *reinterpret_cast<const float4 *>(fc - BX);
-            const float4 yp = *reinterpret_cast<const float4 *>(fc + BX);
-            const float4 zp = *reinterpret_cast<const float4 *>(mn + f * T2::MID_F + oo);
-            nbsum4(c[f], fc[-1], fc[4], ym, yp, prev_mid[f], zp, s01[f], s23[f]);
-            prev_mid[f] = c[f];
-        }
-        if (row_ok) {
-            const long long gbase = k * sz + (long long)y_out * sy + x_out;
-            float4 F4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (g1 != 0.f) F4 = __ldg(reinterpret_cast<const float4 *>(Fc + gbase));
-            const float2 A01 = HET ? f2lo(coef_cur[0]) : Ah, A23 = HET ? f2hi(coef_cur[0]) : Ah;
-            const float2 B01 = HET ? f2lo(coef_cur[1]) : Bh, B23 = HET ? f2hi(coef_cur[1]) : Bh;
-            const float2 g = f2(g1, g1);
-            float2 u01, d01, u23, d23;
-            kv_update2(f2lo(c[0]), s01[0], f2lo(c[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
-            kv_update2(f2hi(c[0]), s23[0], f2hi(c[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
-            *reinterpret_cast<float4 *>(out_u + gbase) =
-                make_float4(m0 ? u01.x : 0.f, m1 ? u01.y : 0.f, m2 ? u23.x : 0.f, m3 ? u23.y : 0.f);
-            *reinterpret_cast<float4 *>(out_d + gbase) =
-                make_float4(m0 ? d01.x : 0.f, m1 ? d01.y : 0.f, m2 ? d23.x : 0.f, m3 ? d23.y : 0.f);
-        }
-        coef_cur[0] = coef_next[0];
-        coef_cur[1] = coef_next[1];
+        second(k, mk, mz, mcn, mnx, Ccur);
+        Ccur[0] = Cnext[0];
+        Ccur[1] = Cnext[1];
         so_k = so_k1;
-        // rotate: the buffer of plane k-1 is the next free one
-        float *t = mprev;
-        mprev = mcur;
-        mcur = mfree;
-        mfree = t;
         s1 = s2;
         if (++s2 == NS) {
             s2 = 0;
             par2 ^= 1u;
         }
+    };
+    // plane k0-1 is in mb0 and (M0, I-sets as set up above), plane k0 in mb1
+    for (int k = k0; k < k1; k += 3) {
+        body(k, I0, I1, I2, M0, M1, M2, mb1, mb2);
+        if (k + 1 < k1) body(k + 1, I1, I2, I0, M1, M2, M0, mb2, mb0);
+        if (k + 2 < k1) body(k + 2, I2, I0, I1, M2, M0, M1, mb0, mb1);
     }
     if (__syncthreads_or(!ok) && tid == 0) {
         atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
@@ -1717,6 +1734,7 @@ static bool pick2b_tile(int tx, int ty, bool het, TmaKernel *k, size_t *smem, in
 static bool tma2_kernel_for(int variant, int tx, int ty, int ns, bool het, TmaKernel *k, size_t *smem, int *nt) {
     if (variant == 4) {
         switch (ns) {
+            case 2: return pick2b_tile<2>(tx, ty, het, k, smem, nt);
             case 3: return pick2b_tile<3>(tx, ty, het, k, smem, nt);
             case 4: return pick2b_tile<4>(tx, ty, het, k, smem, nt);
             case 6: return pick2b_tile<6>(tx, ty, het, k, smem, nt);
