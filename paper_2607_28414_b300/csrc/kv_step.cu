@@ -1262,9 +1262,9 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
     __syncthreads();
     auto slot = [&](int q) { return (int)((unsigned)(q - qb) % NS); };
     auto par = [&](int q) { return ((unsigned)(q - qb) / NS) & 1u; };
-    auto issue = [&](int q) {
-        const uint32_t bar = bar0 + 8 * slot(q);
-        float *st = inr + slot(q) * T2::IN_STAGE;
+    auto issue_to = [&](int q, int sl) {  // plane q into stage slot sl
+        const uint32_t bar = bar0 + 8 * sl;
+        float *st = inr + sl * T2::IN_STAGE;
         mbar_expect_tx(bar, T2::TX_BYTES);
         tma_load_4d(smem_u32(st), &tm_in, x0 - 4, y0 - 2, q, comp, bar);
         tma_load_4d(smem_u32(st + T2::IN_F), &tm_in, x0 - 4, y0 - 2, q, 3 + comp, bar);
@@ -1274,11 +1274,11 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
     auto refill = [&](int upto) {  // thread 0, after a barrier: stage planes up to `upto`
         if (tid == 0) {
             fence_proxy_async();
-            for (; next_issue <= min(k1 + 1, upto); ++next_issue) issue(next_issue);
+            for (; next_issue <= min(k1 + 1, upto); ++next_issue) issue_to(next_issue, slot(next_issue));
         }
     };
     if (tid == 0)
-        for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue(next_issue);
+        for (; next_issue <= min(k1 + 1, qb + NS - 1); ++next_issue) issue_to(next_issue, slot(next_issue));
     bool ok = true;
 
     // Roles. A thread of the group warps owns four intermediate nodes x ..
@@ -1322,20 +1322,21 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
         }
     };
 
-    // Intermediate plane j into mj. The own nodes of input planes j-1 (zm)
-    // and j (c) are in registers, plane j+1 (zn) is read here from the stage
-    // sp; the y neighbours come from the stage sc of plane j, the x
+    // Intermediate plane j into mj. The own nodes of input plane j-1 (zm) are
+    // in registers; plane j (the centre, kept in c for the next plane) and
+    // j+1 are read from the stages sc and sp, the y neighbours from sc, the x
     // neighbours beyond the group from the neighbouring lanes (at the tile's
     // halo columns, from sc). Own results, as stored, into r; own
     // coefficients into cf.
     auto compute_mid = [&](const float *sc, const float *sp, float *mj, int j, const float4 (&zm)[2],
-                           const float4 (&c)[2], float4 (&zn)[2], float4 (&r)[2], float4 (&cf)[2]) {
+                           float4 (&c)[2], float4 (&r)[2], float4 (&cf)[2]) {
         const bool pin = j >= 1 && j <= p.nz - 2;
         if (grp) {
             float2 s01[2], s23[2];
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const float *sf = sc + f * T2::IN_F, *fc = sf + oi;
+                c[f] = *reinterpret_cast<const float4 *>(fc);
                 const float ew = sf[e1];
                 float left = __shfl_up_sync(0xffffffffu, c[f].w, 1);
                 float right = __shfl_down_sync(0xffffffffu, c[f].x, 1);
@@ -1343,8 +1344,8 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
                 right = mc == GX - 1 ? ew : right;
                 const float4 ym = *reinterpret_cast<const float4 *>(fc - BX);
                 const float4 yp = *reinterpret_cast<const float4 *>(fc + BX);
-                zn[f] = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
-                nbsum4(c[f], left, right, ym, yp, zm[f], zn[f], s01[f], s23[f]);
+                const float4 zp = *reinterpret_cast<const float4 *>(sp + f * T2::IN_F + oi);
+                nbsum4(c[f], left, right, ym, yp, zm[f], zp, s01[f], s23[f]);
             }
             float2 A01 = Ah, A23 = Ah, B01 = Bh, B23 = Bh;
             if (HET) {
@@ -1371,8 +1372,8 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const float *fc = sc + f * T2::IN_F + oi;
-                zn[f].x = sp[f * T2::IN_F + oi];
-                sv[f] = kv_add(kv_add(kv_add(fc[-1], fc[1]), kv_add(fc[-BX], fc[BX])), kv_add(zm[f].x, zn[f].x));
+                c[f].x = fc[0];
+                sv[f] = kv_add(kv_add(kv_add(fc[-1], fc[1]), kv_add(fc[-BX], fc[BX])), kv_add(zm[f].x, sp[f * T2::IN_F + oi]));
             }
             const float A = HET ? sc[T2::IN_STATE + om] : p.Af;
             const float B = HET ? sc[T2::IN_STATE + T2::MID_F + om] : p.Bf;
@@ -1422,47 +1423,57 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
             make_float4(mm0 ? d01.x : 0.f, mm1 ? d01.y : 0.f, mm2 ? d23.x : 0.f, mm3 ? d23.y : 0.f);
     };
 
-    // Own nodes in registers: input planes (I*), intermediate planes as
-    // stored (M*), coefficients of planes k (Ccur) and k+1 (Cnext). The
-    // planes rotate through the three sets, unrolled by three below.
-    float4 I0[2] = {}, I1[2] = {}, I2[2] = {}, M0[2] = {}, M1[2] = {}, M2[2] = {}, Ccur[2] = {}, Cnext[2] = {};
+    // Own nodes in registers: input planes (IA, IB: k and k+1), intermediate
+    // planes as stored (M*: k-1, k, k+1), coefficients of planes k (Ccur) and
+    // k+1 (Cnext). The sets rotate, unrolled by three below.
+    float4 IA[2] = {}, IB[2] = {}, M0[2] = {}, M1[2] = {}, M2[2] = {}, Ccur[2] = {}, Cnext[2] = {};
     float *const mb0 = mid, *const mb1 = mid + T2::MID_STAGE, *const mb2 = mid + 2 * T2::MID_STAGE;
 
-    // Prologue: input planes k0-2, k0-1 into registers, intermediate planes
-    // k0-1 and k0 (buffers mb0, mb1).
+    // Prologue: input plane k0-2 into registers, intermediate planes k0-1
+    // and k0 (buffers mb0, mb1); input plane k0 left in IA.
     ok &= mbar_wait_bounded(bar0 + 8 * slot(qb), par(qb));
-    load_in(stage(qb), I1);
+    load_in(stage(qb), IA);
     __syncthreads();
     refill(qb + NS);
     ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 - 1), par(k0 - 1));
     ok &= mbar_wait_bounded(bar0 + 8 * slot(k0), par(k0));
-    load_in(stage(k0 - 1), I2);
-    compute_mid(stage(k0 - 1), stage(k0), mb0, k0 - 1, I1, I2, I0, M0, Cnext);
+    compute_mid(stage(k0 - 1), stage(k0), mb0, k0 - 1, IA, IB, M0, Cnext);
     __syncthreads();
     refill(k0 - 1 + NS);
     ok &= mbar_wait_bounded(bar0 + 8 * slot(k0 + 1), par(k0 + 1));
-    compute_mid(stage(k0), stage(k0 + 1), mb1, k0, I2, I0, I1, M1, Ccur);
+    compute_mid(stage(k0), stage(k0 + 1), mb1, k0, IB, IA, M1, Ccur);
     __syncthreads();  // intermediate planes k0-1 and k0 complete, input plane k0 consumed
     refill(k0 + NS);
-    const bool sens = p.ns > 0 && step < p.cap;
+    // sensors of the intermediate step: only a block whose column holds one
+    // looks them up plane by plane
+    bool sens = p.ns > 0 && step < p.cap;
+    if (sens) {
+        int hit = 0;
+        for (int s = tid; s < p.ns; s += T2::NT) {
+            const int i = p.sensors[3 * s], jj = p.sensors[3 * s + 1], kk = p.sensors[3 * s + 2];
+            hit |= i >= x0 && i < x0 + TX && jj >= y0 && jj < y0 + TY && jj <= p.ny - 2 && kk >= k0 && kk < k1;
+        }
+        sens = __syncthreads_or(hit) != 0;
+    }
     int so_k = sens ? __ldg(p.sens_off + k0) : 0;  // sensors of plane k: sens_ord[so_k .. so_k1)
 
-    // input slots of planes k+1 and k+2, parity of k+2's stage
-    int s1 = slot(k0 + 1), s2 = slot(k0 + 2);
-    uint32_t par2 = par(k0 + 2);
-    // one plane k: input planes k (iz), k+1 (ic) in registers, k+2 into inx;
-    // intermediate planes k-1 (mz), k (mcn) in registers, k+1 into mnx and
-    // its buffer mnb; plane k's buffer mk
-    auto body = [&](int k, const float4 (&iz)[2], const float4 (&ic)[2], float4 (&inx)[2],
-                    const float4 (&mz)[2], const float4 (&mcn)[2], float4 (&mnx)[2], const float *mk,
-                    float *mnb) {
-        const int so_k1 = sens ? __ldg(p.sens_off + k + 1) : 0;
+    // one plane k: input plane k (iz) in registers, k+1 into icn (stage
+    // slots s1 of plane k+1 and s2, parity par2, of plane k+2); intermediate
+    // planes k-1 (mz), k (mcn) in registers, k+1 into mnx and its buffer mnb;
+    // plane k's buffer mk; coefficients of plane k (ccur), plane k+1 into cnx.
+    // Thread 0 then stages plane k+1+NS into slot s1.
+    auto body = [&](int k, const float4 (&iz)[2], float4 (&icn)[2], const float4 (&mz)[2],
+                    const float4 (&mcn)[2], float4 (&mnx)[2], const float *mk, float *mnb, int s1, int s2,
+                    uint32_t par2, const float4 (&ccur)[2], float4 (&cnx)[2]) {
         ok &= mbar_wait_bounded(bar0 + 8 * s2, par2);
-        compute_mid(inr + s1 * T2::IN_STAGE, inr + s2 * T2::IN_STAGE, mnb, k + 1, iz, ic, inx, mnx, Cnext);
+        compute_mid(inr + s1 * T2::IN_STAGE, inr + s2 * T2::IN_STAGE, mnb, k + 1, iz, icn, mnx, cnx);
         __syncthreads();  // intermediate plane k+1 complete; input plane k+1 consumed
-        refill(k + 1 + NS);
-        // sensors of the intermediate step owned by this block (plane k, component comp)
-        if (sens) {
+        if (tid == 0 && k + 1 + NS <= k1 + 1) {
+            fence_proxy_async();
+            issue_to(k + 1 + NS, s1);
+        }
+        if (sens) {  // sensors of the intermediate step owned by this block (plane k, component comp)
+            const int so_k1 = __ldg(p.sens_off + k + 1);
             float *tr = reinterpret_cast<float *>(p.traces) + (size_t)step * p.ns * 3;
             for (int q = so_k + tid; q < so_k1; q += T2::NT) {
                 const int s = p.sens_ord[q];
@@ -1470,23 +1481,54 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
                 if (i >= x0 && i < x0 + TX && jj >= y0 && jj < y0 + TY && jj <= p.ny - 2)
                     tr[3 * s + comp] = mk[(jj - y0 + 1) * BX + (i - x0 + 4)];
             }
+            so_k = so_k1;
         }
-        second(k, mk, mz, mcn, mnx, Ccur);
+        second(k, mk, mz, mcn, mnx, ccur);
+    };
+    // Three planes per round (plane k0-1 in mb0, k0 in mb1 as set up above);
+    // the input and coefficient sets alternate and are realigned once a
+    // round. With three stages the slots of a round are fixed: (0, 1), (1, 2),
+    // (2, 0).
+    auto realign = [&]() {
+        IA[0] = IB[0];
+        IA[1] = IB[1];
         Ccur[0] = Cnext[0];
         Ccur[1] = Cnext[1];
-        so_k = so_k1;
-        s1 = s2;
-        if (++s2 == NS) {
-            s2 = 0;
-            par2 ^= 1u;
-        }
     };
-    // plane k0-1 is in mb0 and (M0, I-sets as set up above), plane k0 in mb1
-    for (int k = k0; k < k1; k += 3) {
-        body(k, I0, I1, I2, M0, M1, M2, mb1, mb2);
-        if (k + 1 < k1) body(k + 1, I1, I2, I0, M1, M2, M0, mb2, mb0);
-        if (k + 2 < k1) body(k + 2, I2, I0, I1, M2, M0, M1, mb0, mb1);
+    if constexpr (NS == 3) {
+        uint32_t rp = 0;  // parity of round r = (k - k0) / 3
+        for (int k = k0; k < k1; k += 3) {
+            body(k, IA, IB, M0, M1, M2, mb1, mb2, 0, 1, rp ^ 1u, Ccur, Cnext);
+            if (k + 1 < k1) body(k + 1, IB, IA, M1, M2, M0, mb2, mb0, 1, 2, rp ^ 1u, Cnext, Ccur);
+            if (k + 2 < k1) body(k + 2, IA, IB, M2, M0, M1, mb0, mb1, 2, 0, rp, Ccur, Cnext);
+            realign();
+            rp ^= 1u;
+        }
+    } else {
+        int s1 = slot(k0 + 1), s2 = slot(k0 + 2);  // slots of planes k+1 and k+2
+        uint32_t par2 = par(k0 + 2);
+        auto advance = [&]() {
+            s1 = s2;
+            if (++s2 == NS) {
+                s2 = 0;
+                par2 ^= 1u;
+            }
+        };
+        for (int k = k0; k < k1; k += 3) {
+            body(k, IA, IB, M0, M1, M2, mb1, mb2, s1, s2, par2, Ccur, Cnext);
+            advance();
+            if (k + 1 < k1) {
+                body(k + 1, IB, IA, M1, M2, M0, mb2, mb0, s1, s2, par2, Cnext, Ccur);
+                advance();
+            }
+            if (k + 2 < k1) {
+                body(k + 2, IA, IB, M2, M0, M1, mb0, mb1, s1, s2, par2, Ccur, Cnext);
+                advance();
+            }
+            realign();
+        }
     }
+    next_issue = k1 + 2;  // every plane up to k1 + 1 has been staged
     if (__syncthreads_or(!ok) && tid == 0) {
         atomicOr(reinterpret_cast<unsigned long long *>(&p.ctrl[kErrFlags]), 1ull);
         for (int q = max(qb, next_issue - NS); q < next_issue; ++q) mbar_wait_bounded(bar0 + 8 * slot(q), par(q));
