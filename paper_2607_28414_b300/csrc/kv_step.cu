@@ -1178,6 +1178,16 @@ k_step2c_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
 // after the barrier). The neighbour sums and the update run on pairs of nodes
 // (packed FP32; each lane rounds as the scalar operation does) in the order
 // of kv_update, so the result is bit for bit that of two single steps.
+//
+// The kernel is bound by the shared-memory pipe, so it reads as little of it
+// as it can. The second step of a group runs on the thread that computed the
+// same four intermediate nodes: their planes k - 1, k and k + 1 (the z
+// neighbours and the centre) stay in its registers, and only the y
+// neighbours come from the buffer. The input plane below the centre stays in
+// registers too. The x neighbours beyond a group are the neighbouring lanes'
+// values (warp shuffles); the first and last group of a row read the tile's
+// halo column in one load that the other lanes aim at one broadcast word.
+// The three planes of a register set rotate, unrolled by three.
 // ---------------------------------------------------------------------------
 template <int TX, bool HET>
 struct Tile2B {
