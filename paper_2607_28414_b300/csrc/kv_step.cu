@@ -1309,6 +1309,9 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
     const bool mload = mrow && xr >= 0 && xr < p.px;  // force row inside the pitched array
     const float *Fm = Fc + (long long)yr * sy + xr;
     const bool row_ok = grp && mr >= 1 && mr <= TY && yr <= p.ny - 2 && xr < p.px;  // output written
+    // no node of the block's intermediate tile (x0 - 1 .. x0 + TX, y0 - 1 ..
+    // y0 + TY) on the boundary: the masks are all true off the end planes
+    const bool inner = x0 >= 2 && x0 + TX <= p.nx - 2 && y0 >= 2 && y0 + TY <= p.ny - 2;
     const float2 Ah = f2(p.Af, p.Af), Bh = f2(p.Bf, p.Bf);
     // Edge words read without branches: the first group of a row reads its
     // left neighbour, the last group its right one (a lane is at most one of
@@ -1372,9 +1375,14 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
             float2 u01, d01, u23, d23;
             kv_update2(f2lo(c[0]), s01[0], f2lo(c[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
             kv_update2(f2hi(c[0]), s23[0], f2hi(c[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
-            const bool q0 = pin && mm0, q1 = pin && mm1, q2 = pin && mm2, q3 = pin && mm3;
-            r[0] = make_float4(q0 ? u01.x : 0.f, q1 ? u01.y : 0.f, q2 ? u23.x : 0.f, q3 ? u23.y : 0.f);
-            r[1] = make_float4(q0 ? d01.x : 0.f, q1 ? d01.y : 0.f, q2 ? d23.x : 0.f, q3 ? d23.y : 0.f);
+            if (inner && pin) {  // block-uniform: no node of the plane on the boundary
+                r[0] = make_float4(u01.x, u01.y, u23.x, u23.y);
+                r[1] = make_float4(d01.x, d01.y, d23.x, d23.y);
+            } else {
+                const bool q0 = pin && mm0, q1 = pin && mm1, q2 = pin && mm2, q3 = pin && mm3;
+                r[0] = make_float4(q0 ? u01.x : 0.f, q1 ? u01.y : 0.f, q2 ? u23.x : 0.f, q3 ? u23.y : 0.f);
+                r[1] = make_float4(q0 ? d01.x : 0.f, q1 ? d01.y : 0.f, q2 ? d23.x : 0.f, q3 ? d23.y : 0.f);
+            }
             *reinterpret_cast<float4 *>(mj + om) = r[0];
             *reinterpret_cast<float4 *>(mj + T2::MID_F + om) = r[1];
         } else {
@@ -1427,10 +1435,15 @@ k_step2b_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ 
         kv_update2(f2lo(mcen[0]), s01[0], f2lo(mcen[1]), s01[1], A01, B01, g, f2lo(F4), u01, d01);
         kv_update2(f2hi(mcen[0]), s23[0], f2hi(mcen[1]), s23[1], A23, B23, g, f2hi(F4), u23, d23);
         if (!row_ok) return;
-        *reinterpret_cast<float4 *>(out_u + gbase) =
-            make_float4(mm0 ? u01.x : 0.f, mm1 ? u01.y : 0.f, mm2 ? u23.x : 0.f, mm3 ? u23.y : 0.f);
-        *reinterpret_cast<float4 *>(out_d + gbase) =
-            make_float4(mm0 ? d01.x : 0.f, mm1 ? d01.y : 0.f, mm2 ? d23.x : 0.f, mm3 ? d23.y : 0.f);
+        if (inner) {
+            *reinterpret_cast<float4 *>(out_u + gbase) = make_float4(u01.x, u01.y, u23.x, u23.y);
+            *reinterpret_cast<float4 *>(out_d + gbase) = make_float4(d01.x, d01.y, d23.x, d23.y);
+        } else {
+            *reinterpret_cast<float4 *>(out_u + gbase) =
+                make_float4(mm0 ? u01.x : 0.f, mm1 ? u01.y : 0.f, mm2 ? u23.x : 0.f, mm3 ? u23.y : 0.f);
+            *reinterpret_cast<float4 *>(out_d + gbase) =
+                make_float4(mm0 ? d01.x : 0.f, mm1 ? d01.y : 0.f, mm2 ? d23.x : 0.f, mm3 ? d23.y : 0.f);
+        }
     };
 
     // Own nodes in registers: input planes (IA, IB: k and k+1), intermediate

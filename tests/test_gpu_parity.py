@@ -152,6 +152,23 @@ def test_two_step_kernel_matches_plain_kernel_bitwise(device, variant, het, n_st
                 assert np.array_equal(f, ref_f), (tx, ty, ns, zc)
 
 
+@pytest.mark.parametrize("het", [True, False])
+def test_two_step_interior_blocks_match_plain_kernel_bitwise(device, het):
+    """Variant 4 on a grid wide enough for blocks whose tile and halo hold no
+    boundary node (the unmasked path of the 64- and 128-wide tiles), against
+    single steps bit for bit."""
+    w = ragged_workload(nx=300, ny=50, nz=20, het=het)
+    v0 = inputs.curl_gaussian_velocity(w.nx, w.ny, w.nz, w.dx, sigma=1e-3, envelope="xyz")
+    ref_tr, ref_f = run_variant(w, {"variant": 1}, 40, v0)
+    assert np.abs(ref_f).max() > 0
+    for tx in (32, 64, 128):
+        for ns in (3, 4):
+            for zc in (7, 18):
+                tr, f = run_variant(w, {"variant": 4, "tx": tx, "ty": 14, "zc": zc, "ns": ns}, 40, v0)
+                assert np.array_equal(tr, ref_tr), (tx, ns, zc)
+                assert np.array_equal(f, ref_f), (tx, ns, zc)
+
+
 @pytest.mark.parametrize("variant", [2, 3, 4])
 def test_two_step_graph_replay_matches_direct(device, variant):
     w = ragged_workload()
