@@ -412,7 +412,7 @@ kv_status kv_get_step_config(kv_handle *h, int *cfg);
 
 /* Autotuner of the FP32 step: times trial_steps steps of every supported
  * (variant, tile, stage count, z chunk; z chunks 16, 32, 64, and for variant 4
- * 32, 64, 128 and a third, a half and all of the interior depth) on this
+ * 32, 64, 128 and a third, a half and all of the interior depth, 3 stages) on this
  * handle's grid with CUDA events
  * on its stream, times the four fastest (and the fastest one-step candidate)
  * again over 4 x trial_steps steps and keeps the fastest of those, a two-step

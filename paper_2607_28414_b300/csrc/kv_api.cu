@@ -874,9 +874,11 @@ kv_status kv_autotune_step(kv_handle *h, int trial_steps, double *best_ms) {
         const int zc = (h->nz - 2 + parts - 1) / parts;
         if (std::find(zcs4.begin(), zcs4.end(), zc) == zcs4.end()) zcs4.push_back(zc);
     }
+    // three stages only: with four or six the 64- and 128-wide tiles spill at
+    // the 96 registers of two blocks per SM, with two the copies' latency shows
+    // (both slower in whole passes; short trials can rank them first)
     for (int tx : {32, 64, 128})
-        for (int ns : {2, 3, 4})
-            for (int zc : zcs4) cands.push_back({4, tx, 14, ns, zc});
+        for (int zc : zcs4) cands.push_back({4, tx, 14, 3, zc});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_error(h, KV_ERR_CUDA, "kv_autotune_step: cudaEventCreate failed");
