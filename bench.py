@@ -573,6 +573,8 @@ def main():
                                         with_source=True)
     if traffic is not None:
         traffic *= spl  # the capture's bytes per step, per launch
+    # DRAM rate the stored bytes imply at this run's launch time
+    dram_gbs = traffic / launch_s / 1e9 if traffic is not None and launch_s > 0 else None
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -666,7 +668,13 @@ def main():
                                                  "+ write 48 B + medium"
                                                  + (", once per two steps" if two_step else "")
                                                  + f") + {FORCE_BYTES_PER_CELL} B/cell on force "
-                                                 "steps")},
+                                                 "steps"),
+                         "dram_gbs_from_traffic": dram_gbs,
+                         "dram_frac_from_traffic": dram_gbs / peak if dram_gbs is not None else None,
+                         "note": ("two steps per launch read and write the state once, so the "
+                                  "single step's algorithmic bytes can exceed the copy peak; "
+                                  "dram_*_from_traffic is what DRAM moved"
+                                  if two_step else None)},
             "gpu_launches": int(launches),
             "clocks": clk,
             "e2e": e2e,
